@@ -1,0 +1,334 @@
+"""Seeded synthetic problem instances for tree-structured coupled OT.
+
+This module only builds *inputs*: tree topologies, support points, fixed
+marginals and (for the stored-cost form) dense cost matrices.  It holds none of
+the solver's arithmetic (no kernels, messages, potentials or updates), so both
+the CUDA path and the CPU oracle can read the very same arrays.
+
+Workloads follow the paper's numerical section (Sec. 5: squared-Euclidean
+costs, probability vectors on a uniform grid in [0,1]) and the five workload
+shapes this project is measured on:
+
+* ``chain_problem``   -- 5-node chain, n=64 uniform 1-D grid, |x-y|^2, eps=0.01,
+  two fixed end nodes with 2-component Gaussian mixtures.
+* ``star_problem``    -- barycenter star: 8 fixed leaves on a 32x32 grid, a free
+  centre on the same grid, squared-Euclidean cost normalised to max 1,
+  eps=0.005, 3-component mixtures.
+* ``prufer_problem``  -- 64-node random tree from a Pruefer sequence with exactly
+  32 leaves, n=4096 points U[0,1]^3 per node, dense FP32 cost per edge,
+  Dirichlet(1) leaf marginals, eps=0.01.
+* ``batched_problems`` -- 512 random trees with 4..32 nodes, n_j uniform in
+  {128..2048}, 2-D uniform points, eps log-uniform in [0.002, 0.05].
+* ``star_problem`` with other seeds/eps -- the warm-start training/test sets.
+
+Every generator takes a ``seed``; by convention ``seed = 1000*workload + instance``.
+All randomness comes from ``numpy.random.default_rng(seed)`` (PCG64).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+COST_SQEUCLID = "sqeuclid"
+COST_DENSE = "dense"
+
+
+@dataclass
+class TreeProblem:
+    """One coupled bi-marginal OT problem on a tree (the problem of Sec. 3).
+
+    Attributes
+    ----------
+    edges : int32 [J-1, 2]; edge e joins ``edges[e,0]`` and ``edges[e,1]``.
+        Its cost matrix is indexed [support of edges[e,0], support of edges[e,1]].
+    n : int32 [J]; support size n_j of every node.
+    fixed : bool [J]; True for the nodes in Gamma (given marginals).
+    marginals : node -> float64 [n_j] probability vector, fixed nodes only.
+    eps : entropic regularisation epsilon.
+    coords : per node float32 [n_j, D] support points.
+    cost_scale : the cost is ``cost_scale * ||x - y||^2`` between support points.
+    cost_kind : ``"sqeuclid"`` (the solver recomputes C from ``coords``) or
+        ``"dense"`` (the solver reads a stored FP32 matrix per edge; the matrix
+        is the FP64 value of the formula above rounded once to FP32).
+    dense_costs : optional list of float32 [n_a, n_b] per edge; filled lazily by
+        ``dense_cost(e)`` when ``cost_kind == "dense"``.
+    """
+
+    name: str
+    edges: np.ndarray
+    n: np.ndarray
+    fixed: np.ndarray
+    marginals: Dict[int, np.ndarray]
+    eps: float
+    coords: List[np.ndarray]
+    cost_scale: float
+    cost_kind: str = COST_SQEUCLID
+    dense_costs: Optional[List[Optional[np.ndarray]]] = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def num_nodes(self) -> int:
+        return int(self.n.shape[0])
+
+    @property
+    def num_edges(self) -> int:
+        return int(self.edges.shape[0])
+
+    @property
+    def dim(self) -> int:
+        return int(self.coords[0].shape[1])
+
+    def dense_cost(self, e: int) -> np.ndarray:
+        """FP32 dense cost of edge e (rows: edges[e,0]); cached after first use."""
+        if self.dense_costs is None:
+            self.dense_costs = [None] * self.num_edges
+        if self.dense_costs[e] is None:
+            a, b = int(self.edges[e, 0]), int(self.edges[e, 1])
+            self.dense_costs[e] = sqeuclid_cost_f32(self.coords[a], self.coords[b], self.cost_scale)
+        return self.dense_costs[e]
+
+    def elements_per_half_step(self) -> int:
+        """Sum over edges of n_a * n_b (each half-step touches every edge once)."""
+        return int(sum(int(self.n[a]) * int(self.n[b]) for a, b in self.edges))
+
+
+# --------------------------------------------------------------------------
+# cost matrices (problem data, FP64 arithmetic rounded once to FP32)
+# --------------------------------------------------------------------------
+
+def sqeuclid_cost_f32(xa: np.ndarray, xb: np.ndarray, scale: float, rows=None) -> np.ndarray:
+    """``float32(scale * sum_d (xa_d - xb_d)^2)`` evaluated in FP64.
+
+    The operation order (difference, square, running sum over d, then the
+    scale) is fixed so that the torch version below yields identical bits.
+    ``rows`` optionally selects a subset of rows of the result.
+    """
+    A = np.asarray(xa, dtype=np.float64)
+    if rows is not None:
+        A = A[np.asarray(rows)]
+    B = np.asarray(xb, dtype=np.float64)
+    acc = None
+    for d in range(A.shape[1]):
+        diff = A[:, d][:, None] - B[:, d][None, :]
+        sq = diff * diff
+        acc = sq if acc is None else acc + sq
+    if scale != 1.0:
+        acc = acc * scale
+    return acc.astype(np.float32)
+
+
+def sqeuclid_cost_f32_torch(xa, xb, scale: float, device):
+    """Same values as ``sqeuclid_cost_f32``, built with torch on ``device``.
+
+    Separate elementwise ops (no fused multiply-add) in FP64, then one rounding
+    to FP32, so the result matches the numpy version bit for bit.
+    """
+    import torch
+
+    A = torch.as_tensor(np.asarray(xa), device=device).to(torch.float64)
+    B = torch.as_tensor(np.asarray(xb), device=device).to(torch.float64)
+    acc = None
+    for d in range(A.shape[1]):
+        diff = A[:, d].unsqueeze(1) - B[:, d].unsqueeze(0)
+        sq = diff * diff
+        acc = sq if acc is None else acc + sq
+        del diff, sq
+    if scale != 1.0:
+        acc = acc * scale
+    out = acc.to(torch.float32)
+    del acc
+    return out
+
+
+# --------------------------------------------------------------------------
+# topologies
+# --------------------------------------------------------------------------
+
+def chain_edges(J: int) -> np.ndarray:
+    return np.array([[i, i + 1] for i in range(J - 1)], dtype=np.int32).reshape(-1, 2)
+
+
+def star_edges(L: int) -> np.ndarray:
+    """Centre node 0 joined to leaves 1..L."""
+    return np.array([[0, l] for l in range(1, L + 1)], dtype=np.int32).reshape(-1, 2)
+
+
+def pruefer_decode(seq) -> np.ndarray:
+    """Tree on labels 0..len(seq)+1 encoded by a Pruefer sequence (standard decoding)."""
+    import heapq
+
+    seq = [int(s) for s in seq]
+    J = len(seq) + 2
+    degree = [1] * J
+    for s in seq:
+        degree[s] += 1
+    heap = [v for v in range(J) if degree[v] == 1]
+    heapq.heapify(heap)
+    edges = []
+    for s in seq:
+        leaf = heapq.heappop(heap)
+        edges.append((leaf, s))
+        degree[leaf] -= 1
+        degree[s] -= 1
+        if degree[s] == 1:
+            heapq.heappush(heap, s)
+    u = heapq.heappop(heap)
+    v = heapq.heappop(heap)
+    edges.append((u, v))
+    return np.array(edges, dtype=np.int32)
+
+
+def pruefer_tree_with_leaves(J: int, num_leaves: int, rng) -> np.ndarray:
+    """Random tree on J labels with exactly ``num_leaves`` leaves.
+
+    A label is a leaf iff it is absent from the Pruefer sequence, so the
+    sequence (length J-2) holds every one of the J-num_leaves interior labels
+    at least once, plus uniform draws from the interior set, shuffled.
+    """
+    if not (2 <= num_leaves <= J - 1) and J > 2:
+        raise ValueError("num_leaves out of range")
+    interior = rng.choice(J, size=J - num_leaves, replace=False)
+    extra = rng.choice(interior, size=(J - 2) - (J - num_leaves), replace=True)
+    seq = np.concatenate([interior, extra])
+    rng.shuffle(seq)
+    return pruefer_decode(seq)
+
+
+def uniform_pruefer_tree(J: int, rng) -> np.ndarray:
+    if J == 2:
+        return np.array([[0, 1]], dtype=np.int32)
+    return pruefer_decode(rng.integers(0, J, size=J - 2))
+
+
+def leaves_of(J: int, edges: np.ndarray) -> np.ndarray:
+    deg = np.bincount(edges.reshape(-1), minlength=J)
+    return deg == 1
+
+
+# --------------------------------------------------------------------------
+# supports and marginals
+# --------------------------------------------------------------------------
+
+def grid_1d(n: int) -> np.ndarray:
+    """x_i = i/(n-1), i = 0..n-1 (endpoints included), float32 [n, 1]."""
+    return (np.arange(n, dtype=np.float64) / (n - 1)).astype(np.float32).reshape(n, 1)
+
+
+def grid_2d(side: int) -> np.ndarray:
+    """Tensor grid (i/(side-1), j/(side-1)), row-major in (i, j), float32 [side^2, 2]."""
+    t = np.arange(side, dtype=np.float64) / (side - 1)
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    return np.stack([X.reshape(-1), Y.reshape(-1)], axis=1).astype(np.float32)
+
+
+def gaussian_mixture(points: np.ndarray, rng, n_comp: int,
+                     sigma_range=(0.05, 0.15), mean_range=(0.15, 0.85)) -> np.ndarray:
+    """Isotropic Gaussian-mixture density at the support points, normalised (FP64)."""
+    P = np.asarray(points, dtype=np.float64)
+    D = P.shape[1]
+    w = rng.dirichlet(np.ones(n_comp))
+    means = rng.uniform(mean_range[0], mean_range[1], size=(n_comp, D))
+    sig = rng.uniform(sigma_range[0], sigma_range[1], size=n_comp)
+    dens = np.zeros(P.shape[0])
+    for c in range(n_comp):
+        r2 = np.sum((P - means[c]) ** 2, axis=1)
+        dens += w[c] * np.exp(-r2 / (2.0 * sig[c] ** 2)) / (2.0 * np.pi * sig[c] ** 2) ** (D / 2.0)
+    return dens / dens.sum()
+
+
+def dirichlet_marginal(n: int, rng) -> np.ndarray:
+    mu = rng.dirichlet(np.ones(n))
+    return mu / mu.sum()
+
+
+def _check_fixed_leaves(J, edges, fixed):
+    deg = np.bincount(edges.reshape(-1), minlength=J)
+    assert all(deg[j] == 1 for j in range(J) if fixed[j])
+
+
+# --------------------------------------------------------------------------
+# the workloads
+# --------------------------------------------------------------------------
+
+def chain_problem(seed: int = 1000, J: int = 5, n: int = 64, eps: float = 0.01,
+                  n_comp: int = 2, cost_kind: str = COST_DENSE) -> TreeProblem:
+    """Chain 0-1-...-(J-1); ends fixed with mixtures on the grid i/(n-1); C=|x-y|^2."""
+    rng = np.random.default_rng(seed)
+    edges = chain_edges(J)
+    x = grid_1d(n)
+    fixed = np.zeros(J, dtype=bool)
+    fixed[0] = fixed[J - 1] = True
+    marg = {0: gaussian_mixture(x, rng, n_comp), J - 1: gaussian_mixture(x, rng, n_comp)}
+    return TreeProblem(name=f"chain{J}_n{n}", edges=edges, n=np.full(J, n, np.int32), fixed=fixed,
+                       marginals=marg, eps=eps, coords=[x] * J, cost_scale=1.0, cost_kind=cost_kind,
+                       meta={"seed": seed})
+
+
+def star_problem(seed: int = 2000, leaves: int = 8, side: int = 32, eps: float = 0.005,
+                 n_comp: int = 3, cost_kind: str = COST_SQEUCLID) -> TreeProblem:
+    """Barycenter star: centre 0 (free), leaves 1..L fixed, all on the side x side grid.
+
+    The squared-Euclidean cost is normalised to max 1 on [0,1]^2 (scale 1/2).
+    """
+    rng = np.random.default_rng(seed)
+    edges = star_edges(leaves)
+    x = grid_2d(side)
+    J = leaves + 1
+    fixed = np.ones(J, dtype=bool)
+    fixed[0] = False
+    marg = {l: gaussian_mixture(x, rng, n_comp) for l in range(1, J)}
+    return TreeProblem(name=f"star{leaves}_grid{side}", edges=edges, n=np.full(J, side * side, np.int32),
+                       fixed=fixed, marginals=marg, eps=eps, coords=[x] * J, cost_scale=0.5,
+                       cost_kind=cost_kind, meta={"seed": seed})
+
+
+def prufer_problem(seed: int = 3000, J: int = 64, n: int = 4096, num_leaves: int = 32, D: int = 3,
+                   eps: float = 0.01, cost_kind: str = COST_DENSE) -> TreeProblem:
+    """Random Pruefer tree with exactly ``num_leaves`` fixed leaves; points U[0,1]^D."""
+    rng = np.random.default_rng(seed)
+    edges = pruefer_tree_with_leaves(J, num_leaves, rng)
+    fixed = leaves_of(J, edges)
+    coords = [rng.random((n, D)).astype(np.float32) for _ in range(J)]
+    marg = {j: dirichlet_marginal(n, rng) for j in range(J) if fixed[j]}
+    _check_fixed_leaves(J, edges, fixed)
+    return TreeProblem(name=f"prufer{J}_n{n}", edges=edges, n=np.full(J, n, np.int32), fixed=fixed,
+                       marginals=marg, eps=eps, coords=coords, cost_scale=1.0, cost_kind=cost_kind,
+                       meta={"seed": seed})
+
+
+def random_tree_problem(rng, J: int, n_range=(128, 2048), eps_range=(0.002, 0.05), D: int = 2,
+                        name: str = "tree") -> TreeProblem:
+    """One tree of the batched workload: uniform Pruefer tree, leaves fixed (1-3 comp mixtures)."""
+    edges = uniform_pruefer_tree(J, rng)
+    fixed = leaves_of(J, edges)
+    n = rng.integers(n_range[0], n_range[1] + 1, size=J).astype(np.int32)
+    coords = [rng.random((int(n[j]), D)).astype(np.float32) for j in range(J)]
+    eps = float(np.exp(rng.uniform(np.log(eps_range[0]), np.log(eps_range[1]))))
+    marg = {}
+    for j in range(J):
+        if fixed[j]:
+            marg[j] = gaussian_mixture(coords[j], rng, int(rng.integers(1, 4)))
+    _check_fixed_leaves(J, edges, fixed)
+    return TreeProblem(name=name, edges=edges, n=n, fixed=fixed, marginals=marg, eps=eps, coords=coords,
+                       cost_scale=1.0, cost_kind=COST_SQEUCLID, meta={})
+
+
+def batched_problems(seed: int = 4000, num_trees: int = 512, J_range=(4, 32), n_range=(128, 2048),
+                     eps_range=(0.002, 0.05)) -> List[TreeProblem]:
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(num_trees):
+        J = int(rng.integers(J_range[0], J_range[1] + 1))
+        out.append(random_tree_problem(rng, J, n_range, eps_range, name=f"batch{i}_J{J}"))
+    return out
+
+
+WORKLOADS = {
+    "chain5_n64_eps0.01": "chain_problem",
+    "star8_grid32_eps0.005": "star_problem",
+    "prufer64_n4096_dense": "prufer_problem",
+    "batched512_trees": "batched_problems",
+    "star8_warmstart": "star_problem",
+}
