@@ -1,0 +1,366 @@
+"""Benchmark: edge-kernel applies per second of the bipartite scaling sweep.
+
+Workload (default): a 64-node random tree (Pruefer sequence, exactly 32 fixed
+leaves), n = 4096 support points per node drawn uniformly in [0,1]^3, a stored
+dense FP32 cost per edge (63 edges, 4.2 GB on the device), Dirichlet(1) leaf
+marginals, eps = 0.01.  One step = one half-step of the sweep: the edge-apply
+launch (every edge's Gibbs kernel applied once toward the active colour, in
+log-sum-exp form, reading all 4.2 GB) followed by the node-update launch
+(Theorem 1 updates + stopping terms).  63 edge applies per step.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "edge-kernel applies/sec"
+UNIT = "edge_applies/s"
+WORKLOAD = "prufer64_n4096_dense_fp32_eps0.01"
+
+
+def workload_problem():
+    import gen
+    return gen.prufer_problem(seed=3000, J=64, n=4096, num_leaves=32, D=3, eps=0.01)
+
+
+def algorithmic_bytes(p) -> int:
+    """Bytes one apply launch must move: each stored cost entry once (4 B) plus
+    the two-float operand of the reduction side and the output of the active side
+    (8 B per support point on each side of every edge)."""
+    tot = 0
+    for a, b in np.asarray(p.edges):
+        na, nb = int(p.n[a]), int(p.n[b])
+        tot += 4 * na * nb + 8 * (na + nb)
+    return tot
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("apply_f32.cu", "ptx.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2406_10849_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per apply launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "apply_f32_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") == kernel_hash() and d.get("workload") == workload:
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return out
+
+
+def cpu_baseline(p, budget_s: float = 12.0, max_applies: int = 16):
+    """FP64 oracle on a bounded sample: edge applies (messages) of half-step 1,
+    timed on the host cores, as it stands."""
+    from oracle import tree_ot as O
+    colour = O.bipartition(p.num_nodes, p.edges)
+    f = O.zero_potentials(p)
+    nb = O.neighbours(p.num_nodes, p.edges)
+    active = [(j, k) for j in range(p.num_nodes) if colour[j] == 0 for k in nb[j]]
+    # build the sampled costs outside the timed loop (the oracle reads them as problem data)
+    done = 0
+    t_total = 0.0
+    for (j, k) in active[:max_applies]:
+        O.cost(p, j, k)  # materialise the FP32 matrix (input), not timed
+        t0 = time.perf_counter()
+        O.message(p, f, j, k)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if t_total >= budget_s:
+            break
+    return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of 63 edge applies of half-step 1 (FP64 numpy log-sum-exp over 4096x4096), "
+                      f"{t_total:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each step is a bounded sample of
+    one edge apply of the workload (REF_ROWS of its 4096 output rows, FP64 numpy
+    log-sum-exp over all 4096 columns); the value is scaled to whole edge applies."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    REF_ROWS = 512
+    p = workload_problem()
+    steps, warm = args.steps, args.warmup
+    from oracle import tree_ot as O
+    colour = O.bipartition(p.num_nodes, p.edges)
+    f = O.zero_potentials(p)
+    nb = O.neighbours(p.num_nodes, p.edges)
+    active = [(j, k) for j in range(p.num_nodes) if colour[j] == 0 for k in nb[j]]
+    for j, k in active[:4]:
+        O.cost(p, j, k)  # the stored FP32 matrices are problem data, built before timing
+    def step(i):
+        j, k = active[i % 4]
+        r0 = (i * REF_ROWS) % int(p.n[j])
+        O.message(p, f, j, k, rows=np.arange(r0, r0 + REF_ROWS))
+    for i in range(warm):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        step(warm + i)
+    dt = time.perf_counter() - t0
+    frac = REF_ROWS / 4096.0
+    value = steps * frac / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD,
+                   "step": f"{REF_ROWS} of 4096 rows of one edge apply (FP64 numpy oracle, host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} x {REF_ROWS} rows of half-step-1 edge applies, 4096 columns each"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-converge", action="store_true", help="skip the time-to-1e-6 solve")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    p = workload_problem()
+    costs = [gen.sqeuclid_cost_f32_torch(p.coords[a], p.coords[b], 1.0, dev) for a, b in p.edges]
+    torch.cuda.synchronize(dev)
+    solver = T.Solver([p], T.options(precision="fp32"), stream=stream, device_costs=[costs])
+    stats = solver.plan_stats()
+    n_apply = p.num_edges
+
+    # warm-up
+    for i in range(args.warmup):
+        c = i % 2
+        solver.apply(c)
+        solver.node_update(c)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev_a0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_a1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    c0 = args.warmup % 2
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for i in range(K):
+            c = (c0 + i) % 2
+            ev_a0[i].record(stream)
+            solver.apply(c)
+            ev_a1[i].record(stream)
+            solver.node_update(c)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+    clocks = clk.summary()
+    elapsed_ms = start.elapsed_time(stop)
+    apply_ms = [ev_a0[i].elapsed_time(ev_a1[i]) for i in range(K)]
+    t_max = elapsed_ms
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n_apply * K / (t_max / 1e3)
+
+    apply_avg_ms = statistics.mean(apply_ms)
+    alg = algorithmic_bytes(p)
+    peak, peak_kind = read_peaks()
+    achieved = alg / (apply_avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(WORKLOAD), "peak_kind": f"hbm_gbs of {peak_kind}",
+                "kernel": "apply_f32_kernel", "apply_ms_avg": apply_avg_ms,
+                "apply_ms_median": statistics.median(apply_ms), "algorithmic_bytes_per_launch": alg}
+
+    extra = {}
+    if rank == 0 and not args.no_converge:
+        # plain FP32 sweep from u = 1 to max marginal L1 <= 1e-6 (the solver's own check)
+        s2 = T.Solver([p], T.options(precision="fp32", tol=1e-6, tol_kind="max", max_half_steps=20000),
+                      stream=stream, device_costs=[costs])
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, res = s2.solve()
+        dt = time.perf_counter() - t0
+        s2.close()
+        extra["time_to_1e-6"] = {"plain_fp32_s": dt, "half_steps": res[0]["half_steps"],
+                                 "max_marginal_l1": res[0]["max_marginal_l1"], "status": rc}
+    solver.close()
+
+    e2e = None
+    if not args.no_e2e:
+        # the same metric through the public API with host inputs: create (host->device copy
+        # of costs, coordinates and marginals), the K half-steps, the FP64 check (device->host)
+        host_costs = [torch.empty(c.shape, dtype=torch.float32, pin_memory=True) for c in costs]
+        for hc, c in zip(host_costs, costs):
+            hc.copy_(c)
+        del costs
+        torch.cuda.empty_cache()
+        hp = gen.prufer_problem(seed=3000, J=64, n=4096, num_leaves=32, D=3, eps=0.01)
+        hp.dense_costs = [hc.numpy() for hc in host_costs]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s3 = T.Solver([hp], T.options(precision="fp32"), stream=stream)
+        s3.half_steps(K)
+        s3.check()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        s3.close()
+        t_e2e = dt
+        if dist is not None:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = sum(int(hc.numel()) * 4 for hc in host_costs) + sum(int(c.size) * 4 for c in hp.coords) + \
+            sum(int(m.size) * 8 for m in hp.marginals.values())
+        d2h = 16 * int(sum(int(hp.n[a]) + int(hp.n[c]) for a, c in hp.edges))  # marginals + potentials
+        e2e = {"value": world * n_apply * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
+               "d2h_bytes_per_step": d2h // K,
+               "note": f"one public-API solve of {K} half-steps from pinned host buffers per run"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu else cpu_baseline(p)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": 64, "edges": 63, "n": 4096, "dim": 3, "eps": 0.01,
+                   "cost": "stored dense FP32, 4.2 GB", "step": "one half-step (apply + node update)",
+                   "l2": "inputs (4.2 GB) exceed L2", "elements_per_step": stats["elements_per_half_step"]},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * K,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,996 @@
+// C ABI of the tree solver: validation, two-colouring, device plan, the solve
+// loop (CUDA-graph chunks of half-steps with device-side retirement), and the
+// host side of the final check.  See include/tree_ot.h for the contract.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tree_ot.h"
+#include "internal.h"
+
+using namespace treeot;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TREE_OT_ERR_OOM : TREE_OT_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// host-only checks (Sec. 3 assumptions)
+// ---------------------------------------------------------------------------
+
+int check_tree(int32_t J, const int32_t* edges, std::vector<std::vector<int32_t>>* adj_out) {
+  if (J < 2) return fail(TREE_OT_ERR_NOT_TREE, "a tree needs at least two nodes");
+  if (!edges) return fail(TREE_OT_ERR_ARG, "edges is NULL");
+  std::vector<std::vector<int32_t>> adj(J);
+  for (int32_t e = 0; e < J - 1; ++e) {
+    const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+    if (a < 0 || b < 0 || a >= J || b >= J || a == b)
+      return fail(TREE_OT_ERR_NOT_TREE, "edge " + std::to_string(e) + " has an invalid endpoint or is a self loop");
+    adj[a].push_back(b);
+    adj[b].push_back(a);
+  }
+  std::vector<uint8_t> seen(J, 0);
+  std::deque<int32_t> q{0};
+  seen[0] = 1;
+  int32_t count = 1;
+  while (!q.empty()) {
+    const int32_t v = q.front();
+    q.pop_front();
+    for (int32_t w : adj[v])
+      if (!seen[w]) {
+        seen[w] = 1;
+        ++count;
+        q.push_back(w);
+      }
+  }
+  // J-1 edges + connected <=> tree (also rules out duplicate edges / cycles)
+  if (count != J) return fail(TREE_OT_ERR_NOT_TREE, "the edges do not connect all nodes (cycle or forest)");
+  if (adj_out) *adj_out = std::move(adj);
+  return TREE_OT_OK;
+}
+
+void colour_tree(int32_t J, const std::vector<std::vector<int32_t>>& adj, uint8_t* colour) {
+  std::vector<int8_t> c(J, -1);
+  c[0] = 0;
+  std::deque<int32_t> q{0};
+  while (!q.empty()) {
+    const int32_t v = q.front();
+    q.pop_front();
+    for (int32_t w : adj[v])
+      if (c[w] < 0) {
+        c[w] = (int8_t)(1 - c[v]);
+        q.push_back(w);
+      }
+  }
+  for (int32_t j = 0; j < J; ++j) colour[j] = (uint8_t)c[j];
+}
+
+int validate_problem(const tree_ot_problem* p, std::vector<std::vector<int32_t>>* adj_out) {
+  if (!p) return fail(TREE_OT_ERR_ARG, "problem is NULL");
+  if (!p->support_size || !p->is_fixed) return fail(TREE_OT_ERR_ARG, "support_size / is_fixed is NULL");
+  std::vector<std::vector<int32_t>> adj;
+  int rc = check_tree(p->num_nodes, p->edges, &adj);
+  if (rc) return rc;
+  const int32_t J = p->num_nodes;
+  for (int32_t j = 0; j < J; ++j)
+    if (p->support_size[j] < 1) return fail(TREE_OT_ERR_ARG, "support size of node " + std::to_string(j) + " < 1");
+  if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(TREE_OT_ERR_EPS, "eps must be positive and finite");
+  for (int32_t j = 0; j < J; ++j) {
+    if (!p->is_fixed[j]) continue;
+    if (adj[j].size() != 1) return fail(TREE_OT_ERR_FIXED_NOT_LEAF, "fixed node " + std::to_string(j) + " is not a leaf");
+    if (p->is_fixed[adj[j][0]])
+      return fail(TREE_OT_ERR_FIXED_ADJACENT,
+                  "edge joins fixed nodes " + std::to_string(j) + " and " + std::to_string(adj[j][0]));
+    if (!p->marginal || !p->marginal[j]) return fail(TREE_OT_ERR_ARG, "marginal of fixed node " + std::to_string(j) + " is NULL");
+    double s = 0.0;
+    for (int32_t x = 0; x < p->support_size[j]; ++x) {
+      const double v = p->marginal[j][x];
+      if (!(v >= 0.0) || !std::isfinite(v))
+        return fail(TREE_OT_ERR_MARGINAL, "marginal of node " + std::to_string(j) + " has a negative or non-finite entry");
+      s += v;
+    }
+    if (std::fabs(s - 1.0) > 1e-9)
+      return fail(TREE_OT_ERR_MARGINAL, "marginal of node " + std::to_string(j) + " does not sum to 1");
+  }
+  if (p->cost_kind == TREE_OT_COST_SQEUCLID) {
+    if (p->dim < 1 || p->dim > 3) return fail(TREE_OT_ERR_ARG, "dim must be 1..3 for the squared-Euclidean cost");
+    if (!p->coords) return fail(TREE_OT_ERR_ARG, "coords is NULL");
+    for (int32_t j = 0; j < J; ++j)
+      if (!p->coords[j]) return fail(TREE_OT_ERR_ARG, "coords of node " + std::to_string(j) + " is NULL");
+    if (!(p->cost_scale > 0.0) || !std::isfinite(p->cost_scale)) return fail(TREE_OT_ERR_ARG, "cost_scale must be > 0");
+    if (!(p->flags & TREE_OT_INPUT_DEVICE)) {
+      for (int32_t j = 0; j < J; ++j)
+        for (int64_t i = 0; i < (int64_t)p->support_size[j] * p->dim; ++i)
+          if (!std::isfinite(p->coords[j][i]))
+            return fail(TREE_OT_ERR_NONFINITE, "coordinates of node " + std::to_string(j) + " are not finite");
+    }
+  } else if (p->cost_kind == TREE_OT_COST_DENSE_F32) {
+    if (!p->dense_cost) return fail(TREE_OT_ERR_ARG, "dense_cost is NULL");
+    for (int32_t e = 0; e < J - 1; ++e)
+      if (!p->dense_cost[e]) return fail(TREE_OT_ERR_ARG, "dense cost of edge " + std::to_string(e) + " is NULL");
+    if (p->coords && (p->dim < 0 || p->dim > 3)) return fail(TREE_OT_ERR_ARG, "dim must be 0..3");
+  } else {
+    return fail(TREE_OT_ERR_ARG, "unknown cost_kind");
+  }
+  if (adj_out) *adj_out = std::move(adj);
+  return TREE_OT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+
+struct tree_ot_handle {
+  tree_ot_options opt{};
+  bool fp64 = false;
+  int nprob = 0;
+  std::vector<ProbD> probs;
+  std::vector<NodeD> nodes;
+  std::vector<EdgeD> edges;
+  std::vector<DEdgeD> dedges;
+  std::vector<int32_t> node_dedges;
+  std::vector<Task> tasks[2];
+  std::vector<NodeChunk> chunks[2];
+  std::vector<Task> check_tasks;
+  std::vector<int32_t> prob_node_base, prob_edge_base, prob_nodes;
+  std::vector<std::vector<double>> mu;  // per global node (fixed nodes), host copy
+  int64_t vec_len = 0, node_len = 0, part_len = 0, coord_len = 0;
+  int32_t nzchunks = 0;
+  int64_t elems = 0, matrix_bytes = 0, device_bytes = 0;
+
+  ProbD* d_probs = nullptr;
+  NodeD* d_nodes = nullptr;
+  EdgeD* d_edges = nullptr;
+  DEdgeD* d_dedges = nullptr;
+  int32_t* d_node_dedges = nullptr;
+  Task* d_tasks[2] = {nullptr, nullptr};
+  NodeChunk* d_chunks[2] = {nullptr, nullptr};
+  Task* d_check_tasks = nullptr;
+  double *d_f = nullptr, *d_m = nullptr, *d_Z = nullptr, *d_rho = nullptr, *d_logg = nullptr, *d_mu = nullptr;
+  double *d_resid_acc = nullptr, *d_resid_dedge = nullptr, *d_res_sum = nullptr, *d_marg = nullptr;
+  double *d_edge_tc = nullptr, *d_edge_mass = nullptr;
+  float *d_hh = nullptr, *d_hl = nullptr, *d_ah = nullptr, *d_al = nullptr, *d_coords = nullptr;
+  float2* d_part32 = nullptr;
+  double2* d_part64 = nullptr;
+  double2* d_zpart = nullptr;
+  unsigned long long* d_res_max = nullptr;
+  int32_t *d_done = nullptr, *d_node_arrive = nullptr, *d_node_count = nullptr, *d_launch_count = nullptr;
+  int32_t *d_err = nullptr, *d_scan = nullptr;
+  int64_t *d_done_at = nullptr, *d_hs = nullptr;
+  std::vector<void*> owned;
+
+  int64_t hs_host = 0;
+  cudaStream_t hstream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  int apply_grid = 1;
+
+  bool have_check = false;
+  std::vector<double> h_marg, h_f, h_Z, h_rho, h_tc, h_mass;
+  std::vector<int32_t> h_done;
+  std::vector<int64_t> h_done_at;
+  double last_wall_ms = 0.0;
+  std::vector<int32_t> last_status;
+
+  template <class T>
+  int alloc(T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    const size_t bytes = sizeof(T) * (size_t)count;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    owned.push_back(*p);
+    device_bytes += (int64_t)bytes;
+    return TREE_OT_OK;
+  }
+};
+
+namespace {
+
+#define RC_TRY(call)      \
+  do {                    \
+    int rc_ = (call);     \
+    if (rc_) return rc_;  \
+  } while (0)
+
+ApplyArgs apply_args(tree_ot_handle* h, int colour) {
+  ApplyArgs a{};
+  a.tasks = h->d_tasks[colour];
+  a.ntasks = (int32_t)h->tasks[colour].size();
+  a.dedges = h->d_dedges;
+  a.edges = h->d_edges;
+  a.nodes = h->d_nodes;
+  a.probs = h->d_probs;
+  a.done = h->d_done;
+  a.m = h->d_m;
+  a.hh = h->d_hh;
+  a.hl = h->d_hl;
+  a.f = h->d_f;
+  a.logg = h->d_logg;
+  a.coords = h->d_coords;
+  a.part32 = h->d_part32;
+  a.part64 = h->d_part64;
+  return a;
+}
+
+NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
+  NodeArgs a{};
+  a.chunks = h->d_chunks[colour];
+  a.nchunks = (int32_t)h->chunks[colour].size();
+  a.colour = colour;
+  a.nodes = h->d_nodes;
+  a.dedges = h->d_dedges;
+  a.node_dedges = h->d_node_dedges;
+  a.probs = h->d_probs;
+  a.nprob = h->nprob;
+  a.done = h->d_done;
+  a.done_at = h->d_done_at;
+  a.f = h->d_f;
+  a.m = h->d_m;
+  a.hh = h->d_hh;
+  a.hl = h->d_hl;
+  a.Z = h->d_Z;
+  a.rho = h->d_rho;
+  a.part32 = h->d_part32;
+  a.part64 = h->d_part64;
+  a.logg = h->d_logg;
+  a.mu = h->d_mu;
+  a.zpart = h->d_zpart;
+  a.resid_acc = h->d_resid_acc;
+  a.resid_dedge = h->d_resid_dedge;
+  a.res_sum = h->d_res_sum;
+  a.res_max = h->d_res_max;
+  a.node_arrive = h->d_node_arrive;
+  a.node_count = h->d_node_count;
+  a.launch_count = h->d_launch_count;
+  a.hs = h->d_hs;
+  a.err = h->d_err;
+  a.tol = h->opt.tol;
+  a.tol_kind = h->opt.tol_kind;
+  a.retire = retire ? 1 : 0;
+  return a;
+}
+
+int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
+  ApplyArgs a = apply_args(h, colour);
+  const int grid = std::max(1, std::min<int>(a.ntasks, h->apply_grid));
+  cudaError_t e = h->fp64 ? launch_apply_f64(a, grid, s) : launch_apply_f32(a, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+  return TREE_OT_OK;
+}
+
+int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
+  cudaError_t e = launch_node_update(node_args(h, colour, retire), h->fp64, s);
+  if (e != cudaSuccess) return cuda_fail(e, "node update launch");
+  return TREE_OT_OK;
+}
+
+int queue_half_steps(tree_ot_handle* h, int64_t T, bool retire, cudaStream_t s) {
+  for (int64_t i = 0; i < T; ++i) {
+    const int colour = (int)(h->hs_host % 2);
+    RC_TRY(launch_apply(h, colour, s));
+    RC_TRY(launch_update(h, colour, retire, s));
+    ++h->hs_host;
+  }
+  return TREE_OT_OK;
+}
+
+int reset_state(tree_ot_handle* h, cudaStream_t s) {
+  CUDA_TRY(cudaMemsetAsync(h->d_f, 0, sizeof(double) * h->vec_len, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_m, 0, sizeof(double) * h->vec_len, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_Z, 0, sizeof(double) * h->nodes.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_rho, 0, sizeof(double) * h->nodes.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_resid_acc, 0, sizeof(double) * h->dedges.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_resid_dedge, 0, sizeof(double) * h->dedges.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_res_sum, 0, sizeof(double) * kResidRing * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_res_max, 0, sizeof(unsigned long long) * kResidRing * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_done, 0, sizeof(int32_t) * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_done_at, 0, sizeof(int64_t) * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_node_arrive, 0, sizeof(int32_t) * h->nodes.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_node_count, 0, sizeof(int32_t) * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_launch_count, 0, sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_hs, 0, sizeof(int64_t), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), s));
+  // apply operand of u = 1: h = log gamma * log2(e)
+  CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, (int32_t)h->dedges.size(),
+                          kLog2e, h->d_hh, h->d_hl, s));
+  h->hs_host = 0;
+  h->have_check = false;
+  return TREE_OT_OK;
+}
+
+int build_graph(tree_ot_handle* h, int len) {
+  if (h->graph && h->graph_len == len) return TREE_OT_OK;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  CUDA_TRY(cudaStreamBeginCapture(h->hstream, cudaStreamCaptureModeThreadLocal));
+  const int64_t saved = h->hs_host;
+  h->hs_host = 0;
+  int rc = queue_half_steps(h, len, true, h->hstream);
+  h->hs_host = saved;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->hstream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  h->graph_len = len;
+  return TREE_OT_OK;
+}
+
+int run_check(tree_ot_handle* h, cudaStream_t s) {
+  const int32_t nd = (int32_t)h->dedges.size();
+  CUDA_TRY(launch_operand(h->d_f, h->d_Z, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, nd, 1.0, h->d_ah, h->d_al,
+                          s));
+  CUDA_TRY(cudaMemsetAsync(h->d_edge_tc, 0, sizeof(double) * h->edges.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_edge_mass, 0, sizeof(double) * h->edges.size(), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_marg, 0, sizeof(double) * h->vec_len, s));
+  CheckArgs c{};
+  c.tasks = h->d_check_tasks;
+  c.ntasks = (int32_t)h->check_tasks.size();
+  c.dedges = h->d_dedges;
+  c.edges = h->d_edges;
+  c.nodes = h->d_nodes;
+  c.probs = h->d_probs;
+  c.ah = h->d_ah;
+  c.al = h->d_al;
+  c.coords = h->d_coords;
+  c.marg = h->d_marg;
+  c.edge_tc = h->d_edge_tc;
+  c.edge_mass = h->d_edge_mass;
+  CUDA_TRY(launch_check(c, s));
+  h->h_marg.resize(h->vec_len);
+  h->h_f.resize(h->vec_len);
+  h->h_Z.resize(h->nodes.size());
+  h->h_rho.resize(h->nodes.size());
+  h->h_tc.resize(h->edges.size());
+  h->h_mass.resize(h->edges.size());
+  CUDA_TRY(cudaMemcpyAsync(h->h_marg.data(), h->d_marg, sizeof(double) * h->vec_len, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(h->h_f.data(), h->d_f, sizeof(double) * h->vec_len, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(h->h_Z.data(), h->d_Z, sizeof(double) * h->nodes.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(h->h_rho.data(), h->d_rho, sizeof(double) * h->nodes.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(h->h_tc.data(), h->d_edge_tc, sizeof(double) * h->edges.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(
+      cudaMemcpyAsync(h->h_mass.data(), h->d_edge_mass, sizeof(double) * h->edges.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->have_check = true;
+  return TREE_OT_OK;
+}
+
+// potential of a directed edge from the stored normalised form: f = f' - eps Z_owner
+inline double true_f(const tree_ot_handle* h, const DEdgeD& d, int32_t x) {
+  return h->h_f[d.off + x] - h->probs[d.prob].eps * h->h_Z[d.owner];
+}
+
+void fill_results(tree_ot_handle* h, tree_ot_result* res) {
+  for (int p = 0; p < h->nprob; ++p) {
+    tree_ot_result r{};
+    const ProbD& P = h->probs[p];
+    double rsum = 0.0, rmax = 0.0, tc = 0.0, pr = 0.0, du = 0.0, mass_total = 0.0;
+    const int32_t nb = h->prob_node_base[p], J = h->prob_nodes[p];
+    for (int32_t jj = 0; jj < J; ++jj) {
+      const int32_t j = nb + jj;
+      const NodeD& nd = h->nodes[j];
+      if (nd.fixed) {
+        const DEdgeD& d = h->dedges[h->node_dedges[nd.dedge_begin]];
+        double t = 0.0;
+        for (int32_t x = 0; x < nd.n; ++x) t += std::fabs(h->h_marg[d.off + x] - h->mu[j][x]);
+        rsum += t;
+        rmax = std::max(rmax, t);
+        for (int32_t x = 0; x < nd.n; ++x)
+          if (h->mu[j][x] > 0.0) du += true_f(h, d, x) * h->mu[j][x];
+      } else {
+        std::vector<double> qbar(nd.n, 0.0);
+        for (int32_t i = 0; i < nd.deg; ++i) {
+          const DEdgeD& d = h->dedges[h->node_dedges[nd.dedge_begin + i]];
+          for (int32_t x = 0; x < nd.n; ++x) qbar[x] += h->h_marg[d.off + x] / nd.deg;
+        }
+        double fsum = 0.0;
+        for (int32_t i = 0; i < nd.deg; ++i) {
+          const DEdgeD& d = h->dedges[h->node_dedges[nd.dedge_begin + i]];
+          double t = 0.0;
+          for (int32_t x = 0; x < nd.n; ++x) {
+            t += std::fabs(h->h_marg[d.off + x] - qbar[x]);
+            fsum += true_f(h, d, x);
+          }
+          rsum += t;
+          rmax = std::max(rmax, t);
+        }
+        du += fsum / nd.n;  // eps * rho_j, rho_j = (1/eps) mean_x sum_k f_(j,k)(x)
+      }
+    }
+    const int32_t eb = h->prob_edge_base[p];
+    for (int32_t ee = 0; ee < J - 1; ++ee) {
+      const int32_t e = eb + ee;
+      tc += h->h_tc[e];
+      mass_total += h->h_mass[e];
+      for (int k = 0; k < 2; ++k) {
+        const DEdgeD& d = h->dedges[2 * e + k];
+        const int32_t n = h->nodes[d.owner].n;
+        for (int32_t x = 0; x < n; ++x) {
+          const double q = h->h_marg[d.off + x];
+          if (q > 0.0) pr += true_f(h, d, x) * q;
+        }
+      }
+    }
+    pr -= P.eps * mass_total;
+    du -= P.eps * mass_total;
+    r.residual_sum_l1 = rsum;
+    r.max_marginal_l1 = rmax;
+    r.transport_cost = tc;
+    r.primal = pr;
+    r.dual = du;
+    const bool done = !h->h_done.empty() && h->h_done[p];
+    r.half_steps = done ? h->h_done_at[p] : h->hs_host;
+    r.status = (h->last_status.empty() ? TREE_OT_OK : h->last_status[p]);
+    r.wall_ms = h->last_wall_ms;
+    res[p] = r;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported entry points
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void tree_ot_default_options(tree_ot_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = TREE_OT_PREC_FP32;
+  opt->apply_mode = TREE_OT_APPLY_AUTO;
+  opt->tol = 1e-6;
+  opt->tol_kind = TREE_OT_TOL_SUM;
+  opt->max_half_steps = 100000;
+  opt->check_every = 32;
+  opt->use_graph = 1;
+  opt->flags = 0;
+}
+
+const char* tree_ot_error_string(int code) {
+  switch (code) {
+    case TREE_OT_OK: return "ok";
+    case TREE_OT_NOT_CONVERGED: return "not converged (iteration cap reached)";
+    case TREE_OT_ERR_ARG: return "invalid argument";
+    case TREE_OT_ERR_NOT_TREE: return "edges do not form a tree";
+    case TREE_OT_ERR_FIXED_NOT_LEAF: return "fixed node is not a leaf";
+    case TREE_OT_ERR_FIXED_ADJACENT: return "edge joins two fixed nodes";
+    case TREE_OT_ERR_MARGINAL: return "invalid marginal";
+    case TREE_OT_ERR_NONFINITE: return "non-finite input or potential";
+    case TREE_OT_ERR_EPS: return "invalid eps";
+    case TREE_OT_ERR_CUDA: return "CUDA error";
+    case TREE_OT_ERR_OOM: return "out of device memory";
+    case TREE_OT_ERR_TIMEOUT: return "device wait timed out";
+    case TREE_OT_ERR_STATE: return "invalid state";
+    default: return "unknown error";
+  }
+}
+
+const char* tree_ot_last_error(void) { return g_err.c_str(); }
+
+int tree_ot_validate(const tree_ot_problem* prob) {
+  g_err.clear();
+  return validate_problem(prob, nullptr);
+}
+
+int tree_ot_bipartition(int32_t num_nodes, const int32_t* edges, uint8_t* colour_out) {
+  g_err.clear();
+  if (!colour_out) return fail(TREE_OT_ERR_ARG, "colour_out is NULL");
+  std::vector<std::vector<int32_t>> adj;
+  int rc = check_tree(num_nodes, edges, &adj);
+  if (rc) return rc;
+  colour_tree(num_nodes, adj, colour_out);
+  return TREE_OT_OK;
+}
+
+int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_ot_options* opt, void* cuda_stream,
+                   tree_ot_handle** out) {
+  g_err.clear();
+  if (!out) return fail(TREE_OT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!probs || num_probs < 1) return fail(TREE_OT_ERR_ARG, "need at least one problem");
+  tree_ot_options o;
+  tree_ot_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != TREE_OT_PREC_FP32 && o.precision != TREE_OT_PREC_FP64)
+    return fail(TREE_OT_ERR_ARG, "unknown precision");
+  if (o.apply_mode != TREE_OT_APPLY_AUTO && o.apply_mode != TREE_OT_APPLY_LSE)
+    return fail(TREE_OT_ERR_ARG, "unknown apply_mode");
+  if (!(o.tol >= 0.0) || o.max_half_steps < 0 || o.check_every < 2 || (o.check_every & 1))
+    return fail(TREE_OT_ERR_ARG, "tol >= 0, max_half_steps >= 0 and an even check_every >= 2 are required");
+  if (o.tol_kind != TREE_OT_TOL_SUM && o.tol_kind != TREE_OT_TOL_MAX) return fail(TREE_OT_ERR_ARG, "unknown tol_kind");
+  std::vector<std::vector<std::vector<int32_t>>> adjs(num_probs);
+  for (int32_t p = 0; p < num_probs; ++p) {
+    int rc = validate_problem(&probs[p], &adjs[p]);
+    if (rc) {
+      g_err = "problem " + std::to_string(p) + ": " + g_err;
+      return rc;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  tree_ot_handle* h = new tree_ot_handle();
+  h->opt = o;
+  h->fp64 = o.precision == TREE_OT_PREC_FP64;
+  h->nprob = num_probs;
+  int rc = TREE_OT_OK;
+  auto bail = [&](int code) {
+    tree_ot_destroy(h);
+    return code;
+  };
+
+  // ---- host plan ---------------------------------------------------------
+  int64_t vec_off = 0, node_off = 0, coord_off = 0, part_off = 0;
+  int32_t chunk_base = 0;
+  std::vector<std::vector<int32_t>> owned_by;  // per global node: owned dedges
+  for (int32_t p = 0; p < num_probs; ++p) {
+    const tree_ot_problem& P = probs[p];
+    const int32_t J = P.num_nodes;
+    const int32_t nbase = (int32_t)h->nodes.size();
+    const int32_t ebase = (int32_t)h->edges.size();
+    h->prob_node_base.push_back(nbase);
+    h->prob_edge_base.push_back(ebase);
+    h->prob_nodes.push_back(J);
+    std::vector<uint8_t> col(J);
+    colour_tree(J, adjs[p], col.data());
+    ProbD pd{};
+    pd.eps = P.eps;
+    pd.inv_eps = 1.0 / P.eps;
+    pd.cost_scale = P.cost_kind == TREE_OT_COST_SQEUCLID ? P.cost_scale : 1.0;
+    pd.s2 = (float)(kLog2e / P.eps);
+    pd.s2_scaled = (float)(pd.cost_scale * kLog2e / P.eps);
+    pd.dim = P.cost_kind == TREE_OT_COST_SQEUCLID ? P.dim : (P.coords ? P.dim : 0);
+    pd.cost_kind = P.cost_kind;
+    const bool have_coords = P.coords != nullptr && pd.dim > 0;
+    for (int32_t j = 0; j < J; ++j) {
+      NodeD nd{};
+      nd.n = P.support_size[j];
+      nd.deg = (int32_t)adjs[p][j].size();
+      nd.prob = p;
+      nd.fixed = P.is_fixed[j] ? 1 : 0;
+      nd.colour = col[j];
+      nd.node_off = node_off;
+      node_off += align_up(nd.n, 32);
+      nd.coord_off = have_coords ? coord_off : -1;
+      if (have_coords) coord_off += align_up((int64_t)nd.n * pd.dim, 4);
+      nd.nchunks = (nd.n + kNodeChunk - 1) / kNodeChunk;
+      nd.chunk_base = chunk_base;
+      chunk_base += nd.nchunks;
+      pd.nodes_in_colour[nd.colour] += 1;
+      h->nodes.push_back(nd);
+      owned_by.emplace_back();
+      std::vector<double> mu;
+      if (nd.fixed) mu.assign(P.marginal[j], P.marginal[j] + nd.n);
+      h->mu.push_back(std::move(mu));
+    }
+    h->probs.push_back(pd);
+    for (int32_t e = 0; e < J - 1; ++e) {
+      EdgeD ed{};
+      ed.a = nbase + P.edges[2 * e];
+      ed.b = nbase + P.edges[2 * e + 1];
+      ed.na = h->nodes[ed.a].n;
+      ed.nb = h->nodes[ed.b].n;
+      ed.ld = align_up(ed.nb, 4);
+      ed.C = nullptr;
+      h->edges.push_back(ed);
+      h->elems += (int64_t)ed.na * ed.nb;
+      const int32_t ge = ebase + e;
+      for (int k = 0; k < 2; ++k) {
+        DEdgeD d{};
+        d.owner = k == 0 ? ed.a : ed.b;
+        d.nbr = k == 0 ? ed.b : ed.a;
+        d.edge = ge;
+        d.dir = k;
+        d.prob = p;
+        const int32_t n_own = h->nodes[d.owner].n, n_nbr = h->nodes[d.nbr].n;
+        if (h->fp64)
+          d.nsplit = 1;
+        else if (P.cost_kind == TREE_OT_COST_DENSE_F32)
+          d.nsplit = k == 0 ? (n_nbr + kRowCols - 1) / kRowCols : (n_nbr + kColRows - 1) / kColRows;
+        else
+          d.nsplit = (n_nbr + kRecRed - 1) / kRecRed;
+        d.off = vec_off;
+        vec_off += align_up(n_own, 32);
+        d.part_off = part_off;
+        part_off += (int64_t)d.nsplit * n_own;
+        h->dedges.push_back(d);
+        owned_by[d.owner].push_back(2 * ge + k);
+      }
+      h->dedges[2 * ge].rev_off = h->dedges[2 * ge + 1].off;
+      h->dedges[2 * ge + 1].rev_off = h->dedges[2 * ge].off;
+      if (P.cost_kind == TREE_OT_COST_DENSE_F32) h->matrix_bytes += 4 * (int64_t)ed.na * ed.nb;
+    }
+  }
+  for (size_t j = 0; j < h->nodes.size(); ++j) {
+    h->nodes[j].dedge_begin = (int32_t)h->node_dedges.size();
+    for (int32_t d : owned_by[j]) h->node_dedges.push_back(d);
+  }
+  h->vec_len = vec_off;
+  h->node_len = node_off;
+  h->coord_len = coord_off;
+  h->part_len = part_off;
+  h->nzchunks = chunk_base;
+
+  // apply tasks and node chunks per colour
+  for (size_t di = 0; di < h->dedges.size(); ++di) {
+    const DEdgeD& d = h->dedges[di];
+    const NodeD& own = h->nodes[d.owner];
+    const NodeD& nbn = h->nodes[d.nbr];
+    const ProbD& pd = h->probs[d.prob];
+    std::vector<Task>& tl = h->tasks[own.colour];
+    const bool dense = pd.cost_kind == TREE_OT_COST_DENSE_F32;
+    if (h->fp64) {
+      for (int32_t o0 = 0; o0 < own.n; o0 += 64)
+        tl.push_back(Task{(int32_t)di, dense ? (d.dir == 0 ? TASK_ROW : TASK_COL) : TASK_RECOMP, o0,
+                          std::min(64, own.n - o0), 0, nbn.n, 0, 0});
+    } else if (dense && d.dir == 0) {
+      for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
+        for (int32_t s = 0; s < d.nsplit; ++s)
+          tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
+                            std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
+    } else if (dense) {
+      for (int32_t s = 0; s < d.nsplit; ++s)
+        for (int32_t o0 = 0; o0 < own.n; o0 += kColCols)
+          tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kColCols, own.n - o0), s * kColRows,
+                            std::min(kColRows, nbn.n - s * kColRows), s, 0});
+    } else {
+      for (int32_t o0 = 0; o0 < own.n; o0 += kRecOut)
+        for (int32_t s = 0; s < d.nsplit; ++s)
+          tl.push_back(Task{(int32_t)di, TASK_RECOMP, o0, std::min(kRecOut, own.n - o0), s * kRecRed,
+                            std::min(kRecRed, nbn.n - s * kRecRed), s, 0});
+    }
+  }
+  for (size_t j = 0; j < h->nodes.size(); ++j) {
+    const NodeD& nd = h->nodes[j];
+    for (int32_t c = 0; c < nd.nchunks; ++c)
+      h->chunks[nd.colour].push_back(
+          NodeChunk{(int32_t)j, c, c * kNodeChunk, std::min(kNodeChunk, nd.n - c * kNodeChunk)});
+  }
+  for (size_t e = 0; e < h->edges.size(); ++e) {
+    const EdgeD& ed = h->edges[e];
+    for (int32_t o0 = 0; o0 < ed.na; o0 += 64)
+      h->check_tasks.push_back(Task{(int32_t)(2 * e), TASK_ROW, o0, std::min(64, ed.na - o0), 0, ed.nb, 0, 0});
+    for (int32_t o0 = 0; o0 < ed.nb; o0 += 256)
+      h->check_tasks.push_back(Task{(int32_t)(2 * e + 1), TASK_COL, o0, std::min(256, ed.nb - o0), 0, ed.na, 0, 0});
+  }
+
+  // ---- device memory -----------------------------------------------------
+  const int64_t NN = (int64_t)h->nodes.size(), NE = (int64_t)h->edges.size(), ND = (int64_t)h->dedges.size();
+  if ((rc = h->alloc(&h->d_probs, num_probs)) || (rc = h->alloc(&h->d_nodes, NN)) ||
+      (rc = h->alloc(&h->d_edges, NE)) || (rc = h->alloc(&h->d_dedges, ND)) ||
+      (rc = h->alloc(&h->d_node_dedges, (int64_t)h->node_dedges.size())) ||
+      (rc = h->alloc(&h->d_tasks[0], (int64_t)h->tasks[0].size())) ||
+      (rc = h->alloc(&h->d_tasks[1], (int64_t)h->tasks[1].size())) ||
+      (rc = h->alloc(&h->d_chunks[0], (int64_t)h->chunks[0].size())) ||
+      (rc = h->alloc(&h->d_chunks[1], (int64_t)h->chunks[1].size())) ||
+      (rc = h->alloc(&h->d_check_tasks, (int64_t)h->check_tasks.size())) || (rc = h->alloc(&h->d_f, h->vec_len)) ||
+      (rc = h->alloc(&h->d_m, h->vec_len)) || (rc = h->alloc(&h->d_hh, h->vec_len)) ||
+      (rc = h->alloc(&h->d_hl, h->vec_len)) || (rc = h->alloc(&h->d_ah, h->vec_len)) ||
+      (rc = h->alloc(&h->d_al, h->vec_len)) || (rc = h->alloc(&h->d_marg, h->vec_len)) ||
+      (rc = h->alloc(&h->d_Z, NN)) || (rc = h->alloc(&h->d_rho, NN)) || (rc = h->alloc(&h->d_logg, h->node_len)) ||
+      (rc = h->alloc(&h->d_mu, h->node_len)) || (rc = h->alloc(&h->d_coords, h->coord_len)) ||
+      (rc = h->alloc(&h->d_zpart, h->nzchunks)) || (rc = h->alloc(&h->d_resid_acc, ND)) ||
+      (rc = h->alloc(&h->d_resid_dedge, ND)) || (rc = h->alloc(&h->d_res_sum, (int64_t)kResidRing * num_probs)) ||
+      (rc = h->alloc(&h->d_res_max, (int64_t)kResidRing * num_probs)) || (rc = h->alloc(&h->d_done, num_probs)) ||
+      (rc = h->alloc(&h->d_done_at, num_probs)) || (rc = h->alloc(&h->d_node_arrive, NN)) ||
+      (rc = h->alloc(&h->d_node_count, num_probs)) || (rc = h->alloc(&h->d_launch_count, 1)) ||
+      (rc = h->alloc(&h->d_hs, 1)) || (rc = h->alloc(&h->d_err, 1)) || (rc = h->alloc(&h->d_scan, 1)) ||
+      (rc = h->alloc(&h->d_edge_tc, NE)) || (rc = h->alloc(&h->d_edge_mass, NE)))
+    return bail(rc);
+  if (h->fp64) {
+    if ((rc = h->alloc(&h->d_part64, h->part_len))) return bail(rc);
+  } else {
+    if ((rc = h->alloc(&h->d_part32, h->part_len))) return bail(rc);
+  }
+
+  auto up = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (bytes == 0) return TREE_OT_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? TREE_OT_OK : cuda_fail(e, "cudaMemcpyAsync(upload)");
+  };
+
+  // node vectors: log gamma and mu (FP64)
+  {
+    std::vector<double> lg(h->node_len, 0.0), mu(h->node_len, 0.0);
+    for (size_t j = 0; j < h->nodes.size(); ++j) {
+      const NodeD& nd = h->nodes[j];
+      if (!nd.fixed) continue;
+      for (int32_t x = 0; x < nd.n; ++x) {
+        const double v = h->mu[j][x];
+        mu[nd.node_off + x] = v;
+        lg[nd.node_off + x] = v > 0.0 ? std::log(v) : -INFINITY;
+      }
+    }
+    if ((rc = up(h->d_logg, lg.data(), sizeof(double) * lg.size())) ||
+        (rc = up(h->d_mu, mu.data(), sizeof(double) * mu.size())))
+      return bail(rc);
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  // coordinates
+  for (int32_t p = 0; p < num_probs; ++p) {
+    const tree_ot_problem& P = probs[p];
+    const ProbD& pd = h->probs[p];
+    if (!P.coords || pd.dim == 0) continue;
+    const cudaMemcpyKind kind =
+        (P.flags & TREE_OT_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int32_t j = 0; j < P.num_nodes; ++j) {
+      const NodeD& nd = h->nodes[h->prob_node_base[p] + j];
+      cudaError_t e = cudaMemcpyAsync(h->d_coords + nd.coord_off, P.coords[j], sizeof(float) * nd.n * pd.dim, kind, s);
+      if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpyAsync(coords)"));
+    }
+  }
+  // dense costs: borrow aligned device matrices, otherwise copy into a padded buffer
+  CUDA_TRY(cudaMemsetAsync(h->d_scan, 0, sizeof(int32_t), s));
+  for (int32_t p = 0; p < num_probs; ++p) {
+    const tree_ot_problem& P = probs[p];
+    if (P.cost_kind != TREE_OT_COST_DENSE_F32) continue;
+    for (int32_t e = 0; e < P.num_nodes - 1; ++e) {
+      EdgeD& ed = h->edges[h->prob_edge_base[p] + e];
+      const float* src = P.dense_cost[e];
+      const bool dev = (P.flags & TREE_OT_INPUT_DEVICE) != 0;
+      if (dev && ed.nb % 4 == 0 && ((uintptr_t)src % 16) == 0) {
+        ed.C = src;
+        ed.ld = ed.nb;
+      } else {
+        float* dst = nullptr;
+        if ((rc = h->alloc(&dst, (int64_t)ed.na * ed.ld))) return bail(rc);
+        if (dev) {
+          cudaError_t ce = launch_pad_copy(src, ed.nb, dst, ed.ld, ed.na, ed.nb, s);
+          if (ce != cudaSuccess) return bail(cuda_fail(ce, "pad copy"));
+        } else {
+          if (ed.ld != ed.nb) {
+            cudaError_t ce = launch_fill_f32(dst, (int64_t)ed.na * ed.ld, INFINITY, s);
+            if (ce != cudaSuccess) return bail(cuda_fail(ce, "fill"));
+          }
+          cudaError_t ce = cudaMemcpy2DAsync(dst, sizeof(float) * ed.ld, src, sizeof(float) * ed.nb,
+                                             sizeof(float) * ed.nb, ed.na, cudaMemcpyHostToDevice, s);
+          if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpy2DAsync(cost)"));
+        }
+        ed.C = dst;
+      }
+      cudaError_t ce = launch_scan_cost(ed.C, ed.ld, ed.na, ed.nb, h->d_scan, s);
+      if (ce != cudaSuccess) return bail(cuda_fail(ce, "cost scan"));
+    }
+  }
+  // plan tables
+  if ((rc = up(h->d_probs, h->probs.data(), sizeof(ProbD) * h->probs.size())) ||
+      (rc = up(h->d_nodes, h->nodes.data(), sizeof(NodeD) * h->nodes.size())) ||
+      (rc = up(h->d_edges, h->edges.data(), sizeof(EdgeD) * h->edges.size())) ||
+      (rc = up(h->d_dedges, h->dedges.data(), sizeof(DEdgeD) * h->dedges.size())) ||
+      (rc = up(h->d_node_dedges, h->node_dedges.data(), sizeof(int32_t) * h->node_dedges.size())) ||
+      (rc = up(h->d_tasks[0], h->tasks[0].data(), sizeof(Task) * h->tasks[0].size())) ||
+      (rc = up(h->d_tasks[1], h->tasks[1].data(), sizeof(Task) * h->tasks[1].size())) ||
+      (rc = up(h->d_chunks[0], h->chunks[0].data(), sizeof(NodeChunk) * h->chunks[0].size())) ||
+      (rc = up(h->d_chunks[1], h->chunks[1].data(), sizeof(NodeChunk) * h->chunks[1].size())) ||
+      (rc = up(h->d_check_tasks, h->check_tasks.data(), sizeof(Task) * h->check_tasks.size())))
+    return bail(rc);
+  int32_t bad = 0;
+  {
+    cudaError_t ce = cudaMemcpyAsync(&bad, h->d_scan, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "scan read-back"));
+    ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize(create)"));
+  }
+  if (bad) return bail(fail(TREE_OT_ERR_NONFINITE, "a dense cost holds NaN or -inf"));
+
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  h->apply_grid = sms * apply_ctas_per_sm();
+  {
+    cudaError_t ce = cudaStreamCreateWithFlags(&h->hstream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
+  }
+  if ((rc = reset_state(h, s))) return bail(rc);
+  {
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize(create)"));
+  }
+  *out = h;
+  return TREE_OT_OK;
+}
+
+int tree_ot_destroy(tree_ot_handle* h) {
+  if (!h) return TREE_OT_OK;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->hstream) cudaStreamDestroy(h->hstream);
+  for (void* p : h->owned) cudaFree(p);
+  delete h;
+  return TREE_OT_OK;
+}
+
+int tree_ot_reset(tree_ot_handle* h, void* cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(TREE_OT_ERR_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  RC_TRY(reset_state(h, s));
+  h->h_done.clear();
+  h->h_done_at.clear();
+  h->last_status.clear();
+  return TREE_OT_OK;
+}
+
+int tree_ot_half_steps(tree_ot_handle* h, void* cuda_stream, int64_t T) {
+  g_err.clear();
+  if (!h || T < 0) return fail(TREE_OT_ERR_ARG, "handle is NULL or T < 0");
+  return queue_half_steps(h, T, false, (cudaStream_t)cuda_stream);
+}
+
+int tree_ot_apply(tree_ot_handle* h, void* cuda_stream, int32_t colour) {
+  g_err.clear();
+  if (!h || (colour != 0 && colour != 1)) return fail(TREE_OT_ERR_ARG, "handle is NULL or colour not 0/1");
+  return launch_apply(h, colour, (cudaStream_t)cuda_stream);
+}
+
+int tree_ot_node_update(tree_ot_handle* h, void* cuda_stream, int32_t colour) {
+  g_err.clear();
+  if (!h || (colour != 0 && colour != 1)) return fail(TREE_OT_ERR_ARG, "handle is NULL or colour not 0/1");
+  if ((h->hs_host % 2) != colour) return fail(TREE_OT_ERR_STATE, "node_update colour does not follow the schedule");
+  RC_TRY(launch_update(h, colour, false, (cudaStream_t)cuda_stream));
+  ++h->hs_host;
+  return TREE_OT_OK;
+}
+
+int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results) {
+  g_err.clear();
+  if (!h) return fail(TREE_OT_ERR_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int G = h->opt.check_every;
+  h->h_done.assign(h->nprob, 0);
+  h->h_done_at.assign(h->nprob, 0);
+  int32_t err = 0;
+  if (h->hs_host % 2) RC_TRY(queue_half_steps(h, 1, true, s));
+  bool use_graph = h->opt.use_graph != 0;
+  if (use_graph) RC_TRY(build_graph(h, G));
+  while (h->hs_host < h->opt.max_half_steps) {
+    const int64_t left = h->opt.max_half_steps - h->hs_host;
+    if (use_graph && left >= G) {
+      CUDA_TRY(cudaGraphLaunch(h->graph, s));
+      h->hs_host += G;
+    } else {
+      RC_TRY(queue_half_steps(h, std::min<int64_t>(G, left), true, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&err, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return fail(TREE_OT_ERR_NONFINITE, "a potential became non-finite (an infeasible or degenerate input)");
+    bool all = true;
+    for (int p = 0; p < h->nprob; ++p) all = all && h->h_done[p];
+    if (all) break;
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(
+      cudaMemcpyAsync(h->h_done_at.data(), h->d_done_at, sizeof(int64_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  RC_TRY(run_check(h, s));
+  h->last_status.assign(h->nprob, TREE_OT_OK);
+  bool any_nc = false;
+  for (int p = 0; p < h->nprob; ++p)
+    if (!h->h_done[p]) {
+      h->last_status[p] = TREE_OT_NOT_CONVERGED;
+      any_nc = true;
+    }
+  h->last_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (results) fill_results(h, results);
+  return any_nc ? TREE_OT_NOT_CONVERGED : TREE_OT_OK;
+}
+
+int tree_ot_check(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results) {
+  g_err.clear();
+  if (!h) return fail(TREE_OT_ERR_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (h->h_done.empty()) {
+    h->h_done.assign(h->nprob, 0);
+    h->h_done_at.assign(h->nprob, 0);
+  }
+  RC_TRY(run_check(h, s));
+  if (results) fill_results(h, results);
+  return TREE_OT_OK;
+}
+
+int tree_ot_marginals(tree_ot_handle* h, int32_t prob, int32_t node, double* out) {
+  g_err.clear();
+  if (!h || !out || prob < 0 || prob >= h->nprob || node < 0 || node >= h->prob_nodes[prob])
+    return fail(TREE_OT_ERR_ARG, "bad handle, problem, node or output pointer");
+  if (!h->have_check) return fail(TREE_OT_ERR_STATE, "call tree_ot_check or tree_ot_solve first");
+  const NodeD& nd = h->nodes[h->prob_node_base[prob] + node];
+  for (int32_t x = 0; x < nd.n; ++x) {
+    double q = 0.0;
+    for (int32_t i = 0; i < nd.deg; ++i) q += h->h_marg[h->dedges[h->node_dedges[nd.dedge_begin + i]].off + x];
+    out[x] = q / nd.deg;
+  }
+  return TREE_OT_OK;
+}
+
+int tree_ot_get_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, int32_t dedge, double* out) {
+  g_err.clear();
+  if (!h || !out || prob < 0 || prob >= h->nprob || dedge < 0 || dedge >= 2 * (h->prob_nodes[prob] - 1))
+    return fail(TREE_OT_ERR_ARG, "bad handle, problem, directed edge or output pointer");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const DEdgeD& d = h->dedges[2 * h->prob_edge_base[prob] + dedge];
+  const int32_t n = h->nodes[d.owner].n;
+  double z = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(out, h->d_f + d.off, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&z, h->d_Z + d.owner, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const double eps = h->probs[prob].eps;
+  for (int32_t x = 0; x < n; ++x) out[x] -= eps * z;
+  return TREE_OT_OK;
+}
+
+int tree_ot_set_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, int32_t dedge, const double* in) {
+  g_err.clear();
+  if (!h || !in || prob < 0 || prob >= h->nprob || dedge < 0 || dedge >= 2 * (h->prob_nodes[prob] - 1))
+    return fail(TREE_OT_ERR_ARG, "bad handle, problem, directed edge or input pointer");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int32_t di = 2 * h->prob_edge_base[prob] + dedge;
+  const DEdgeD& d = h->dedges[di];
+  const int32_t n = h->nodes[d.owner].n;
+  for (int32_t x = 0; x < n; ++x)
+    if (!std::isfinite(in[x])) return fail(TREE_OT_ERR_NONFINITE, "potential entries must be finite");
+  double z = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&z, h->d_Z + d.owner, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> v(in, in + n);
+  const double eps = h->probs[prob].eps;
+  for (int32_t x = 0; x < n; ++x) v[x] += eps * z;
+  CUDA_TRY(cudaMemcpyAsync(h->d_f + d.off, v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges + di, h->d_nodes, h->d_probs, 1, kLog2e, h->d_hh,
+                          h->d_hl, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->have_check = false;
+  return TREE_OT_OK;
+}
+
+int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
+  g_err.clear();
+  if (!h || !stats || nstats < 0) return fail(TREE_OT_ERR_ARG, "bad handle or stats pointer");
+  const int64_t v[9] = {(int64_t)h->dedges.size(),
+                        (int64_t)h->edges.size(),
+                        h->elems,
+                        h->matrix_bytes,
+                        (int64_t)h->tasks[0].size(),
+                        (int64_t)h->tasks[1].size(),
+                        h->device_bytes,
+                        (int64_t)h->chunks[0].size(),
+                        (int64_t)h->chunks[1].size()};
+  for (int32_t i = 0; i < nstats && i < 9; ++i) stats[i] = v[i];
+  return TREE_OT_OK;
+}
+
+}  // extern "C"

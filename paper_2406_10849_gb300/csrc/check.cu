@@ -1,0 +1,254 @@
+// Final check of the current potentials: row and column sums of every plan
+//   B_e(x,y) = exp( a(x) + b(y) - C_e(x,y)/eps ),
+//   a = f_(a,b)/eps + log gamma_a,  b = f_(b,a)/eps + log gamma_b,
+// plus sum_e <C_e,B_e> and ||B_e||_1, accumulated in FP64 per row / column.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the exponent is
+// formed in double-float arithmetic: a and b arrive as (hi, lo) FP32 pairs
+// computed from the FP64 potentials, C/eps is an exact FP32 x (hi, lo) product
+// (Dekker's product via FMA), and the sums use Knuth's error-free TwoSum, so
+// the exponent is exact to ~1e-12 before one accurate expf of its high part.
+// Each plan entry then has ~1e-7 relative error with no systematic part.
+#include <cmath>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace treeot {
+namespace {
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+
+// exact-ish square of (p - q) as a double-float
+__device__ __forceinline__ DF sq_diff(float p, float q) {
+  const DF d = two_sum(p, -q);
+  const float h = d.hi * d.hi;
+  const float e = fmaf(d.hi, d.hi, -h) + 2.f * d.hi * d.lo;
+  return {h, e};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return {s.hi, s.lo + a.lo + b.lo};
+}
+
+// C(x,y) as a double-float; dense costs are exact FP32 values
+__device__ __forceinline__ DF cost_df(const CheckArgs& A, const EdgeD& e, const ProbD& P, int x, int y,
+                                     const float* pa, const float* pb) {
+  if (P.cost_kind == 0) return {e.C[(int64_t)x * e.ld + y], 0.f};
+  DF c = sq_diff(pa[0], pb[0]);
+  if (P.dim > 1) c = df_add(c, sq_diff(pa[1], pb[1]));
+  if (P.dim > 2) c = df_add(c, sq_diff(pa[2], pb[2]));
+  return c;
+}
+
+// B = exp(a + b - C * k), k = scale / eps as (kh, kl); returns B and adds C*B to tc
+__device__ __forceinline__ float plan_entry(float ah, float al, float bh, float bl, DF c, float kh, float kl,
+                                            float& cost_out) {
+  const DF s = two_sum(ah, bh);
+  const float p = c.hi * kh;
+  const float pe = fmaf(c.hi, kl, fmaf(c.lo, kh, fmaf(c.hi, kh, -p)));
+  const DF d = two_sum(s.hi, -p);
+  const float lo = (s.lo + d.lo) + (al + bl) - pe;
+  cost_out = c.hi + c.lo;
+  const float E = expf(d.hi);
+  return E == 0.f ? 0.f : E * (1.f + lo);
+}
+
+__global__ void __launch_bounds__(256) check_kernel(CheckArgs A) {
+  __shared__ float sbh[256], sbl[256];
+  __shared__ float sq[256 * 3];
+  for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
+    const Task t = A.tasks[ti];
+    const DEdgeD d = A.dedges[t.dedge];
+    const EdgeD e = A.edges[d.edge];
+    const ProbD P = A.probs[d.prob];
+    const double kd = (P.cost_kind == 0 ? 1.0 : P.cost_scale) * P.inv_eps;
+    const float kh = (float)kd, kl = (float)(kd - (double)kh);
+    const NodeD na = A.nodes[e.a], nb = A.nodes[e.b];
+    // a-side operand: rows (owner a, dedge 2e) ; b-side: columns (owner b, dedge 2e+1)
+    const int64_t a_off = d.dir == 0 ? d.off : d.rev_off;
+    const int64_t b_off = d.dir == 0 ? d.rev_off : d.off;
+    const int D = P.dim;
+    double tc_acc = 0.0, mass_acc = 0.0;
+    if (t.kind == TASK_ROW) {
+      // warp per row x in [o0, o0+ocount) of node a; lanes stride the columns
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int r = warp; r < t.ocount; r += 8) {
+        const int x = t.o0 + r;
+        const float ah = A.ah[a_off + x], al = A.al[a_off + x];
+        const float* pa = A.coords + (na.coord_off >= 0 ? na.coord_off + (int64_t)x * D : 0);
+        float sum = 0.f, comp = 0.f, tcs = 0.f, tcc = 0.f;
+        if (ah > -INFINITY) {
+          for (int y = lane; y < e.nb; y += 32) {
+            const float* pb = A.coords + (nb.coord_off >= 0 ? nb.coord_off + (int64_t)y * D : 0);
+            const float bh = A.ah[b_off + y], bl = A.al[b_off + y];
+            if (!(bh > -INFINITY)) continue;
+            float cst;
+            const float B = plan_entry(ah, al, bh, bl, cost_df(A, e, P, x, y, pa, pb), kh, kl, cst);
+            // Kahan sums
+            const float y1 = B - comp;
+            const float t1 = sum + y1;
+            comp = (t1 - sum) - y1;
+            sum = t1;
+            const float cb = (P.cost_kind == 0 ? cst : cst * (float)P.cost_scale) * B;
+            const float y2 = cb - tcc;
+            const float t2 = tcs + y2;
+            tcc = (t2 - tcs) - y2;
+            tcs = t2;
+          }
+        }
+        const double rs = warp_sum_d((double)sum - (double)comp);
+        const double tr = warp_sum_d((double)tcs - (double)tcc);
+        if (lane == 0) {
+          A.marg[a_off + x] = rs;
+          tc_acc += tr;
+          mass_acc += rs;
+        }
+      }
+    } else {
+      // thread per column y in [o0, o0+ocount) of node b; rows staged by 256
+      const int ycol = t.o0 + threadIdx.x;
+      const bool on = threadIdx.x < t.ocount;
+      const float bh = on ? A.ah[b_off + ycol] : -INFINITY;
+      const float bl = on ? A.al[b_off + ycol] : 0.f;
+      const float* pb = A.coords + ((nb.coord_off >= 0 && on) ? nb.coord_off + (int64_t)ycol * D : 0);
+      float sum = 0.f, comp = 0.f;
+      for (int x0 = 0; x0 < e.na; x0 += 256) {
+        __syncthreads();
+        const int xl = x0 + threadIdx.x;
+        if (xl < e.na) {
+          sbh[threadIdx.x] = A.ah[a_off + xl];
+          sbl[threadIdx.x] = A.al[a_off + xl];
+          if (na.coord_off >= 0)
+            for (int k = 0; k < D; ++k) sq[threadIdx.x * 3 + k] = A.coords[na.coord_off + (int64_t)xl * D + k];
+        }
+        __syncthreads();
+        const int cnt = min(256, e.na - x0);
+        if (on && bh > -INFINITY) {
+          for (int i = 0; i < cnt; ++i) {
+            const float ahx = sbh[i];
+            if (!(ahx > -INFINITY)) continue;
+            float cst;
+            const float B = plan_entry(ahx, sbl[i], bh, bl, cost_df(A, e, P, x0 + i, ycol, sq + 3 * i, pb), kh,
+                                       kl, cst);
+            const float y1 = B - comp;
+            const float t1 = sum + y1;
+            comp = (t1 - sum) - y1;
+            sum = t1;
+          }
+        }
+      }
+      if (on) A.marg[b_off + ycol] = (double)sum - (double)comp;
+    }
+    if (t.kind == TASK_ROW) {
+      if ((threadIdx.x & 31) == 0 && (tc_acc != 0.0 || mass_acc != 0.0)) {
+        atomicAdd(&A.edge_tc[d.edge], tc_acc);
+        atomicAdd(&A.edge_mass[d.edge], mass_acc);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// v = (f'/eps - Z_owner + log gamma_owner) * scale, split into FP32 (hi, lo), per
+// directed-edge entry.  Z may be null (the apply operand leaves Z out).
+__global__ void operand_kernel(const double* f, const double* Z, const double* logg, const DEdgeD* dedges,
+                               const NodeD* nodes, const ProbD* probs, int32_t d0, int32_t ndedges, double scale,
+                               float* vh, float* vl) {
+  const int di = d0 + blockIdx.y;
+  if (di >= ndedges) return;
+  const DEdgeD d = dedges[di];
+  const NodeD nd = nodes[d.owner];
+  const double inv_eps = probs[d.prob].inv_eps;
+  const double z = Z ? Z[d.owner] : 0.0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nd.n; x += gridDim.x * blockDim.x) {
+    const double lg = logg[nd.node_off + x];
+    const double a = (f[d.off + x] * inv_eps - z + lg) * scale;
+    const float hi = (float)a;
+    vh[d.off + x] = (lg == -INFINITY) ? -INFINITY : hi;
+    vl[d.off + x] = isfinite(a) ? (float)(a - (double)hi) : 0.f;
+  }
+}
+
+// counts NaN and -inf entries of a padded dense cost (+inf is allowed)
+__global__ void scan_cost_kernel(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad) {
+  int local = 0;
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = C[(i / cols) * ld + (i % cols)];
+    if (v != v || v == -INFINITY) local = 1;
+  }
+  if (__syncthreads_or(local) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+__global__ void fill_kernel(float* p, int64_t n, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void pad_copy_kernel(const float* src, int64_t src_ld, float* dst, int64_t dst_ld, int32_t rows,
+                                int32_t cols) {
+  const int r = blockIdx.y;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < dst_ld; c += (int64_t)gridDim.x * blockDim.x)
+    dst[(int64_t)r * dst_ld + c] = c < cols ? src[(int64_t)r * src_ld + c] : INFINITY;
+}
+
+}  // namespace
+
+cudaError_t launch_check(const CheckArgs& a, cudaStream_t s) {
+  if (a.ntasks <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = a.ntasks < sms * 4 ? a.ntasks : sms * 4;
+  check_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_operand(const double* f, const double* Z, const double* logg, const DEdgeD* dedges,
+                           const NodeD* nodes, const ProbD* probs, int32_t ndedges, double scale, float* vh, float* vl,
+                           cudaStream_t s) {
+  for (int32_t d0 = 0; d0 < ndedges; d0 += 65535) {
+    const int32_t cnt = ndedges - d0 < 65535 ? ndedges - d0 : 65535;
+    dim3 grid(4, cnt);
+    operand_kernel<<<grid, 256, 0, s>>>(f, Z, logg, dedges, nodes, probs, d0, ndedges, scale, vh, vl);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_cost(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad, cudaStream_t s) {
+  if ((int64_t)rows * cols <= 0) return cudaSuccess;
+  scan_cost_kernel<<<1024, 256, 0, s>>>(C, ld, rows, cols, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  fill_kernel<<<(int)blocks, 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_copy(const float* src, int64_t src_ld, float* dst, int64_t dst_ld, int32_t rows,
+                            int32_t cols, cudaStream_t s) {
+  for (int32_t r0 = 0; r0 < rows; r0 += 65535) {
+    const int32_t cnt = rows - r0 < 65535 ? rows - r0 : 65535;
+    dim3 grid(4, cnt);
+    pad_copy_kernel<<<grid, 256, 0, s>>>(src + (int64_t)r0 * src_ld, src_ld, dst + (int64_t)r0 * dst_ld, dst_ld, cnt,
+                                         cols);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace treeot

@@ -1,0 +1,351 @@
+"""ctypes binding of libtreeot.so (include/tree_ot.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  If the shared library
+is missing this module raises at import time; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtreeot.so")
+
+OK = 0
+NOT_CONVERGED = 1
+ERR = {
+    -1: "ARG", -2: "NOT_TREE", -3: "FIXED_NOT_LEAF", -4: "FIXED_ADJACENT", -5: "MARGINAL",
+    -6: "NONFINITE", -7: "EPS", -8: "CUDA", -9: "OOM", -10: "TIMEOUT", -11: "STATE",
+}
+COST_DENSE_F32 = 0
+COST_SQEUCLID = 1
+INPUT_DEVICE = 1
+PREC = {"fp32": 0, "fp64": 1}
+TOL_KIND = {"sum": 0, "max": 1}
+APPLY = {"auto": 0, "lse": 1}
+
+
+class TreeOTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tree_ot error {code} ({ERR.get(code, '?')}): {msg}")
+        self.code = code
+        self.kind = ERR.get(code, "?")
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("num_nodes", C.c_int32),
+        ("edges", C.POINTER(C.c_int32)),
+        ("support_size", C.POINTER(C.c_int32)),
+        ("is_fixed", C.POINTER(C.c_uint8)),
+        ("marginal", C.POINTER(C.POINTER(C.c_double))),
+        ("eps", C.c_double),
+        ("cost_kind", C.c_int32),
+        ("dim", C.c_int32),
+        ("coords", C.POINTER(C.POINTER(C.c_float))),
+        ("cost_scale", C.c_double),
+        ("dense_cost", C.POINTER(C.POINTER(C.c_float))),
+        ("flags", C.c_uint32),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32),
+        ("apply_mode", C.c_int32),
+        ("tol", C.c_double),
+        ("tol_kind", C.c_int32),
+        ("max_half_steps", C.c_int64),
+        ("check_every", C.c_int32),
+        ("use_graph", C.c_int32),
+        ("flags", C.c_uint32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32),
+        ("half_steps", C.c_int64),
+        ("residual_sum_l1", C.c_double),
+        ("max_marginal_l1", C.c_double),
+        ("primal", C.c_double),
+        ("dual", C.c_double),
+        ("transport_cost", C.c_double),
+        ("wall_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every exported symbol of include/tree_ot.h with its ctypes signature
+SIGNATURES = {
+    "tree_ot_default_options": (None, [C.POINTER(Options)]),
+    "tree_ot_error_string": (C.c_char_p, [C.c_int]),
+    "tree_ot_last_error": (C.c_char_p, []),
+    "tree_ot_validate": (C.c_int, [C.POINTER(Problem)]),
+    "tree_ot_bipartition": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_uint8)]),
+    "tree_ot_create": (C.c_int, [C.POINTER(Problem), C.c_int32, C.POINTER(Options), C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "tree_ot_destroy": (C.c_int, [C.c_void_p]),
+    "tree_ot_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tree_ot_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Result)]),
+    "tree_ot_half_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "tree_ot_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "tree_ot_node_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "tree_ot_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Result)]),
+    "tree_ot_marginals": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_get_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_set_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_plan_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtreeot.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, allow=(OK,)):
+    if rc in allow:
+        return rc
+    msg = _lib.tree_ot_last_error().decode(errors="replace")
+    raise TreeOTError(rc, msg)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr_of(obj, ctype):
+    """(pointer, keepalive) for a numpy array or a torch tensor (host or device)."""
+    if hasattr(obj, "data_ptr"):
+        return C.cast(C.c_void_p(obj.data_ptr()), C.POINTER(ctype)), obj
+    arr = np.ascontiguousarray(obj)
+    return arr.ctypes.data_as(C.POINTER(ctype)), arr
+
+
+class _Marshalled:
+    """ctypes image of one problem plus the buffers it points into."""
+
+    def __init__(self, p, device_costs=None, device_coords=None):
+        keep = []
+        J = int(p.num_nodes)
+        self.J = J
+        edges = np.ascontiguousarray(np.asarray(p.edges, dtype=np.int32).reshape(-1))
+        n = np.ascontiguousarray(np.asarray(p.n, dtype=np.int32))
+        fixed = np.ascontiguousarray(np.asarray(p.fixed, dtype=np.uint8))
+        keep += [edges, n, fixed]
+        marg_ptrs = (C.POINTER(C.c_double) * J)()
+        for j in range(J):
+            if fixed[j]:
+                m = np.ascontiguousarray(np.asarray(p.marginals[j], dtype=np.float64))
+                keep.append(m)
+                marg_ptrs[j] = m.ctypes.data_as(C.POINTER(C.c_double))
+        keep.append(marg_ptrs)
+        flags = 0
+        coord_src = device_coords if device_coords is not None else p.coords
+        coords_ptrs = (C.POINTER(C.c_float) * J)()
+        dim = int(p.coords[0].shape[1]) if p.coords is not None else 0
+        for j in range(J):
+            ptr, k = _ptr_of(coord_src[j] if device_coords is not None
+                             else np.asarray(p.coords[j], dtype=np.float32), C.c_float)
+            keep.append(k)
+            coords_ptrs[j] = ptr
+        keep.append(coords_ptrs)
+        dense_ptrs = None
+        kind = COST_SQEUCLID if p.cost_kind == "sqeuclid" else COST_DENSE_F32
+        if kind == COST_DENSE_F32:
+            dense_ptrs = (C.POINTER(C.c_float) * max(1, J - 1))()
+            for e in range(J - 1):
+                src = device_costs[e] if device_costs is not None else p.dense_cost(e)
+                ptr, k = _ptr_of(src, C.c_float)
+                keep.append(k)
+                dense_ptrs[e] = ptr
+            keep.append(dense_ptrs)
+        if device_costs is not None or device_coords is not None:
+            flags |= INPUT_DEVICE
+            if device_coords is None:
+                # device flag covers coords too: stage them on the device
+                import torch
+                dcs = [torch.as_tensor(np.asarray(c, np.float32)).cuda() for c in p.coords]
+                keep += dcs
+                for j in range(J):
+                    coords_ptrs[j] = C.cast(C.c_void_p(dcs[j].data_ptr()), C.POINTER(C.c_float))
+        self.struct = Problem(
+            num_nodes=J,
+            edges=edges.ctypes.data_as(C.POINTER(C.c_int32)),
+            support_size=n.ctypes.data_as(C.POINTER(C.c_int32)),
+            is_fixed=fixed.ctypes.data_as(C.POINTER(C.c_uint8)),
+            marginal=marg_ptrs,
+            eps=float(p.eps),
+            cost_kind=kind,
+            dim=dim,
+            coords=coords_ptrs,
+            cost_scale=float(p.cost_scale),
+            dense_cost=dense_ptrs,
+            flags=flags,
+        )
+        self.keep = keep
+
+
+def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, check_every=32, use_graph=True,
+            apply_mode="auto") -> Options:
+    load()
+    o = Options()
+    _lib.tree_ot_default_options(C.byref(o))
+    o.precision = PREC[precision]
+    o.apply_mode = APPLY[apply_mode]
+    o.tol = float(tol)
+    o.tol_kind = TOL_KIND[tol_kind]
+    o.max_half_steps = int(max_half_steps)
+    o.check_every = int(check_every)
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def validate(problem) -> int:
+    """tree_ot_validate on one problem; returns the code (0 = valid)."""
+    load()
+    m = _Marshalled(problem)
+    return _lib.tree_ot_validate(C.byref(m.struct))
+
+
+def bipartition(num_nodes: int, edges) -> np.ndarray:
+    load()
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    out = np.zeros(num_nodes, dtype=np.uint8)
+    _check(_lib.tree_ot_bipartition(num_nodes, e.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out
+
+
+class Solver:
+    """One handle over a batch of problems (tree_ot_create .. tree_ot_destroy)."""
+
+    def __init__(self, problems: Sequence, opts: Optional[Options] = None, stream=None,
+                 device_costs: Optional[List] = None, device_coords: Optional[List] = None, **kw):
+        load()
+        self.problems = list(problems)
+        dc = device_costs if device_costs is not None else [None] * len(self.problems)
+        dk = device_coords if device_coords is not None else [None] * len(self.problems)
+        self._m = [_Marshalled(p, dc[i], dk[i]) for i, p in enumerate(self.problems)]
+        arr = (Problem * len(self._m))(*[m.struct for m in self._m])
+        self._arr = arr
+        self.opts = opts if opts is not None else options(**kw)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(_lib.tree_ot_create(arr, len(self._m), C.byref(self.opts), C.c_void_p(_stream_ptr(stream)),
+                                   C.byref(h)))
+        self.h = h
+        # borrowed device buffers must outlive the handle
+        self._borrowed = [m.keep for m in self._m]
+
+    def _s(self):
+        return C.c_void_p(_stream_ptr(self.stream))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.tree_ot_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self):
+        res = (Result * len(self._m))()
+        rc = _check(_lib.tree_ot_solve(self.h, self._s(), res), allow=(OK, NOT_CONVERGED))
+        return rc, [r.as_dict() for r in res]
+
+    def half_steps(self, T: int):
+        _check(_lib.tree_ot_half_steps(self.h, self._s(), int(T)))
+
+    def apply(self, colour: int):
+        _check(_lib.tree_ot_apply(self.h, self._s(), int(colour)))
+
+    def node_update(self, colour: int):
+        _check(_lib.tree_ot_node_update(self.h, self._s(), int(colour)))
+
+    def reset(self):
+        _check(_lib.tree_ot_reset(self.h, self._s()))
+
+    def check(self):
+        res = (Result * len(self._m))()
+        _check(_lib.tree_ot_check(self.h, self._s(), res))
+        return [r.as_dict() for r in res]
+
+    def marginal(self, prob: int, node: int) -> np.ndarray:
+        n = int(self.problems[prob].n[node])
+        out = np.zeros(n, np.float64)
+        _check(_lib.tree_ot_marginals(self.h, prob, node, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def potential(self, prob: int, dedge: int) -> np.ndarray:
+        p = self.problems[prob]
+        e = dedge // 2
+        owner = int(p.edges[e][dedge % 2])
+        out = np.zeros(int(p.n[owner]), np.float64)
+        _check(_lib.tree_ot_get_potentials(self.h, self._s(), prob, dedge,
+                                           out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def potentials(self, prob: int = 0) -> dict:
+        """{(j,k): f_(j,k)} for every directed edge of problem ``prob``."""
+        p = self.problems[prob]
+        out = {}
+        for e, (a, b) in enumerate(np.asarray(p.edges)):
+            out[(int(a), int(b))] = self.potential(prob, 2 * e)
+            out[(int(b), int(a))] = self.potential(prob, 2 * e + 1)
+        return out
+
+    def set_potential(self, prob: int, dedge: int, values):
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+        _check(_lib.tree_ot_set_potentials(self.h, self._s(), prob, dedge, v.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def set_potentials(self, f: dict, prob: int = 0):
+        p = self.problems[prob]
+        for e, (a, b) in enumerate(np.asarray(p.edges)):
+            self.set_potential(prob, 2 * e, f[(int(a), int(b))])
+            self.set_potential(prob, 2 * e + 1, f[(int(b), int(a))])
+
+    def plan_stats(self) -> dict:
+        st = (C.c_int64 * 9)()
+        _check(_lib.tree_ot_plan_stats(self.h, st, 9))
+        keys = ["directed_edges", "edges", "elements_per_half_step", "matrix_bytes_per_half_step",
+                "apply_tasks_c0", "apply_tasks_c1", "device_bytes", "node_ctas_c0", "node_ctas_c1"]
+        return dict(zip(keys, [int(x) for x in st]))
