@@ -6,7 +6,7 @@ dense FP32 cost per edge (63 edges, 4.2 GB on the device), Dirichlet(1) leaf
 marginals, eps = 0.01.  One step = one half-step of the sweep: the edge-apply
 launch (every edge's Gibbs kernel applied once toward the active colour, in
 log-sum-exp form, reading all 4.2 GB) followed by the node-update launch
-(Theorem 1 updates + stopping terms).  63 edge applies per step.
+(block updates of thm:tree_dual_var + stopping terms).  63 edge applies per step.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -32,11 +32,18 @@ import numpy as np  # noqa: E402
 METRIC = "edge-kernel applies/sec"
 UNIT = "edge_applies/s"
 WORKLOAD = "prufer64_n4096_dense_fp32_eps0.01"
+NODES = 64
 
 
-def workload_problem():
+def workload_name(nodes: int) -> str:
+    return WORKLOAD if nodes == 64 else f"prufer{nodes}_n4096_dense_fp32_eps0.01"
+
+
+def workload_problem(nodes: int = NODES):
+    """The Pruefer-tree workload; nodes < 64 gives the same construction on a smaller
+    tree (used for profiling captures that must stay small)."""
     import gen
-    return gen.prufer_problem(seed=3000, J=64, n=4096, num_leaves=32, D=3, eps=0.01)
+    return gen.prufer_problem(seed=3000, J=nodes, n=4096, num_leaves=nodes // 2, D=3, eps=0.01)
 
 
 def algorithmic_bytes(p) -> int:
@@ -164,7 +171,7 @@ def cpu_baseline(p, budget_s: float = 12.0, max_applies: int = 16):
         if t_total >= budget_s:
             break
     return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} of 63 edge applies of half-step 1 (FP64 numpy log-sum-exp over 4096x4096), "
+            "sample": f"{done} of {p.num_edges} edge applies of half-step 1 (FP64 numpy log-sum-exp over 4096x4096), "
                       f"{t_total:.1f} s"}
 
 
@@ -219,6 +226,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-1e-6 solve")
+    ap.add_argument("--nodes", type=int, default=NODES, help="tree size (64 = the benchmark workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -241,7 +249,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    p = workload_problem()
+    p = workload_problem(args.nodes)
+    workload = workload_name(args.nodes)
     costs = [gen.sqeuclid_cost_f32_torch(p.coords[a], p.coords[b], 1.0, dev) for a, b in p.edges]
     torch.cuda.synchronize(dev)
     solver = T.Solver([p], T.options(precision="fp32"), stream=stream, device_costs=[costs])
@@ -291,8 +300,8 @@ def main():
     peak, peak_kind = read_peaks()
     achieved = alg / (apply_avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(WORKLOAD), "peak_kind": f"hbm_gbs of {peak_kind}",
-                "kernel": "apply_f32_kernel", "apply_ms_avg": apply_avg_ms,
+                "traffic": profiled_traffic(workload), "peak_kind": f"hbm_gbs of {peak_kind}",
+                "kernel": "apply_dense_kernel", "apply_ms_avg": apply_avg_ms,
                 "apply_ms_median": statistics.median(apply_ms), "algorithmic_bytes_per_launch": alg}
 
     extra = {}
@@ -318,7 +327,7 @@ def main():
             hc.copy_(c)
         del costs
         torch.cuda.empty_cache()
-        hp = gen.prufer_problem(seed=3000, J=64, n=4096, num_leaves=32, D=3, eps=0.01)
+        hp = workload_problem(args.nodes)
         hp.dense_costs = [hc.numpy() for hc in host_costs]
         if dist is not None:
             dist.barrier()
@@ -351,8 +360,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": 64, "edges": 63, "n": 4096, "dim": 3, "eps": 0.01,
-                   "cost": "stored dense FP32, 4.2 GB", "step": "one half-step (apply + node update)",
+        "config": {"workload": workload, "nodes": p.num_nodes, "edges": p.num_edges, "n": 4096, "dim": 3,
+                   "eps": 0.01, "cost": f"stored dense FP32, {stats['matrix_bytes_per_half_step'] / 1e9:.2f} GB", "step": "one half-step (apply + node update)",
                    "l2": "inputs (4.2 GB) exceed L2", "elements_per_step": stats["elements_per_half_step"]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * K,
     }

@@ -12,7 +12,7 @@
  * gamma_j = mu_j on Gamma and 1 elsewhere (eq. jointdist), subject to
  * B_(j,k) 1 = mu_j, B_(j,k)^T 1 = mu_k, 1^T mu_j = 1 for free j.
  *
- * Method: the closed-form block updates of Theorem 1 (thm:tree_dual_var) in
+ * Method: the closed-form block updates of theorem thm:tree_dual_var in
  * log form, scheduled as in the Bipartite Iterative Scaling algorithm: the tree
  * is two-coloured; a half-step updates every node of one colour from its
  * neighbours' current potentials.  The colour of node 0 goes first.  One

@@ -18,7 +18,7 @@ paper's notation:
 * potentials lambda_(j,k) = eps * log u_(j,k) (Sec. 3.2); here called ``f[(j,k)]``,
   one vector of length n_j per directed edge.
 
-Updates (Theorem 1, thm:tree_dual_var), written in log form with the message
+Updates (theorem thm:tree_dual_var, Sec. 3.1), written in log form with the message
     m_(j,k)(x) = log( K_(j,k) (u_(k,j) * gamma_k) )(x)
                = LSE_y [ (f_(k,j)(y) - C_(j,k)(x,y)) / eps + log gamma_k(y) ]:
 * fixed j:  u_(j,k_j) = 1 ./ (K u_(k_j,j))          ->  f_(j,k_j) = -eps m_(j,k_j)
@@ -33,12 +33,12 @@ from the neighbours' current potentials.  S_1 is the colour class of node 0.
 Stopping quantity (the while-condition of that algorithm):
     r = sum_{j in Gamma} ||B_(j,k_j) 1 - mu_j||_1
       + sum_{j free} sum_{k in N(j)} ||q_(j,k) - qbar_j||_1,
-with q_(j,k) = B_(j,k) 1 and qbar_j their arithmetic mean (Lemma 4).
+with q_(j,k) = B_(j,k) 1 and qbar_j their arithmetic mean (lemma lem:f_upper_bound_tree).
 
 Readings of the paper taken here (also listed in the design notes):
 * "iteration" t counts half-steps; S_1 (node 0's colour) goes first;
-* the closed form of Theorem 1 is used (it equals the multiplicative listing
-  from u = 1, Proposition 1; ``multiplicative_half_step`` implements the
+* the closed form of thm:tree_dual_var is used (it equals the multiplicative
+  listing from u = 1, proposition cor:equi; ``multiplicative_half_step`` implements the
   listing's form for that check);
 * potentials where gamma_j(x) = 0 are still defined by the update formula.
 """
@@ -202,11 +202,11 @@ def message(problem, f: Potentials, j: int, k: int, rows=None) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# one half-step of the bipartite schedule (Theorem 1 applied to all j in S)
+# one half-step of the bipartite schedule (thm:tree_dual_var applied to all j in S)
 # ---------------------------------------------------------------------------
 
 def update_node(problem, f: Potentials, j: int, nb: List[List[int]]):
-    """New potentials {f_(j,k)}_k of node j and rho_j (None for fixed nodes), Theorem 1."""
+    """New potentials {f_(j,k)}_k of node j and rho_j (None for fixed nodes), thm:tree_dual_var."""
     eps = problem.eps
     msgs = {k: message(problem, f, j, k) for k in nb[j]}
     if problem.fixed[j]:
@@ -375,7 +375,7 @@ def gauge_fix(problem, f: Potentials) -> Potentials:
 
 
 # ---------------------------------------------------------------------------
-# the algorithm listing's multiplicative form (Proposition 1 check)
+# the algorithm listing's multiplicative form (proposition cor:equi check)
 # ---------------------------------------------------------------------------
 
 def multiplicative_half_step(problem, u: Dict[Tuple[int, int], np.ndarray], colour, side: int):

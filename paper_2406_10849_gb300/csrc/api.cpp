@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -38,6 +39,17 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// v = hi + lo with hi the largest float strictly below v, so lo > 0: with an
+// infinite cost c the apply's second product c * lo then stays -inf (a zero or
+// negative lo would turn inf * lo into NaN)
+void split_positive(double v, float* hi, float* lo) {
+  float h = (float)v;
+  if ((double)h >= v) h = std::nextafter(h, 0.0f);
+  *hi = h;
+  *lo = (float)(v - (double)h);
+  if (!(*lo > 0.0f)) *lo = std::numeric_limits<float>::denorm_min();
+}
 
 // ---------------------------------------------------------------------------
 // host-only checks (Sec. 3 assumptions)
@@ -156,7 +168,9 @@ struct tree_ot_handle {
   std::vector<EdgeD> edges;
   std::vector<DEdgeD> dedges;
   std::vector<int32_t> node_dedges;
-  std::vector<Task> tasks[2];
+  std::vector<Task> tasks[2];              // per colour, grouped by kernel slot
+  int32_t slot_begin[2][kApplySlots] = {};
+  int32_t slot_count[2][kApplySlots] = {};
   std::vector<NodeChunk> chunks[2];
   std::vector<Task> check_tasks;
   std::vector<int32_t> prob_node_base, prob_edge_base, prob_nodes;
@@ -190,7 +204,7 @@ struct tree_ot_handle {
   cudaStream_t hstream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
-  int apply_grid = 1;
+  int apply_grid[kApplySlots] = {1, 1, 1, 1};
 
   bool have_check = false;
   std::vector<double> h_marg, h_f, h_Z, h_rho, h_tc, h_mass;
@@ -280,9 +294,21 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
 
 int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
   ApplyArgs a = apply_args(h, colour);
-  const int grid = std::max(1, std::min<int>(a.ntasks, h->apply_grid));
-  cudaError_t e = h->fp64 ? launch_apply_f64(a, grid, s) : launch_apply_f32(a, grid, s);
-  if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+  if (h->fp64) {
+    const int grid = std::max(1, std::min<int>(a.ntasks, h->apply_grid[0]));
+    cudaError_t e = launch_apply_f64(a, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+    return TREE_OT_OK;
+  }
+  for (int slot = 0; slot < kApplySlots; ++slot) {
+    const int32_t cnt = h->slot_count[colour][slot];
+    if (cnt == 0) continue;
+    a.tasks = h->d_tasks[colour] + h->slot_begin[colour][slot];
+    a.ntasks = cnt;
+    const int grid = std::max(1, std::min<int>(cnt, h->apply_grid[slot]));
+    cudaError_t e = launch_apply_f32(a, slot, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+  }
   return TREE_OT_OK;
 }
 
@@ -320,7 +346,7 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), s));
   // apply operand of u = 1: h = log gamma * log2(e)
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, (int32_t)h->dedges.size(),
-                          kLog2e, h->d_hh, h->d_hl, s));
+                          kLog2e, true, h->d_hh, h->d_hl, s));
   h->hs_host = 0;
   h->have_check = false;
   return TREE_OT_OK;
@@ -353,8 +379,8 @@ int build_graph(tree_ot_handle* h, int len) {
 
 int run_check(tree_ot_handle* h, cudaStream_t s) {
   const int32_t nd = (int32_t)h->dedges.size();
-  CUDA_TRY(launch_operand(h->d_f, h->d_Z, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, nd, 1.0, h->d_ah, h->d_al,
-                          s));
+  CUDA_TRY(launch_operand(h->d_f, h->d_Z, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, nd, 1.0, false, h->d_ah,
+                          h->d_al, s));
   CUDA_TRY(cudaMemsetAsync(h->d_edge_tc, 0, sizeof(double) * h->edges.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_edge_mass, 0, sizeof(double) * h->edges.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_marg, 0, sizeof(double) * h->vec_len, s));
@@ -367,11 +393,14 @@ int run_check(tree_ot_handle* h, cudaStream_t s) {
   c.probs = h->d_probs;
   c.ah = h->d_ah;
   c.al = h->d_al;
+  c.f = h->d_f;
+  c.Z = h->d_Z;
+  c.logg = h->d_logg;
   c.coords = h->d_coords;
   c.marg = h->d_marg;
   c.edge_tc = h->d_edge_tc;
   c.edge_mass = h->d_edge_mass;
-  CUDA_TRY(launch_check(c, s));
+  CUDA_TRY(h->fp64 ? launch_check64(c, s) : launch_check(c, s));
   h->h_marg.resize(h->vec_len);
   h->h_f.resize(h->vec_len);
   h->h_Z.resize(h->nodes.size());
@@ -571,8 +600,8 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     pd.eps = P.eps;
     pd.inv_eps = 1.0 / P.eps;
     pd.cost_scale = P.cost_kind == TREE_OT_COST_SQEUCLID ? P.cost_scale : 1.0;
-    pd.s2 = (float)(kLog2e / P.eps);
-    pd.s2_scaled = (float)(pd.cost_scale * kLog2e / P.eps);
+    split_positive(kLog2e / P.eps, &pd.s2, &pd.s2_lo);
+    split_positive(pd.cost_scale * kLog2e / P.eps, &pd.s2_scaled, &pd.s2_scaled_lo);
     pd.dim = P.cost_kind == TREE_OT_COST_SQEUCLID ? P.dim : (P.coords ? P.dim : 0);
     pd.cost_kind = P.cost_kind;
     const bool have_coords = P.coords != nullptr && pd.dim > 0;
@@ -672,6 +701,21 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
         for (int32_t s = 0; s < d.nsplit; ++s)
           tl.push_back(Task{(int32_t)di, TASK_RECOMP, o0, std::min(kRecOut, own.n - o0), s * kRecRed,
                             std::min(kRecRed, nbn.n - s * kRecRed), s, 0});
+    }
+  }
+  // group each colour's tasks by kernel slot (stored costs; recomputed costs by dimension)
+  for (int c = 0; c < 2; ++c) {
+    auto slot_of = [&](const Task& t) {
+      if (h->fp64 || t.kind != TASK_RECOMP) return 0;
+      return (int)h->probs[h->dedges[t.dedge].prob].dim;
+    };
+    std::stable_sort(h->tasks[c].begin(), h->tasks[c].end(),
+                     [&](const Task& x, const Task& y) { return slot_of(x) < slot_of(y); });
+    for (const Task& t : h->tasks[c]) h->slot_count[c][slot_of(t)] += 1;
+    int32_t b = 0;
+    for (int s2 = 0; s2 < kApplySlots; ++s2) {
+      h->slot_begin[c][s2] = b;
+      b += h->slot_count[c][s2];
     }
   }
   for (size_t j = 0; j < h->nodes.size(); ++j) {
@@ -810,7 +854,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  h->apply_grid = sms * apply_ctas_per_sm();
+  for (int slot = 0; slot < kApplySlots; ++slot) h->apply_grid[slot] = sms * apply_ctas_per_sm(slot);
   {
     cudaError_t ce = cudaStreamCreateWithFlags(&h->hstream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
@@ -970,8 +1014,8 @@ int tree_ot_set_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, i
   const double eps = h->probs[prob].eps;
   for (int32_t x = 0; x < n; ++x) v[x] += eps * z;
   CUDA_TRY(cudaMemcpyAsync(h->d_f + d.off, v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges + di, h->d_nodes, h->d_probs, 1, kLog2e, h->d_hh,
-                          h->d_hl, s));
+  CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges + di, h->d_nodes, h->d_probs, 1, kLog2e, true,
+                          h->d_hh, h->d_hl, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   h->have_check = false;
   return TREE_OT_OK;

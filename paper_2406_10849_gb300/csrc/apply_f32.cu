@@ -1,24 +1,31 @@
 // Edge apply, FP32 per-element arithmetic: one persistent launch computes the
 // partial log-sum-exp messages of every directed edge owned by the active colour
-// (Theorem 1's K_(j,k)(u_(k,j) gamma_k), in log form), in base 2:
+// (the K_(j,k)(u_(k,j) gamma_k) of the block-update theorem, in log form), in
+// base 2:
 //
 //   m2_(j,k)(x) = log2 sum_y 2^( h_(k,j)(y) - s * C(x,y) ),
-//   h_(k,j)(y)  = (f_(k,j)(y)/eps + log gamma_k(y)) * log2(e)   (two floats: hi + lo)
-//   s           = log2(e) / eps.
+//   h_(k,j)(y)  = (f_(k,j)(y)/eps + log gamma_k(y)) * log2(e),    s = log2(e)/eps.
 //
-// Each thread keeps, per output x, a frame R (an FP32 value close to the row's
-// maximum, seeded from the previous message of that row) and a sum of
-// 2^(t - R).  The per-element argument t = (hh - R) + hl - s*C stays small for
-// the terms that matter, so FP32 rounding of large potentials never enters.
-// A chunk whose maximum exceeds the frame (or lies far below it) moves the
-// frame.  Results are written as (frame, sum) pairs per reduction split and
-// merged by the node-update kernel in FP64.
+// Exactness of the per-element argument.  h arrives as two floats, hh on a
+// 2^-10 grid plus a small remainder hl; every frame R (a per-output shift close
+// to the running maximum) is kept on the same grid.  hh - R is then exact, the
+// product C*s is formed inside an FMA (s itself as s_hi + s_lo), and only the
+// small final argument t = (hh - R) - C*s + hl is ever rounded.  Terms near the
+// maximum therefore carry ~1e-7 relative error however large f/eps and C/eps are.
+//
+// Frames.  A frame starts at the output's previous message.  A chunk whose
+// maximum lies above the frame, or (when nothing has been accumulated yet) far
+// below it, moves the frame to the quantised chunk maximum and the chunk's terms
+// are recomputed from the new frame.  Results are (frame, sum) pairs per
+// reduction split; the node update merges them, ignoring empty pieces.
 //
 // Task kinds: ROW (stored matrix, reduce along a contiguous row: one warp per
-// row, lanes across 1024 columns), COL (stored matrix, reduce down columns: a
-// warp owns 128 columns, 8 warps split the rows, merged through shared
-// memory), RECOMP (squared-Euclidean cost recomputed from coordinates: each
-// thread owns 4 outputs, reduction points are staged in shared memory).
+// row with a warp-uniform frame, lanes across 1024 columns), COL (stored matrix,
+// reduce down columns: a warp owns 128 columns, 8 warps split the rows and merge
+// through shared memory) -- both in apply_dense_kernel, where each term is formed
+// twice (maximum first, then the sum) so no term array stays live -- and RECOMP
+// (squared-Euclidean cost recomputed from coordinates: each thread owns 4
+// outputs, reduction points staged in shared memory) in apply_recomp_kernel<D>.
 #include <cfloat>
 #include <cmath>
 
@@ -30,19 +37,22 @@ namespace treeot {
 namespace {
 
 #define kInf (__int_as_float(0x7f800000))
+constexpr float kWindow = 12.f;   // a frame up to this far above the chunk maximum is kept
 
-// shift all terms of a thread's chunk when its maximum leaves the frame
-__device__ __forceinline__ void maybe_reframe(float cm, float& R, float* t, int cnt) {
-  if ((cm > 0.f || cm < -64.f) && cm > -kInf) {
-    R += cm;
-    for (int i = 0; i < cnt; ++i) t[i] -= cm;
-  }
+__device__ __forceinline__ float quant(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
+
+// t = (hh - R) - c*s + hl, s = s_hi + s_lo
+__device__ __forceinline__ float arg1(float hh, float R, float c, float shi, float slo, float hl) {
+  float t = fmaf(-c, shi, hh - R);
+  t = fmaf(-c, slo, t);
+  return t + hl;
 }
 
 __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const EdgeD e = A.edges[d.edge];
-  const float s = A.probs[d.prob].s2;
+  const ProbD P = A.probs[d.prob];
+  const float shi = P.s2, slo = P.s2_lo;
   const int n_owner = e.na;
   float* sh = sm;
   float* sl = sm + kRowCols;
@@ -57,7 +67,7 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const int nvec = (t.rcount + 3) >> 2;
   const float4* sh4 = reinterpret_cast<const float4*>(sh);
   const float4* sl4 = reinterpret_cast<const float4*>(sl);
-  const float2 negs = make_float2(-s, -s);
+  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
   for (int r = warp; r < t.ocount; r += kApplyThreads / 32) {
     const int x = t.o0 + r;
     const float4* row = reinterpret_cast<const float4*>(e.C + (int64_t)x * e.ld + t.r0);
@@ -67,48 +77,67 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
       const int v = lane + 32 * i;
       c[i] = v < nvec ? ldg_stream(row + v) : make_float4(kInf, kInf, kInf, kInf);
     }
-    float R = frame_of(A.m[d.off + x]);
-    const float2 negR = make_float2(-R, -R);
-    float tv[32];
+    float R = quant(frame_of(A.m[d.off + x]));  // warp-uniform
+    // pass 1: maximum of the terms relative to the current frame
     float cm = -kInf;
+    {
+      const float2 negR = make_float2(-R, -R);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int v = lane + 32 * i;
-      const float4 H = sh4[v];
-      const float4 L = sl4[v];
-      const float2 d01 = add2(add2(make_float2(H.x, H.y), negR), make_float2(L.x, L.y));
-      const float2 d23 = add2(add2(make_float2(H.z, H.w), negR), make_float2(L.z, L.w));
-      const float2 t01 = fma2(make_float2(c[i].x, c[i].y), negs, d01);
-      const float2 t23 = fma2(make_float2(c[i].z, c[i].w), negs, d23);
-      tv[4 * i + 0] = t01.x;
-      tv[4 * i + 1] = t01.y;
-      tv[4 * i + 2] = t23.x;
-      tv[4 * i + 3] = t23.y;
-      cm = max3f(cm, t01.x, t01.y);
-      cm = max3f(cm, t23.x, t23.y);
+      for (int i = 0; i < 8; ++i) {
+        const int v = lane + 32 * i;
+        const float4 H = sh4[v];
+        const float4 L = sl4[v];
+        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(make_float2(H.x, H.y), negR));
+        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(make_float2(H.z, H.w), negR));
+        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), make_float2(L.x, L.y));
+        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), make_float2(L.z, L.w));
+        cm = max3f(cm, t01.x, t01.y);
+        cm = max3f(cm, t23.x, t23.y);
+      }
     }
-    maybe_reframe(cm, R, tv, 32);
-    // pairwise sum of the 32 terms
-    float p[16];
+    const float cw = warp_max(cm);
+    if ((cw > 0.5f || cw < -kWindow) && cw > -kInf) R += quant(cw);  // warp-uniform move onto the grid
+    // pass 2: the terms from the final frame, pairwise-summed
+    float acc = 0.f;
+    {
+      const float2 negR = make_float2(-R, -R);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) p[i] = ex2(tv[2 * i]) + ex2(tv[2 * i + 1]);
-#pragma unroll
-    for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-      for (int i = 0; i < w; ++i) p[i] += p[i + w];
-    float acc = p[0];
-    const float Rm = warp_max(R);
-    acc = (R == Rm) ? acc : acc * ex2(R - Rm);
+      for (int i = 0; i < 8; ++i) {
+        const int v = lane + 32 * i;
+        const float4 H = sh4[v];
+        const float4 L = sl4[v];
+        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(make_float2(H.x, H.y), negR));
+        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(make_float2(H.z, H.w), negR));
+        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), make_float2(L.x, L.y));
+        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), make_float2(L.z, L.w));
+        acc += (ex2(t01.x) + ex2(t01.y)) + (ex2(t23.x) + ex2(t23.y));
+      }
+    }
     acc = warp_sum(acc);
-    if (lane == 0) A.part32[d.part_off + (int64_t)t.split * n_owner + x] = make_float2(Rm, acc);
+    if (lane == 0) A.part32[d.part_off + (int64_t)t.split * n_owner + x] = make_float2(R, acc);
   }
   __syncthreads();
+}
+
+// merge (frame, sum) pieces, skipping empty ones; result written as one piece
+__device__ __forceinline__ float2 merge_pieces(const float2* p, int n, int stride) {
+  float Rm = -kInf;
+  for (int w = 0; w < n; ++w)
+    if (p[w * stride].y > 0.f) Rm = fmaxf(Rm, p[w * stride].x);
+  if (Rm == -kInf) return make_float2(0.f, 0.f);
+  float S = 0.f;
+  for (int w = 0; w < n; ++w) {
+    const float2 q = p[w * stride];
+    if (q.y > 0.f) S += (q.x == Rm) ? q.y : q.y * ex2(q.x - Rm);
+  }
+  return make_float2(Rm, S);
 }
 
 __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const EdgeD e = A.edges[d.edge];
-  const float s = A.probs[d.prob].s2;
+  const ProbD P = A.probs[d.prob];
+  const float shi = P.s2, slo = P.s2_lo;
   const int n_owner = e.nb;
   float* sh = sm;
   float* sl = sm + kColRows;
@@ -124,88 +153,111 @@ __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
   const int rpw = (t.rcount + 7) / 8;
   const int rr0 = warp * rpw;
   const int rr1 = min(rr0 + rpw, t.rcount);
-  const int c0 = 4 * lane;                      // first of this lane's 4 columns (task-relative)
+  const int c0 = 4 * lane;  // first of this lane's 4 columns (task-relative)
   const bool lane_on = c0 < t.ocount;
   float R[4], acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int col = t.o0 + c0 + k;
-    R[k] = (lane_on && c0 + k < t.ocount) ? frame_of(A.m[d.off + col]) : 0.f;
+    R[k] = (lane_on && c0 + k < t.ocount) ? quant(frame_of(A.m[d.off + t.o0 + c0 + k])) : 0.f;
     acc[k] = 0.f;
   }
-  const float2 negs = make_float2(-s, -s);
+  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
   const float* base = e.C + t.o0 + c0;
   for (int rr = rr0; rr < rr1; rr += 8) {
     float4 c[8];
+    float hh[8], hl[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int xr = rr + i;
-      c[i] = (lane_on && xr < rr1)
-                 ? ldg_stream(reinterpret_cast<const float4*>(base + (int64_t)(t.r0 + xr) * e.ld))
-                 : make_float4(kInf, kInf, kInf, kInf);
+      const bool ok = xr < rr1;
+      c[i] = (lane_on && ok) ? ldg_stream(reinterpret_cast<const float4*>(base + (int64_t)(t.r0 + xr) * e.ld))
+                             : make_float4(kInf, kInf, kInf, kInf);
+      hh[i] = ok ? sh[xr] : 0.f;
+      hl[i] = ok ? sl[xr] : 0.f;
     }
-    float tv[4][8];
-    const float2 nR01 = make_float2(-R[0], -R[1]);
-    const float2 nR23 = make_float2(-R[2], -R[3]);
+    // pass 1: per-column maximum of this chunk relative to the current frames
+    float cm[4] = {-kInf, -kInf, -kInf, -kInf};
+    {
+      const float2 nR01 = make_float2(-R[0], -R[1]);
+      const float2 nR23 = make_float2(-R[2], -R[3]);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int xr = min(rr + i, kColRows - 1);
-      const float hh = sh[xr], hl = sl[xr];
-      const float2 d01 = add2(add2(make_float2(hh, hh), nR01), make_float2(hl, hl));
-      const float2 d23 = add2(add2(make_float2(hh, hh), nR23), make_float2(hl, hl));
-      const float2 t01 = fma2(make_float2(c[i].x, c[i].y), negs, d01);
-      const float2 t23 = fma2(make_float2(c[i].z, c[i].w), negs, d23);
-      tv[0][i] = t01.x;
-      tv[1][i] = t01.y;
-      tv[2][i] = t23.x;
-      tv[3][i] = t23.y;
+      for (int i = 0; i < 8; ++i) {
+        const float2 h2 = make_float2(hh[i], hh[i]), l2 = make_float2(hl[i], hl[i]);
+        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(h2, nR01));
+        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(h2, nR23));
+        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), l2);
+        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), l2);
+        cm[0] = fmaxf(cm[0], t01.x);
+        cm[1] = fmaxf(cm[1], t01.y);
+        cm[2] = fmaxf(cm[2], t23.x);
+        cm[3] = fmaxf(cm[3], t23.y);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      float cm = max3f(tv[k][0], tv[k][1], tv[k][2]);
-      cm = max3f(cm, tv[k][3], tv[k][4]);
-      cm = max3f(cm, tv[k][5], tv[k][6]);
-      cm = fmaxf(cm, tv[k][7]);
-      if ((cm > 0.f || (acc[k] == 0.f && cm < -64.f)) && cm > -kInf) {
-        acc[k] *= ex2(-cm);
-        R[k] += cm;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) tv[k][i] -= cm;
+      if ((cm[k] > 0.5f || (acc[k] == 0.f && cm[k] < -kWindow)) && cm[k] > -kInf) {
+        const float Rn = R[k] + quant(cm[k]);
+        acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
+        R[k] = Rn;
       }
-      const float a = (ex2(tv[k][0]) + ex2(tv[k][1])) + (ex2(tv[k][2]) + ex2(tv[k][3]));
-      const float b = (ex2(tv[k][4]) + ex2(tv[k][5])) + (ex2(tv[k][6]) + ex2(tv[k][7]));
-      acc[k] += a + b;
+    }
+    // pass 2: terms from the (possibly moved) frames
+    {
+      const float2 nR01 = make_float2(-R[0], -R[1]);
+      const float2 nR23 = make_float2(-R[2], -R[3]);
+      float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float2 h2 = make_float2(hh[i], hh[i]), l2 = make_float2(hl[i], hl[i]);
+        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(h2, nR01));
+        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(h2, nR23));
+        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), l2);
+        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), l2);
+        a01 = add2(a01, make_float2(ex2(t01.x), ex2(t01.y)));
+        a23 = add2(a23, make_float2(ex2(t23.x), ex2(t23.y)));
+      }
+      acc[0] += a01.x;
+      acc[1] += a01.y;
+      acc[2] += a23.x;
+      acc[3] += a23.y;
     }
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) comb[warp * kColCols + c0 + k] = make_float2(R[k], acc[k]);
   __syncthreads();
-  for (int c = tid; c < t.ocount; c += kApplyThreads) {
-    float Rm = -kInf;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) Rm = fmaxf(Rm, comb[w * kColCols + c].x);
-    float S = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const float2 p = comb[w * kColCols + c];
-      S += (p.x == Rm) ? p.y : p.y * ex2(p.x - Rm);
-    }
-    A.part32[d.part_off + (int64_t)t.split * n_owner + t.o0 + c] = make_float2(Rm, S);
-  }
+  for (int c = tid; c < t.ocount; c += kApplyThreads)
+    A.part32[d.part_off + (int64_t)t.split * n_owner + t.o0 + c] = merge_pieces(comb + c, 8, kColCols);
   __syncthreads();
 }
 
 // squared Euclidean cost from coordinates; D in {1,2,3}
 template <int D>
+__device__ __forceinline__ float sqdist(float px, float py, float pz, float4 q) {
+  // q holds the negated coordinates of the reduction point
+  const float dx = px + q.x;
+  float c = dx * dx;
+  if (D > 1) {
+    const float dy = py + q.y;
+    c = fmaf(dy, dy, c);
+  }
+  if (D > 2) {
+    const float dz = pz + q.z;
+    c = fmaf(dz, dz, c);
+  }
+  return c;
+}
+
+template <int D>
 __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const NodeD own = A.nodes[d.owner];
   const NodeD nbn = A.nodes[d.nbr];
-  const float s = A.probs[d.prob].s2_scaled;
+  const ProbD P = A.probs[d.prob];
+  const float shi = P.s2_scaled, slo = P.s2_scaled_lo;
   const int n_owner = own.n;
   const int tid = threadIdx.x;
-  float4* st = reinterpret_cast<float4*>(sm);           // [256]: (-q0, -q1, -q2 or hh, hh or hl)
-  float* stl = sm + 4 * kApplyThreads;                  // [256]: hl (D == 3)
+  float4* st = reinterpret_cast<float4*>(sm);  // [256]: (-q0, -q1, -q2 or hh, hh or hl)
+  float* stl = sm + 4 * kApplyThreads;         // [256]: hl (D == 3)
   float px[4], py[4], pz[4], R[4], acc[4];
   bool on[4];
 #pragma unroll
@@ -217,10 +269,13 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
     px[i] = p[0];
     py[i] = D > 1 ? p[1] : 0.f;
     pz[i] = D > 2 ? p[2] : 0.f;
-    R[i] = on[i] ? frame_of(A.m[d.off + o]) : 0.f;
+    R[i] = on[i] ? quant(frame_of(A.m[d.off + o])) : 0.f;
     acc[i] = 0.f;
   }
-  const float2 negs = make_float2(-s, -s);
+  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
+  const float2 px01 = make_float2(px[0], px[1]), px23 = make_float2(px[2], px[3]);
+  const float2 py01 = make_float2(py[0], py[1]), py23 = make_float2(py[2], py[3]);
+  const float2 pz01 = make_float2(pz[0], pz[1]), pz23 = make_float2(pz[2], pz[3]);
   for (int ch = 0; ch < t.rcount; ch += kApplyThreads) {
     __syncthreads();
     {
@@ -239,24 +294,15 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
     }
     __syncthreads();
     const int cnt = min(kApplyThreads, t.rcount - ch);
-    const float2 nR01 = make_float2(-R[0], -R[1]);
-    const float2 nR23 = make_float2(-R[2], -R[3]);
-    const float2 px01 = make_float2(px[0], px[1]), px23 = make_float2(px[2], px[3]);
-    const float2 py01 = make_float2(py[0], py[1]), py23 = make_float2(py[2], py[3]);
-    const float2 pz01 = make_float2(pz[0], pz[1]), pz23 = make_float2(pz[2], pz[3]);
     for (int j = 0; j < cnt; j += 8) {
       float tv[4][8];
+      const float2 nR01 = make_float2(-R[0], -R[1]);
+      const float2 nR23 = make_float2(-R[2], -R[3]);
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const float4 q = st[j + jj];       // entries past cnt hold hh = -inf: zero terms
-        float hh, hl;
-        if (D == 3) {
-          hh = q.w;
-          hl = stl[j + jj];
-        } else {
-          hh = q.z;
-          hl = q.w;
-        }
+        const float4 q = st[j + jj];  // entries past cnt hold hh = -inf: zero terms
+        const float hh = D == 3 ? q.w : q.z;
+        const float hl = D == 3 ? stl[j + jj] : q.w;
         const float2 qx = make_float2(q.x, q.x);
         float2 c01, c23;
         {
@@ -276,11 +322,11 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
           c01 = fma2(dz01, dz01, c01);
           c23 = fma2(dz23, dz23, c23);
         }
-        const float2 hh2 = make_float2(hh, hh), hl2 = make_float2(hl, hl);
-        const float2 d01 = add2(add2(hh2, nR01), hl2);
-        const float2 d23 = add2(add2(hh2, nR23), hl2);
-        const float2 t01 = fma2(c01, negs, d01);
-        const float2 t23 = fma2(c23, negs, d23);
+        const float2 h2 = make_float2(hh, hh), l2 = make_float2(hl, hl);
+        float2 t01 = fma2(c01, nhi, add2(h2, nR01));
+        float2 t23 = fma2(c23, nhi, add2(h2, nR23));
+        t01 = add2(fma2(c01, nlo, t01), l2);
+        t23 = add2(fma2(c23, nlo, t23), l2);
         tv[0][jj] = t01.x;
         tv[1][jj] = t01.y;
         tv[2][jj] = t23.x;
@@ -292,18 +338,23 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
         cm = max3f(cm, tv[k][3], tv[k][4]);
         cm = max3f(cm, tv[k][5], tv[k][6]);
         cm = fmaxf(cm, tv[k][7]);
-        if ((cm > 0.f || (acc[k] == 0.f && cm < -64.f)) && cm > -kInf) {
-          acc[k] *= ex2(-cm);
-          R[k] += cm;
+        if ((cm > 0.5f || (acc[k] == 0.f && cm < -kWindow)) && cm > -kInf) {
+          const float Rn = R[k] + quant(cm);
+          acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
+          R[k] = Rn;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) tv[k][i] -= cm;
+          for (int jj = 0; jj < 8; ++jj) {
+            const float4 q = st[j + jj];
+            const float hh = D == 3 ? q.w : q.z;
+            const float hl = D == 3 ? stl[j + jj] : q.w;
+            tv[k][jj] = arg1(hh, Rn, sqdist<D>(px[k], py[k], pz[k], q), shi, slo, hl);
+          }
         }
         const float a = (ex2(tv[k][0]) + ex2(tv[k][1])) + (ex2(tv[k][2]) + ex2(tv[k][3]));
         const float b = (ex2(tv[k][4]) + ex2(tv[k][5])) + (ex2(tv[k][6]) + ex2(tv[k][7]));
         acc[k] += a + b;
       }
     }
-    // frames may have moved: the next chunk re-reads R
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -314,44 +365,54 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
   }
 }
 
-__global__ void __launch_bounds__(kApplyThreads, 2) apply_f32_kernel(ApplyArgs A) {
-  __shared__ __align__(16) float sm[2 * kColRows + 2 * 8 * kColCols];  // 12 KB, covers all task kinds
+__global__ void __launch_bounds__(kApplyThreads, 2) apply_dense_kernel(ApplyArgs A) {
+  __shared__ __align__(16) float sm[2 * kColRows + 2 * 8 * kColCols];  // 12 KB
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
-    const int prob = A.dedges[t.dedge].prob;
-    if (A.done[prob]) continue;
-    switch (t.kind) {
-      case TASK_ROW:
-        row_task(A, t, sm);
-        break;
-      case TASK_COL:
-        col_task(A, t, sm);
-        break;
-      default: {
-        const int D = A.probs[prob].dim;
-        if (D == 1)
-          recomp_task<1>(A, t, sm);
-        else if (D == 2)
-          recomp_task<2>(A, t, sm);
-        else
-          recomp_task<3>(A, t, sm);
-        __syncthreads();
-      }
-    }
+    if (A.done[A.dedges[t.dedge].prob]) continue;
+    if (t.kind == TASK_ROW)
+      row_task(A, t, sm);
+    else
+      col_task(A, t, sm);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kApplyThreads, 2) apply_recomp_kernel(ApplyArgs A) {
+  __shared__ __align__(16) float sm[5 * kApplyThreads];  // 5 KB
+  for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
+    const Task t = A.tasks[ti];
+    if (A.done[A.dedges[t.dedge].prob]) continue;
+    recomp_task<D>(A, t, sm);
+    __syncthreads();
   }
 }
 
 }  // namespace
 
-int apply_ctas_per_sm() {
+int apply_ctas_per_sm(int slot) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_f32_kernel, kApplyThreads, 0);
+  if (slot == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_dense_kernel, kApplyThreads, 0);
+  else if (slot == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<1>, kApplyThreads, 0);
+  else if (slot == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<2>, kApplyThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<3>, kApplyThreads, 0);
   return n > 0 ? n : 1;
 }
 
-cudaError_t launch_apply_f32(const ApplyArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int grid, cudaStream_t s) {
   if (a.ntasks <= 0) return cudaSuccess;
-  apply_f32_kernel<<<grid, kApplyThreads, 0, s>>>(a);
+  if (slot == 0)
+    apply_dense_kernel<<<grid, kApplyThreads, 0, s>>>(a);
+  else if (slot == 1)
+    apply_recomp_kernel<1><<<grid, kApplyThreads, 0, s>>>(a);
+  else if (slot == 2)
+    apply_recomp_kernel<2><<<grid, kApplyThreads, 0, s>>>(a);
+  else
+    apply_recomp_kernel<3><<<grid, kApplyThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

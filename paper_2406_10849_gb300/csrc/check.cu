@@ -160,11 +160,74 @@ __global__ void __launch_bounds__(256) check_kernel(CheckArgs A) {
   }
 }
 
+// FP64 version of the check for FP64 handles (small problems): every plan entry
+// exp(a + b - C/eps) in double precision.
+__device__ __forceinline__ double a64(const CheckArgs& A, const DEdgeD& d, const NodeD& own, double inv_eps,
+                                      int64_t off, int x) {
+  const double lg = A.logg[own.node_off + x];
+  if (lg == -INFINITY) return -INFINITY;
+  return A.f[off + x] * inv_eps - A.Z[d.owner] + lg;
+}
+
+__global__ void __launch_bounds__(256) check64_kernel(CheckArgs A) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
+    const Task t = A.tasks[ti];
+    const DEdgeD d = A.dedges[t.dedge];
+    const EdgeD e = A.edges[d.edge];
+    const ProbD P = A.probs[d.prob];
+    const NodeD na = A.nodes[e.a], nb = A.nodes[e.b];
+    const DEdgeD dr = A.dedges[t.dedge ^ 1];
+    const DEdgeD& da = d.dir == 0 ? d : dr;   // owner a (rows)
+    const DEdgeD& db = d.dir == 0 ? dr : d;   // owner b (columns)
+    const int D = P.dim;
+    // output index i of this task's owner; the other side is reduced
+    for (int r = warp; r < t.ocount; r += 8) {
+      const int i = t.o0 + r;
+      double sum = 0.0, tc = 0.0;
+      const int nother = t.kind == TASK_ROW ? e.nb : e.na;
+      const double ai = t.kind == TASK_ROW ? a64(A, da, na, P.inv_eps, da.off, i) : a64(A, db, nb, P.inv_eps, db.off, i);
+      if (ai > -INFINITY) {
+        for (int j = lane; j < nother; j += 32) {
+          const int x = t.kind == TASK_ROW ? i : j;
+          const int y = t.kind == TASK_ROW ? j : i;
+          const double bj = t.kind == TASK_ROW ? a64(A, db, nb, P.inv_eps, db.off, y) : a64(A, da, na, P.inv_eps, da.off, x);
+          if (!(bj > -INFINITY)) continue;
+          double C;
+          if (P.cost_kind == 0) {
+            C = (double)e.C[(int64_t)x * e.ld + y];
+          } else {
+            C = 0.0;
+            for (int k = 0; k < D; ++k) {
+              const double dd = (double)A.coords[na.coord_off + (int64_t)x * D + k] -
+                                (double)A.coords[nb.coord_off + (int64_t)y * D + k];
+              C += dd * dd;
+            }
+            C *= P.cost_scale;
+          }
+          const double B = exp(ai + bj - C * P.inv_eps);
+          sum += B;
+          tc += B * C;
+        }
+      }
+      sum = warp_sum_d(sum);
+      tc = warp_sum_d(tc);
+      if (lane == 0) {
+        A.marg[d.off + i] = sum;
+        if (t.kind == TASK_ROW) {
+          atomicAdd(&A.edge_tc[d.edge], tc);
+          atomicAdd(&A.edge_mass[d.edge], sum);
+        }
+      }
+    }
+  }
+}
+
 // v = (f'/eps - Z_owner + log gamma_owner) * scale, split into FP32 (hi, lo), per
 // directed-edge entry.  Z may be null (the apply operand leaves Z out).
 __global__ void operand_kernel(const double* f, const double* Z, const double* logg, const DEdgeD* dedges,
                                const NodeD* nodes, const ProbD* probs, int32_t d0, int32_t ndedges, double scale,
-                               float* vh, float* vl) {
+                               bool quantize, float* vh, float* vl) {
   const int di = d0 + blockIdx.y;
   if (di >= ndedges) return;
   const DEdgeD d = dedges[di];
@@ -174,7 +237,7 @@ __global__ void operand_kernel(const double* f, const double* Z, const double* l
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nd.n; x += gridDim.x * blockDim.x) {
     const double lg = logg[nd.node_off + x];
     const double a = (f[d.off + x] * inv_eps - z + lg) * scale;
-    const float hi = (float)a;
+    const float hi = quantize ? (float)(rint(a * kGrid) / kGrid) : (float)a;
     vh[d.off + x] = (lg == -INFINITY) ? -INFINITY : hi;
     vl[d.off + x] = isfinite(a) ? (float)(a - (double)hi) : 0.f;
   }
@@ -205,6 +268,12 @@ __global__ void pad_copy_kernel(const float* src, int64_t src_ld, float* dst, in
 
 }  // namespace
 
+cudaError_t launch_check64(const CheckArgs& a, cudaStream_t s) {
+  if (a.ntasks <= 0) return cudaSuccess;
+  check64_kernel<<<a.ntasks < 1024 ? a.ntasks : 1024, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check(const CheckArgs& a, cudaStream_t s) {
   if (a.ntasks <= 0) return cudaSuccess;
   int dev = 0, sms = 0;
@@ -216,12 +285,12 @@ cudaError_t launch_check(const CheckArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_operand(const double* f, const double* Z, const double* logg, const DEdgeD* dedges,
-                           const NodeD* nodes, const ProbD* probs, int32_t ndedges, double scale, float* vh, float* vl,
-                           cudaStream_t s) {
+                           const NodeD* nodes, const ProbD* probs, int32_t ndedges, double scale, bool quantize,
+                           float* vh, float* vl, cudaStream_t s) {
   for (int32_t d0 = 0; d0 < ndedges; d0 += 65535) {
     const int32_t cnt = ndedges - d0 < 65535 ? ndedges - d0 : 65535;
     dim3 grid(4, cnt);
-    operand_kernel<<<grid, 256, 0, s>>>(f, Z, logg, dedges, nodes, probs, d0, ndedges, scale, vh, vl);
+    operand_kernel<<<grid, 256, 0, s>>>(f, Z, logg, dedges, nodes, probs, d0, ndedges, scale, quantize, vh, vl);
   }
   return cudaGetLastError();
 }

@@ -5,9 +5,9 @@
 // j and carries the potential f_(j,k) = eps log u_(j,k) (length n_j).  The
 // "message" of that directed edge is
 //     m_(j,k)(x) = LSE_y [ (f_(k,j)(y) - C_(j,k)(x,y)) / eps + log gamma_k(y) ],
-// the log of K_(j,k)(u_(k,j) gamma_k) that Theorem 1's updates divide by.  A
+// the log of K_(j,k)(u_(k,j) gamma_k) that the block updates (thm:tree_dual_var) divide by.  A
 // half-step on colour c computes the messages of every directed edge whose
-// owner has colour c (edge apply), then applies Theorem 1 at those owners
+// owner has colour c (edge apply), then applies those updates at the owners
 // (node update).
 #pragma once
 #include <cstdint>
@@ -27,6 +27,7 @@ constexpr int kRecOut = 1024;          // RECOMP task: outputs per task (256 thr
 constexpr int kRecRed = 512;           // RECOMP task: reduction points per task
 constexpr int kNodeThreads = 256;
 constexpr int kNodeChunk = 512;        // node update: support points per CTA
+constexpr double kGrid = 1024.0;       // apply operands and frames live on a 2^-10 grid
 
 enum TaskKind : int32_t {
   TASK_ROW = 0,     // stored matrix, owner is the row node: reduce along a row
@@ -69,8 +70,8 @@ struct NodeChunk {
 struct ProbD {
   double eps, inv_eps;
   double cost_scale;
-  float s2;          // log2(e) / eps, rounded to FP32
-  float s2_scaled;   // cost_scale * log2(e) / eps (recompute)
+  float s2, s2_lo;                 // log2(e) / eps as a two-float (hi + lo)
+  float s2_scaled, s2_scaled_lo;   // cost_scale * log2(e) / eps (recompute), two-float
   int32_t dim;
   int32_t cost_kind;
   int32_t nodes_in_colour[2];
@@ -103,7 +104,7 @@ struct ApplyArgs {
 
 // Potentials are stored in a normalised form: f[d] holds f'_(j,k) with the
 // free-node constant split off, f_(j,k) = f'_(j,k) - eps * Z[j] (Z = 0 for
-// fixed nodes), where Z_j = LSE_x s_j(x) and rho_j = -|N(j)| Z_j (Theorem 1).
+// fixed nodes), where Z_j = LSE_x s_j(x) and rho_j = -|N(j)| Z_j (thm:tree_dual_var).
 // h[d] = (f'/eps + log gamma_owner) * log2(e); the apply therefore returns the
 // message plus Z of the neighbour, which the node update subtracts.
 struct NodeArgs {
@@ -156,6 +157,9 @@ struct CheckArgs {
   const ProbD* probs;
   const float* ah;     // per directed edge: a = f/eps + log gamma_owner, high FP32 part
   const float* al;     // low part
+  const double* f;     // FP64 check: potentials f' (with Z and log gamma read directly)
+  const double* Z;
+  const double* logg;
   const float* coords;
   double* marg;        // per directed edge: B 1 on the owner's side (layout of f)
   double* edge_tc;     // per edge sum C B
@@ -163,18 +167,22 @@ struct CheckArgs {
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
-cudaError_t launch_apply_f32(const ApplyArgs& a, int grid, cudaStream_t s);
+// slot 0: stored-cost tasks (ROW/COL); slot D (1..3): recomputed squared-Euclidean tasks
+cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int grid, cudaStream_t s);
 cudaError_t launch_apply_f64(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s);
-// v = (f'/eps - Z_owner + log gamma) * scale as FP32 (hi, lo); Z may be null
+// v = (f'/eps - Z_owner + log gamma) * scale as FP32 (hi, lo); Z may be null.
+// quantize: hi on the 2^-10 grid (the apply operand), else hi = nearest float.
 cudaError_t launch_operand(const double* f, const double* Z, const double* logg, const DEdgeD* dedges,
-                           const NodeD* nodes, const ProbD* probs, int32_t ndedges, double scale, float* vh, float* vl,
-                           cudaStream_t s);
+                           const NodeD* nodes, const ProbD* probs, int32_t ndedges, double scale, bool quantize,
+                           float* vh, float* vl, cudaStream_t s);
+cudaError_t launch_check64(const CheckArgs& a, cudaStream_t s);
 cudaError_t launch_scan_cost(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad, cudaStream_t s);
 cudaError_t launch_check(const CheckArgs& a, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
 cudaError_t launch_pad_copy(const float* src, int64_t src_ld, float* dst, int64_t dst_ld, int32_t rows,
                             int32_t cols, cudaStream_t s);
-int apply_ctas_per_sm();
+int apply_ctas_per_sm(int slot);
+constexpr int kApplySlots = 4;
 
 }  // namespace treeot

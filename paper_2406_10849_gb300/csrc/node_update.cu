@@ -1,4 +1,4 @@
-// Node update of one half-step (Theorem 1, thm:tree_dual_var, in log form),
+// Node update of one half-step (the block-update theorem thm:tree_dual_var, in log form),
 // fused with the stopping terms of the Bipartite Iterative Scaling algorithm.
 //
 // One CTA handles a chunk of up to kNodeChunk support points of one node j of
@@ -25,15 +25,20 @@
 namespace treeot {
 namespace {
 
+// merge the apply's (frame, sum) pieces of one output; empty pieces (sum 0) carry no frame
 __device__ __forceinline__ double merge32(const float2* part, int nsplit, int64_t stride) {
   float Rm = -INFINITY;
-  for (int p = 0; p < nsplit; ++p) Rm = fmaxf(Rm, part[p * stride].x);
+  for (int p = 0; p < nsplit; ++p) {
+    const float2 v = part[p * stride];
+    if (v.y > 0.f) Rm = fmaxf(Rm, v.x);
+  }
+  if (Rm == -INFINITY) return -INFINITY;
   float S = 0.f;
   for (int p = 0; p < nsplit; ++p) {
     const float2 v = part[p * stride];
-    S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
+    if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
   }
-  if (!(S > 0.f) || !isfinite(S) || !isfinite(Rm)) return (S > 0.f) ? INFINITY : -INFINITY;
+  if (!isfinite(S) || !(S > 0.f)) return (S > 0.f) ? INFINITY : -INFINITY;
   int e;
   const float mant = frexpf(S, &e);  // S = mant * 2^e, mant in [0.5, 1)
   return ((double)Rm + (double)e) * kLn2 + (double)logf(mant);
@@ -58,9 +63,15 @@ __device__ __forceinline__ double expx(double a) {
   return (double)ex2((float)(a * kLog2e));
 }
 
+// two-float split of an apply operand: hi on the 2^-10 grid, lo the (small) rest
 __device__ __forceinline__ void split2(double v, float& hi, float& lo) {
-  hi = (float)v;
-  lo = isfinite(v) ? (float)(v - (double)hi) : 0.f;
+  if (!isfinite(v)) {
+    hi = (float)v;
+    lo = 0.f;
+    return;
+  }
+  hi = (float)(rint(v * kGrid) / kGrid);
+  lo = (float)(v - (double)hi);
 }
 
 // block-wide sum / max of a double (kNodeThreads threads); result valid in all threads

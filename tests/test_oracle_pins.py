@@ -148,7 +148,7 @@ def test_general_optimiser_finds_same_plans(seed, J):
 
 @pytest.mark.parametrize("seed,J", [(31, 4), (32, 6)])
 def test_lp_limit_within_entropic_bound(seed, J):
-    """OPT_LP <= TC(B_eps) <= OPT_LP + 2 eps |E| log d (Lemma 6 with zero residual)."""
+    """OPT_LP <= TC(B_eps) <= OPT_LP + 2 eps |E| log d (lemma lem:round_applied with zero residual)."""
     p = random_small_tree(seed, J, nmin=3, nmax=4, eps=0.02)
     f = converged(p, tol=1e-12)
     costs = [O.cost(p, int(a), int(b)) for a, b in p.edges]
@@ -180,7 +180,7 @@ def tree_traj():
 
 
 def test_unit_mass_every_half_step(tree_traj):
-    """Lemma 3: ||B_e||_1 = 1 after every update."""
+    """Lemma cor:tree_mass: ||B_e||_1 = 1 after every update."""
     p, traj = tree_traj
     for f in traj[1:]:
         for a, b in p.edges:
@@ -188,7 +188,7 @@ def test_unit_mass_every_half_step(tree_traj):
 
 
 def test_potential_oscillation_bound(tree_traj):
-    """Lemma 4: max lambda - min lambda <= 2 C_inf on every directed edge, every iterate."""
+    """Lemma lem:tree_dual_varia_bounds: max lambda - min lambda <= 2 C_inf on every directed edge, every iterate."""
     p, traj = tree_traj
     cinf = O.c_infinity(p)
     for f in traj:
@@ -197,7 +197,8 @@ def test_potential_oscillation_bound(tree_traj):
 
 
 def test_dual_decrease_and_gap_bounds(tree_traj):
-    """Lemma 5 (f^t - f* <= 2C_inf/eps * r_t) and Lemma 6 (f^t - f^{t+1} >= r_t^2/(22|E|))."""
+    """Lemma lem:f_upper_bound_tree (f^t - f* <= 2C_inf/eps * r_t) and lemma lem:f_lower_bound_tree
+    (f^t - f^{t+1} >= r_t^2/(22|E|))."""
     p, traj = tree_traj
     fstar = O.dual_objective(p, converged(p, tol=1e-13))
     cinf = O.c_infinity(p)
@@ -213,7 +214,7 @@ def test_dual_decrease_and_gap_bounds(tree_traj):
 
 
 def test_iteration_bound():
-    """Theorem 2: r <= delta' within 2 + 88 |E| C_inf / (delta' eps) half-steps."""
+    """Theorem thm:num_iter: r <= delta' within 2 + 88 |E| C_inf / (delta' eps) half-steps."""
     p = random_small_tree(43, 6, eps=0.2)
     delta = 1e-3
     _, T, r = O.solve(p, tol=delta)
@@ -232,7 +233,7 @@ def test_primal_dual_gap_closes():
 # ---------------------------------------------------------------------------
 
 def test_listing_form_equals_closed_form():
-    """Proposition 1: the multiplicative updates of the listing equal Theorem 1 from u = 1."""
+    """Proposition cor:equi: the multiplicative updates of the listing equal thm:tree_dual_var from u = 1."""
     p = random_small_tree(51, 7, eps=0.3)
     colour = O.bipartition(p.num_nodes, p.edges)
     f = O.zero_potentials(p)
