@@ -198,6 +198,36 @@ int tree_ot_set_potentials(tree_ot_handle *h, void *cuda_stream, int32_t prob, i
  * owned by the handle, [7] node-update CTAs of colour 0, [8] of colour 1. */
 int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
+/* Allocation-free apply of one stored cost matrix (the paper has no
+ * counterpart: this is a packaging of the edge-apply kernel for callers that
+ * cannot allocate device memory -- code running while a CUDA graph is being
+ * captured, serving runtimes that own every byte of device memory through a
+ * pre-sized pool, or real-time loops that forbid the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause).
+ *
+ *   m_out[x] = log sum_{y < n_cols} exp( g[y] - cost[x * ld + y] / eps ),  x < n_rows
+ *
+ * cost: device, n_rows x ld FP32 row-major (ld >= n_cols, ld % 4 == 0, base
+ *       16-byte aligned); entries past n_cols in a row are ignored; +inf entries
+ *       contribute nothing; NaN / -inf are not allowed (not checked).
+ * g:    device, n_cols FP64 (e.g. f_(k,j)/eps + log gamma_k of the neighbour).
+ * m_out: device, n_rows FP64 (natural log; -inf where every term is zero).
+ * All three are caller-owned; the call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  Its scratch -- the two-float
+ * operand and the per-1024-column partial sums -- lives in a file-scope device
+ * array of 4 MiB that every GPU that loads the library holds until exit;
+ * requests needing more than that (2 * roundup64(n_cols) + 2 * n_rows *
+ * ceil(n_cols / 1024) floats > 2^20) are rejected with TREE_OT_ERR_ARG.
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call reuses the same array and overwrites the
+ * part it reads before reading it, so nothing needs clearing, but calls whose
+ * work overlaps on the GPU (different streams, or different host threads) race
+ * on it: serialise them.  Work is queued on cuda_stream; the call does not
+ * synchronise it. */
+int tree_ot_edge_apply_noalloc(const float *cost, int64_t ld, int32_t n_rows, int32_t n_cols, const double *g,
+                               double eps, double *m_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

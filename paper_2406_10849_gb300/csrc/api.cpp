@@ -1037,4 +1037,26 @@ int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
   return TREE_OT_OK;
 }
 
+int tree_ot_edge_apply_noalloc(const float* cost, int64_t ld, int32_t n_rows, int32_t n_cols, const double* g,
+                               double eps, double* m_out, void* cuda_stream) {
+  g_err.clear();
+  if (!cost || !g || !m_out) return fail(TREE_OT_ERR_ARG, "cost, g and m_out must be device pointers");
+  if (n_rows < 1 || n_cols < 1 || ld < n_cols || (ld % 4) != 0 || ((uintptr_t)cost % 16) != 0)
+    return fail(TREE_OT_ERR_ARG, "need n_rows, n_cols >= 1, ld >= n_cols, ld % 4 == 0 and a 16-byte aligned cost");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(TREE_OT_ERR_EPS, "eps must be positive and finite");
+  float* scratch = nullptr;
+  int64_t cap = 0;
+  CUDA_TRY(noalloc_scratch(&scratch, &cap));
+  const int64_t need = noalloc_scratch_floats_needed(n_rows, n_cols);
+  if (need > cap)
+    return fail(TREE_OT_ERR_ARG, "tree_ot_edge_apply_noalloc: " + std::to_string(n_rows) + " x " +
+                                     std::to_string(n_cols) + " needs " + std::to_string(need) +
+                                     " scratch floats, more than the fixed " + std::to_string(cap));
+  float shi, slo;
+  split_positive(kLog2e / eps, &shi, &slo);
+  CUDA_TRY(launch_edge_apply_noalloc(cost, ld, n_rows, n_cols, g, shi, slo, m_out, scratch,
+                                     (cudaStream_t)cuda_stream));
+  return TREE_OT_OK;
+}
+
 }  // extern "C"

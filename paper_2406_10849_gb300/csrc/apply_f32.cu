@@ -26,8 +26,10 @@
 // twice (maximum first, then the sum) so no term array stays live -- and RECOMP
 // (squared-Euclidean cost recomputed from coordinates: each thread owns 4
 // outputs, reduction points staged in shared memory) in apply_recomp_kernel<D>.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -388,6 +390,129 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_recomp_kernel(ApplyArg
   }
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the stored-cost row apply (see
+// tree_ot_edge_apply_noalloc in include/tree_ot.h).  Its scratch (the two-float
+// operand and the per-split partial sums) lives in one file-scope device array
+// instead of memory the caller or the library allocates.
+// ---------------------------------------------------------------------------
+
+constexpr int64_t kNoAllocScratchFloats = int64_t(1) << 20;  // 4 MiB per device
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+// h(y) = g(y) * log2(e) as a two-float (hi on the 2^-10 grid); y < n_cols
+__global__ void noalloc_operand_kernel(const double* g, int32_t n_cols, float* hh, float* hl) {
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n_cols; y += gridDim.x * blockDim.x) {
+    const double v = g[y] * 1.4426950408889634074;
+    if (!isfinite(v)) {
+      hh[y] = (float)v;
+      hl[y] = 0.f;
+    } else {
+      const float hi = (float)(rint(v * 1024.0) / 1024.0);
+      hh[y] = hi;
+      hl[y] = (float)(v - (double)hi);
+    }
+  }
+}
+
+// one CTA per (64-row block, 1024-column split); a warp per row, frame found
+// by a max pass over the register-resident costs, then the sum pass
+__global__ void __launch_bounds__(kApplyThreads) noalloc_row_kernel(const float* C, int64_t ld, int32_t n_rows,
+                                                                    int32_t n_cols, const float* hh_g,
+                                                                    const float* hl_g, float shi, float slo,
+                                                                    int32_t nsplit, float2* part) {
+  __shared__ __align__(16) float sh[kRowCols];
+  __shared__ __align__(16) float sl[kRowCols];
+  const int split = blockIdx.x % nsplit;
+  const int o0 = (blockIdx.x / nsplit) * (8 * kRowRowsPerWarp);
+  const int r0 = split * kRowCols;
+  const int rcount = min(kRowCols, n_cols - r0);
+  const int ocount = min(8 * kRowRowsPerWarp, n_rows - o0);
+  for (int i = threadIdx.x; i < kRowCols; i += kApplyThreads) {
+    const bool v = i < rcount;
+    sh[i] = v ? hh_g[r0 + i] : 0.f;
+    sl[i] = v ? hl_g[r0 + i] : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4* sh4 = reinterpret_cast<const float4*>(sh);
+  const float4* sl4 = reinterpret_cast<const float4*>(sl);
+  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
+  const int nvec = (rcount + 3) >> 2;
+  for (int r = warp; r < ocount; r += kApplyThreads / 32) {
+    const int x = o0 + r;
+    const float* rowp = C + (int64_t)x * ld + r0;
+    float4 c[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int v = lane + 32 * i;
+      if (v < nvec) {
+        c[i] = ldg_stream(reinterpret_cast<const float4*>(rowp) + v);
+        // columns past n_cols belong to the caller's row padding: no term
+        const int y = 4 * v;
+        if (y + 0 >= rcount) c[i].x = kInf;
+        if (y + 1 >= rcount) c[i].y = kInf;
+        if (y + 2 >= rcount) c[i].z = kInf;
+        if (y + 3 >= rcount) c[i].w = kInf;
+      } else {
+        c[i] = make_float4(kInf, kInf, kInf, kInf);
+      }
+    }
+    float R = 0.f;
+    float cm = -kInf;
+    for (int pass = 0; pass < 2; ++pass) {
+      const float2 negR = make_float2(-R, -R);
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int v = lane + 32 * i;
+        const float4 H = sh4[v];
+        const float4 L = sl4[v];
+        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(make_float2(H.x, H.y), negR));
+        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(make_float2(H.z, H.w), negR));
+        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), make_float2(L.x, L.y));
+        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), make_float2(L.z, L.w));
+        if (pass == 0) {
+          cm = max3f(cm, t01.x, t01.y);
+          cm = max3f(cm, t23.x, t23.y);
+        } else {
+          acc += (ex2(t01.x) + ex2(t01.y)) + (ex2(t23.x) + ex2(t23.y));
+        }
+      }
+      if (pass == 0) {
+        const float cw = warp_max(cm);
+        if (cw > -kInf) R = quant(cw);
+      } else {
+        acc = warp_sum(acc);
+        if (lane == 0) part[(int64_t)split * n_rows + x] = make_float2(R, acc);
+      }
+    }
+  }
+}
+
+// m_out[x] = ln 2 * log2 sum_s S_s 2^(R_s) over the non-empty pieces (natural log)
+__global__ void noalloc_merge_kernel(const float2* part, int32_t n_rows, int32_t nsplit, double* m_out) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n_rows; x += gridDim.x * blockDim.x) {
+    float Rm = -kInf;
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 v = part[(int64_t)s * n_rows + x];
+      if (v.y > 0.f) Rm = fmaxf(Rm, v.x);
+    }
+    if (Rm == -kInf) {
+      m_out[x] = -INFINITY;
+      continue;
+    }
+    float S = 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 v = part[(int64_t)s * n_rows + x];
+      if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
+    }
+    int e;
+    const float mant = frexpf(S, &e);
+    m_out[x] = ((double)Rm + (double)e) * 0.69314718055994530942 + (double)logf(mant);
+  }
+}
+
 }  // namespace
 
 int apply_ctas_per_sm(int slot) {
@@ -413,6 +538,54 @@ cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int grid, cudaStream_
     apply_recomp_kernel<2><<<grid, kApplyThreads, 0, s>>>(a);
   else
     apply_recomp_kernel<3><<<grid, kApplyThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+
+// ---- allocation-free entry point: host side ---------------------------------
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+float* g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+// Device address of the scratch array for the current device; resolved once per
+// device (this lookup is the only set-up the entry point performs).
+cudaError_t noalloc_scratch(float** out, int64_t* capacity_floats) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_dev_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_dev_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_dev_ptr[dev];
+  *capacity_floats = kNoAllocScratchFloats;
+  return cudaSuccess;
+}
+
+int64_t noalloc_scratch_floats_needed(int32_t n_rows, int32_t n_cols) {
+  const int64_t nsplit = (n_cols + kRowCols - 1) / kRowCols;
+  const int64_t op = 2 * ((int64_t)(n_cols + 63) / 64 * 64);
+  return op + 2 * nsplit * (int64_t)n_rows;
+}
+
+cudaError_t launch_edge_apply_noalloc(const float* C, int64_t ld, int32_t n_rows, int32_t n_cols, const double* g,
+                                      float shi, float slo, double* m_out, float* scratch, cudaStream_t s) {
+  const int32_t nsplit = (n_cols + kRowCols - 1) / kRowCols;
+  const int64_t op_len = (int64_t)(n_cols + 63) / 64 * 64;
+  float* hh = scratch;
+  float* hl = scratch + op_len;
+  float2* part = reinterpret_cast<float2*>(scratch + 2 * op_len);  // 2*op_len is a multiple of 128 floats
+  const int ob = (n_rows + 8 * kRowRowsPerWarp - 1) / (8 * kRowRowsPerWarp);
+  noalloc_operand_kernel<<<std::min<int64_t>(1024, (n_cols + 255) / 256), 256, 0, s>>>(g, n_cols, hh, hl);
+  noalloc_row_kernel<<<ob * nsplit, kApplyThreads, 0, s>>>(C, ld, n_rows, n_cols, hh, hl, shi, slo, nsplit, part);
+  noalloc_merge_kernel<<<std::min<int64_t>(1024, (n_rows + 255) / 256), 256, 0, s>>>(part, n_rows, nsplit, m_out);
   return cudaGetLastError();
 }
 

@@ -183,6 +183,11 @@ cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
 cudaError_t launch_pad_copy(const float* src, int64_t src_ld, float* dst, int64_t dst_ld, int32_t rows,
                             int32_t cols, cudaStream_t s);
 int apply_ctas_per_sm(int slot);
+// allocation-free single-matrix row apply (scratch in a file-scope device array)
+cudaError_t noalloc_scratch(float** out, int64_t* capacity_floats);
+int64_t noalloc_scratch_floats_needed(int32_t n_rows, int32_t n_cols);
+cudaError_t launch_edge_apply_noalloc(const float* C, int64_t ld, int32_t n_rows, int32_t n_cols, const double* g,
+                                      float shi, float slo, double* m_out, float* scratch, cudaStream_t s);
 constexpr int kApplySlots = 4;
 
 }  // namespace treeot

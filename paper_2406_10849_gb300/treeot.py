@@ -101,6 +101,8 @@ SIGNATURES = {
     "tree_ot_get_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "tree_ot_set_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "tree_ot_plan_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]),
+    "tree_ot_edge_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_double,
+                                             C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -349,3 +351,18 @@ class Solver:
         keys = ["directed_edges", "edges", "elements_per_half_step", "matrix_bytes_per_half_step",
                 "apply_tasks_c0", "apply_tasks_c1", "device_bytes", "node_ctas_c0", "node_ctas_c1"]
         return dict(zip(keys, [int(x) for x in st]))
+
+
+def edge_apply_noalloc(cost, g, eps: float, m_out, ld: int = None, stream=None):
+    """tree_ot_edge_apply_noalloc on device tensors: m_out[x] = LSE_y(g[y] - cost[x, y] / eps).
+
+    cost: CUDA float32 (n_rows, ld) tensor (its first n_cols = len(g) columns are used),
+    g: CUDA float64 (n_cols,), m_out: CUDA float64 (n_rows,).  Marshalling only.
+    """
+    load()
+    n_rows = int(cost.shape[0])
+    n_cols = int(g.shape[0])
+    ld = int(cost.stride(0)) if ld is None else int(ld)
+    _check(_lib.tree_ot_edge_apply_noalloc(C.c_void_p(cost.data_ptr()), ld, n_rows, n_cols,
+                                           C.c_void_p(g.data_ptr()), float(eps), C.c_void_p(m_out.data_ptr()),
+                                           C.c_void_p(_stream_ptr(stream))))
