@@ -67,23 +67,28 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_hash() -> str:
+KERNEL_SOURCES = {"apply_dense_kernel": "apply_f32.cu", "apply_dense_tma_kernel": "apply_tma.cu"}
+
+
+def kernel_hash(kernel: str = "apply_dense_kernel") -> str:
     h = hashlib.sha256()
-    for f in ("apply_f32.cu", "ptx.cuh", "internal.h"):
+    for f in (KERNEL_SOURCES[kernel], "ptx.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2406_10849_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, kernel: str):
     """DRAM bytes per apply launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current source of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "apply_f32_traffic.json")
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        if d.get("kernel_hash") == kernel_hash() and d.get("workload") == workload:
-            return float(d["dram_bytes_per_launch"])
+            entries = json.load(fh)
+        for d in entries if isinstance(entries, list) else [entries]:
+            if (d.get("kernel", "apply_dense_kernel") == kernel and d.get("kernel_hash") == kernel_hash(kernel)
+                    and d.get("workload") == workload):
+                return float(d["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -217,6 +222,196 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Per-SM unit rates of the GB300 SM used for the recomputed-cost roofline:
+# 128 FP32 lanes (FFMA / FADD / FMUL, packed f32x2 included: a packed op is two
+# lane operations) and 32 MUFU ex2 per clock, both measured with a throughput
+# microbenchmark on this GPU (115 and 30 per clock per SM achieved).
+FP32_LANES_PER_CLK = 128.0
+EX2_PER_CLK = 32.0
+# FP32-pipe lane operations the recomputed-cost apply spends per element (2-D
+# points): difference, square, difference, FMA for |p - q|^2; operand minus
+# frame, two FMAs with s = s_hi + s_lo, low-part add for the argument; one add
+# into the sum.  The running maximum uses the ALU pipe and ex2 the MUFU.
+RECOMP_FP32_OPS_PER_ELEM = 9.0
+
+
+def fp32_peak(sms: int, mhz: float) -> float:
+    return FP32_LANES_PER_CLK * sms * mhz * 1e6
+
+
+def sfu_peak(sms: int, mhz: float) -> float:
+    return EX2_PER_CLK * sms * mhz * 1e6
+
+
+def run_batched(args):
+    """Independent random trees (4..32 nodes, n_j in 128..2048, 2-D points,
+    eps log-uniform in [0.002, 0.05], squared-Euclidean cost recomputed in the
+    kernel) in one handle; one step = one half-step over all trees."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+    from paper_2406_10849_gb300 import shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    probs = gen.batched_problems(seed=4000, num_trees=args.trees)
+    solver = T.Solver(probs, T.options(precision="fp32"), stream=stream)
+    stats = solver.plan_stats()
+    elems = stats["elements_per_half_step"]
+    n_apply = stats["edges"]
+    for i in range(args.warmup):
+        solver.apply(i % 2)
+        solver.node_update(i % 2)
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    c0 = args.warmup % 2
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            solver.apply((c0 + i) % 2)
+            ev[i][1].record(stream)
+            solver.node_update((c0 + i) % 2)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+    clocks = clk.summary()
+    t_ms = start.elapsed_time(stop)
+    t_max = shard.max_over_ranks(t_ms, dist, dev)
+    apply_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks["sm_mhz"] or 2070.0
+    elem_rate = elems / (apply_ms / 1e3)
+    achieved = RECOMP_FP32_OPS_PER_ELEM * elem_rate
+    peak = fp32_peak(sms, mhz)
+    extra = {}
+    if rank == 0 and not args.no_converge:
+        solver.reset()
+        s2 = T.Solver(probs, T.options(precision="fp32", tol=1e-6, tol_kind="max", max_half_steps=20000),
+                      stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, res = s2.solve()
+        dt = time.perf_counter() - t0
+        s2.close()
+        hs = [r["half_steps"] for r in res]
+        extra["solve_to_1e-6"] = {"seconds": dt, "converged": sum(1 for r in res if r["status"] == 0),
+                                  "trees": len(res), "half_steps_median": int(np.median(hs)),
+                                  "half_steps_max": int(max(hs)),
+                                  "worst_max_marginal_l1": max(r["max_marginal_l1"] for r in res)}
+    solver.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": world * n_apply * K / (t_max / 1e3), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched{args.trees}_trees_2d_sqeuclid", "trees": args.trees, "edges": n_apply,
+                   "elements_per_step": elems, "step": "one half-step over every tree (apply + node update)",
+                   "l2": "no stored costs; per-step vectors exceed L2",
+                   "autotuned_tile": {"output_block": stats["recompute_output_block"],
+                                      "ctas_per_sm": stats["recompute_ctas_per_sm"],
+                                      "register_variant": stats["recompute_variant"]}},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "apply_recomp_kernel<2>",
+                     "apply_ms_avg": apply_ms, "elements_per_s": elem_rate,
+                     "ops_per_element": RECOMP_FP32_OPS_PER_ELEM,
+                     "peak_kind": f"FP32 lanes: 128/clk/SM x {sms} SMs x {mhz:.0f} MHz (median SM clock under load)",
+                     "sfu_frac": elem_rate / sfu_peak(sms, mhz)},
+        "clocks": clocks, "gpu_launches": 2 * K,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_warmstart(args):
+    """Learned warm start on barycenter stars (8 fixed leaves on a side x side grid,
+    free centre, eps log-uniform in [0.0025, 0.01] for training): solve the
+    training stars from u = 1 on the GPU, train the MLP on their leaf potentials
+    with the library's own kernels, then solve the held-out stars (eps = 0.005)
+    from u = 1 and from the predicted leaf potentials, each to max marginal L1
+    <= 1e-6 in one batched handle.  The JSON line reports the warm-start wall
+    time (prediction included) with the zero-init time beside it."""
+    import torch
+
+    import gen
+    from paper_2406_10849_gb300 import warmstart as W
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    side, B = args.side, 512
+    t0 = time.perf_counter()
+    X, Y, hs_train = [], [], []
+    for b in range(0, args.train_trees, B):
+        probs = gen.warmstart_stars(5_000_000 + b, min(B, args.train_trees - b), side=side)
+        res, s, _ = W.zero_solve(probs)
+        X.append(torch.from_numpy(W.inputs(probs)).to(dev))
+        Y.append(W.targets(s, probs).clone())
+        s.close()
+        hs_train += [r["half_steps"] for r in res]
+    X, Y = torch.cat(X), torch.cat(Y)
+    t_data = time.perf_counter() - t0
+    ws = W.WarmStart(side * side, 512, 256, seed=0)
+    t1 = time.perf_counter()
+    hist = ws.train(X, Y, epochs=args.epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t1
+    test = gen.warmstart_stars(9_000_000, args.test_trees, side=side, eps=0.005)
+    W.zero_solve(test[:4])[1].close()  # first-use costs (autotuner cache) outside the timed solves
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize(dev)
+        rz, s, tz = W.zero_solve(test)
+        s.close()
+        rw, fallbacks, tw = ws.warm_solve(test)
+    clocks = clk.summary()
+    hz = np.array([r["half_steps"] for r in rz], dtype=np.float64)
+    hw = np.array([r["half_steps"] for r in rw], dtype=np.float64)
+    line = {
+        "metric": "time to max marginal L1 <= 1e-6, warm start vs u = 1", "value": tw, "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": tw * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 solve, bf16 MLP", "data": "synthetic",
+        "config": {"workload": f"warmstart_star{side * side}_train{args.train_trees}_test{args.test_trees}",
+                   "leaves": 8, "n": side * side, "train_eps": [0.0025, 0.01], "test_eps": 0.005,
+                   "mlp": f"{side * side + 1}-512-512-{side * side} GELU, bf16 weights, fp32 master + Adam",
+                   "epochs": args.epochs},
+        "zero_init_seconds": tz, "speedup": tz / tw,
+        "half_steps": {"zero_mean": float(hz.mean()), "warm_mean": float(hw.mean()),
+                       "zero_median": float(np.median(hz)), "warm_median": float(np.median(hw)),
+                       "zero_max": int(hz.max()), "warm_max": int(hw.max()),
+                       "paired_frac_warm_fewer": float(np.mean(hw < hz))},
+        "fallbacks": fallbacks,
+        "worst_max_marginal_l1": {"warm": max(r["max_marginal_l1"] for r in rw),
+                                  "zero": max(r["max_marginal_l1"] for r in rz)},
+        "training": {"data_seconds": t_data, "train_seconds": t_train, "samples": int(X.shape[0]),
+                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                     "target_variance": float(Y.var().item()),
+                     "train_half_steps_mean": float(np.mean(hs_train))},
+        "clocks": clocks,
+    }
+    ws.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,11 +422,26 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-1e-6 solve")
     ap.add_argument("--nodes", type=int, default=NODES, help="tree size (64 = the benchmark workload)")
+    ap.add_argument("--workload", default="prufer", choices=["prufer", "batched", "warmstart"],
+                    help="prufer: the 64-node stored-cost tree (default); batched: independent random trees "
+                         "with costs recomputed from 2-D points (measured against the MUFU ex2 roofline); "
+                         "warmstart: learned warm start on barycenter stars, warm vs u = 1")
+    ap.add_argument("--train-trees", type=int, default=20000, help="warmstart: training stars")
+    ap.add_argument("--test-trees", type=int, default=2000, help="warmstart: held-out stars")
+    ap.add_argument("--side", type=int, default=32, help="warmstart: grid side (n = side^2)")
+    ap.add_argument("--epochs", type=int, default=30, help="warmstart: training epochs")
+    ap.add_argument("--trees", type=int, default=512, help="batched workload: number of trees")
+    ap.add_argument("--dense-kernel", default="auto", choices=["auto", "tma", "ldg"],
+                    help="stored-cost apply kernel (auto: the solver's autotuner picks)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
 
     import torch
 
@@ -253,8 +463,10 @@ def main():
     workload = workload_name(args.nodes)
     costs = [gen.sqeuclid_cost_f32_torch(p.coords[a], p.coords[b], 1.0, dev) for a, b in p.edges]
     torch.cuda.synchronize(dev)
-    solver = T.Solver([p], T.options(precision="fp32"), stream=stream, device_costs=[costs])
+    solver = T.Solver([p], T.options(precision="fp32", dense_kernel=args.dense_kernel), stream=stream,
+                      device_costs=[costs])
     stats = solver.plan_stats()
+    kernel = "apply_dense_tma_kernel" if stats["dense_tma"] else "apply_dense_kernel"
     n_apply = p.num_edges
 
     # warm-up
@@ -300,8 +512,8 @@ def main():
     peak, peak_kind = read_peaks()
     achieved = alg / (apply_avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(workload), "peak_kind": f"hbm_gbs of {peak_kind}",
-                "kernel": "apply_dense_kernel", "apply_ms_avg": apply_avg_ms,
+                "traffic": profiled_traffic(workload, kernel), "peak_kind": f"hbm_gbs of {peak_kind}",
+                "kernel": kernel, "apply_ms_avg": apply_avg_ms,
                 "apply_ms_median": statistics.median(apply_ms), "algorithmic_bytes_per_launch": alg}
 
     extra = {}
@@ -314,8 +526,22 @@ def main():
         rc, res = s2.solve()
         dt = time.perf_counter() - t0
         s2.close()
-        extra["time_to_1e-6"] = {"plain_fp32_s": dt, "half_steps": res[0]["half_steps"],
-                                 "max_marginal_l1": res[0]["max_marginal_l1"], "status": rc}
+        ttt = {"plain_fp32_s": dt, "plain_half_steps": res[0]["half_steps"],
+               "plain_max_marginal_l1": res[0]["max_marginal_l1"], "plain_status": rc}
+        # absorbed BF16 phase, then FP32 refinement, same tolerance and check
+        s3 = T.Solver([p], T.options(precision="fp32", tol=1e-6, tol_kind="max", max_half_steps=20000,
+                                     apply_mode="bf16"), stream=stream, device_costs=[costs])
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc3, res3 = s3.solve()
+        dt3 = time.perf_counter() - t0
+        s3.close()
+        ttt.update({"bf16_refined_s": dt3, "bf16_half_steps": res3[0]["half_steps"],
+                    "bf16_max_marginal_l1": res3[0]["max_marginal_l1"], "bf16_status": rc3,
+                    "speedup": dt / dt3 if dt3 > 0 else None,
+                    "note": "wall time of tree_ot_solve from u = 1 to max marginal L1 < 1e-6 (GPU check), "
+                            "setup excluded"})
+        extra["time_to_1e-6"] = ttt
     solver.close()
 
     e2e = None

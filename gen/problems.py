@@ -315,6 +315,20 @@ def random_tree_problem(rng, J: int, n_range=(128, 2048), eps_range=(0.002, 0.05
                        cost_scale=1.0, cost_kind=COST_SQEUCLID, meta={})
 
 
+def warmstart_stars(seed0: int, count: int, side: int = 32, leaves: int = 8, eps_range=(0.0025, 0.01),
+                    eps: float = None) -> List[TreeProblem]:
+    """Barycenter stars of the star generator for the learned warm start: star i
+    uses seed seed0 + i; eps is log-uniform in eps_range (training) unless fixed."""
+    out = []
+    for i in range(count):
+        e = eps
+        if e is None:
+            rng = np.random.default_rng(seed0 + i + 7_000_000)
+            e = float(np.exp(rng.uniform(np.log(eps_range[0]), np.log(eps_range[1]))))
+        out.append(star_problem(seed=seed0 + i, leaves=leaves, side=side, eps=e))
+    return out
+
+
 def batched_problems(seed: int = 4000, num_trees: int = 512, J_range=(4, 32), n_range=(128, 2048),
                      eps_range=(0.002, 0.05)) -> List[TreeProblem]:
     rng = np.random.default_rng(seed)

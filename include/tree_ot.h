@@ -96,6 +96,14 @@ typedef struct tree_ot_problem {
 
 #define TREE_OT_APPLY_AUTO       0
 #define TREE_OT_APPLY_LSE        1  /* log-sum-exp on C (stored or recomputed)             */
+#define TREE_OT_APPLY_BF16       2  /* stored costs: absorbed BF16 kernel, then FP32 LSE
+                                       refinement (see refine_tol, absorb_tau, lowp_start)  */
+
+/* options.flags: which kernel streams stored costs (FP32 path).  With neither
+ * bit the autotuner (autotune = 1) times both and keeps the faster; with
+ * autotune = 0 the plain-load kernel runs. */
+#define TREE_OT_OPT_DENSE_TMA    1u /* bulk-copy staged kernel (one producer warp, ring)   */
+#define TREE_OT_OPT_DENSE_LDG    2u /* plain 16-byte streaming loads                       */
 
 #define TREE_OT_TOL_SUM          0  /* the paper's stopping sum (Bipartite Iterative Scaling) */
 #define TREE_OT_TOL_MAX          1  /* the largest single term of that sum                 */
@@ -108,7 +116,23 @@ typedef struct tree_ot_options {
     int64_t max_half_steps;   /* iteration cap (half-steps)                               */
     int32_t check_every;      /* half-steps between convergence read-backs (even, >= 2)  */
     int32_t use_graph;        /* 1: replay each chunk of half-steps as a CUDA graph      */
-    uint32_t flags;           /* reserved, 0                                             */
+    uint32_t flags;           /* TREE_OT_OPT_* bits, 0 by default                        */
+    /* APPLY_BF16 only (problems with stored costs):
+     * the first lowp_start half-steps use the FP32 kernel; then the potentials
+     * are absorbed into a BF16 copy of the Gibbs kernel,
+     *     Kt(x,y) = 2^(A(x) + B(y) - C(x,y) log2(e)/eps - rho(x))   (row max 1),
+     * A, B the apply operands at absorption time, and each apply multiplies Kt
+     * by 2^(h - base) on the reduction side (FP32 accumulation).  An edge whose
+     * operand drifts more than absorb_tau (log2 units) from its base is
+     * re-absorbed on the device.  When a problem's stopping quantity falls below
+     * refine_tol it switches to the FP32 log-sum-exp kernel for good. */
+    double refine_tol;        /* default 1e-5                                            */
+    double absorb_tau;        /* default 48                                              */
+    int32_t lowp_start;       /* default 16                                              */
+    int32_t autotune;         /* 1 (default): at create, time the recomputed-cost apply for
+                                 each tile shape (output block 256/512/1024, CTAs per SM)
+                                 and keep the fastest, cached per problem shape; and time
+                                 the two stored-cost kernels (see TREE_OT_OPT_DENSE_*)  */
 } tree_ot_options;
 
 /* ---- per-problem result ------------------------------------------------- */
@@ -121,11 +145,14 @@ typedef struct tree_ot_result {
     double dual;                /* -eps f(u,rho) of eq. tree_dual_mass_consv              */
     double transport_cost;      /* sum_e <C_e,B_e>                                       */
     double wall_ms;             /* host wall time of the solve call                      */
+    int64_t lowp_half_steps;    /* APPLY_BF16: half-steps spent in the absorbed BF16 phase */
+    int64_t absorptions;        /* APPLY_BF16: edge absorptions performed (whole handle)  */
 } tree_ot_result;
 
 typedef struct tree_ot_handle tree_ot_handle;
 
-/* Fill *opt with defaults: FP32, AUTO, tol 1e-6 (SUM), cap 100000, check 32, graph on. */
+/* Fill *opt with defaults: FP32, AUTO, tol 1e-6 (SUM), cap 100000, check 32, graph on,
+ * refine_tol 1e-5, absorb_tau 48, lowp_start 16, autotune on. */
 void tree_ot_default_options(tree_ot_options *opt);
 
 /* Human-readable name of a return code (static string). */
@@ -156,8 +183,16 @@ int tree_ot_destroy(tree_ot_handle *h);
 int tree_ot_reset(tree_ot_handle *h, void *cuda_stream);
 
 /* Iterate from the current state until every problem meets opt->tol or the
- * cap, then run the FP64 check.  results: host array [num_probs] (may be NULL).
- * Returns TREE_OT_NOT_CONVERGED if some problem hit the cap. */
+ * cap, then run the FP64 check.  A problem retires on the FP32 stopping
+ * quantity the half-step kernels accumulate (Algorithm "Bipartite Iterative
+ * Scaling"'s while-condition, or its largest term); the FP64-grade check of the
+ * returned potentials then certifies it: if the check exceeds tol, the problem
+ * resumes with a proportionally lower retirement threshold (at most 8 times,
+ * and only while each round improves the check by 10%: FP32 iterates have an
+ * accuracy floor, typically 1e-7 to 1e-6 in max marginal L1, that grows as eps
+ * shrinks).
+ * results: host array [num_probs] (may be NULL).  Returns TREE_OT_NOT_CONVERGED
+ * if some problem hit the cap or was not certified. */
 int tree_ot_solve(tree_ot_handle *h, void *cuda_stream, tree_ot_result *results);
 
 /* Queue exactly T half-steps (no convergence test, no retirement, no sync).
@@ -190,12 +225,35 @@ int tree_ot_marginals(tree_ot_handle *h, int32_t prob, int32_t node, double *out
 int tree_ot_get_potentials(tree_ot_handle *h, void *cuda_stream, int32_t prob, int32_t dedge, double *out);
 int tree_ot_set_potentials(tree_ot_handle *h, void *cuda_stream, int32_t prob, int32_t dedge, const double *in);
 
+/* Set many directed-edge potentials at once from DEVICE memory (a predicted
+ * warm start lands here without a host round trip).  Item i sets the potential
+ * of directed edge dedges[i] of problem probs[i] (host arrays of `count`) to
+ * values[i * ld + x], x < n_owner (device FP32, cost units, row stride ld >= the
+ * largest n_owner).  All items are checked first: a non-finite value returns
+ * TREE_OT_ERR_NONFINITE and changes nothing.  One stream synchronisation per
+ * call; the values buffer may be reused once the call returns. */
+int tree_ot_set_potentials_batch(tree_ot_handle *h, void *cuda_stream, int32_t count, const int32_t *probs,
+                                 const int32_t *dedges, const float *values, int64_t ld);
+
+/* The reverse: values[i * ld + x] = f(x) of directed edge dedges[i] of problem
+ * probs[i], x < n_owner, as FP32 cost units into DEVICE memory (ld >= the
+ * largest n_owner; entries past n_owner are left alone).  flags & 1: subtract
+ * the mean over x (the gauge mean_x f = 0; plans do not depend on the gauge).
+ * Enqueued on the stream; returns without synchronising. */
+#define TREE_OT_GET_CENTRED 1u
+int tree_ot_get_potentials_batch(tree_ot_handle *h, void *cuda_stream, int32_t count, const int32_t *probs,
+                                 const int32_t *dedges, float *values, int64_t ld, uint32_t flags);
+
 /* Plan statistics of the handle (host values), first nstats of:
  * [0] directed edges, [1] edges, [2] plan elements per half-step
  * (sum_e n_a n_b: every half-step applies every edge once), [3] stored cost
  * bytes read per half-step (4 sum_e n_a n_b for dense costs, 0 when costs are
  * recomputed), [4] apply tasks of colour 0, [5] of colour 1, [6] device bytes
- * owned by the handle, [7] node-update CTAs of colour 0, [8] of colour 1. */
+ * owned by the handle, [7] node-update CTAs of colour 0, [8] of colour 1,
+ * [9] output block of recomputed-cost tasks, [10] their CTAs per SM (0 = by
+ * occupancy), [11] their kernel register budget (0: 2 CTAs per SM, 1: 3), all
+ * as chosen by the autotuner, [12] 1 when stored costs stream through the
+ * bulk-copy staged kernel (TREE_OT_OPT_DENSE_TMA or the autotuner's choice). */
 int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
 /* Allocation-free apply of one stored cost matrix (the paper has no
@@ -227,6 +285,40 @@ int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
  * synchronise it. */
 int tree_ot_edge_apply_noalloc(const float *cost, int64_t ld, int32_t n_rows, int32_t n_cols, const double *g,
                                double eps, double *m_out, void *cuda_stream);
+
+/* ---- warm-start predictor ------------------------------------------------
+ * The paper has no counterpart: this is a learned initialisation for the
+ * potentials of the leaves of a star (a project extension; the solver itself
+ * never depends on it).  A 3-layer MLP,
+ *     y = W3 g(W2 g(W1 x + b1) + b2) + b3,   g = GELU (erf form),
+ * with FP32 master parameters laid out as [W1 (hidden x in), b1, W2 (hidden x
+ * hidden), b2, W3 (out x hidden), b3] (each tensor starting at a multiple of
+ * 8 floats; tree_ot_mlp_num_params returns the six offsets), BF16 copies of
+ * the weights and BF16 activations feeding tensor-core MMAs with FP32
+ * accumulation.  Loss: mean squared error over the batch and outputs.
+ * x, y, target, grads are device pointers (row-major batch x dim FP32); get /
+ * set_params use host memory (set_params also clears Adam's moments).
+ * Not thread-safe per handle.  Errors: tree_ot_mlp_last_error(). */
+typedef struct tree_ot_mlp tree_ot_mlp;
+int tree_ot_mlp_create(int32_t in_dim, int32_t hidden, int32_t out_dim, int32_t max_batch, uint64_t seed,
+                       tree_ot_mlp **out);
+int tree_ot_mlp_destroy(tree_ot_mlp *m);
+int tree_ot_mlp_num_params(tree_ot_mlp *m, int64_t *n, int64_t *offsets /* [6] or NULL */);
+int tree_ot_mlp_get_params(tree_ot_mlp *m, float *host_out);
+int tree_ot_mlp_set_params(tree_ot_mlp *m, const float *host_in);
+/* Input transform applied inside the first kernel: features 0..count-1 of every
+ * row become log(max(x, floor_value)) * scale (default count 0: none). */
+int tree_ot_mlp_set_input_log(tree_ot_mlp *m, int32_t count, double floor_value, double scale);
+/* y = MLP(x) for batch rows (batch <= max_batch). */
+int tree_ot_mlp_forward(tree_ot_mlp *m, void *cuda_stream, const float *x, int32_t batch, float *y);
+/* Forward + backward of the MSE loss; grads (device, num_params floats, the
+ * parameter layout) and loss (host) may be NULL.  Parameters are unchanged. */
+int tree_ot_mlp_backward(tree_ot_mlp *m, void *cuda_stream, const float *x, const float *target, int32_t batch,
+                         float *grads, double *loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) at learning rate lr. */
+int tree_ot_mlp_train_step(tree_ot_mlp *m, void *cuda_stream, const float *x, const float *target, int32_t batch,
+                           double lr, double *loss);
+const char *tree_ot_mlp_last_error(void);
 
 #ifdef __cplusplus
 }

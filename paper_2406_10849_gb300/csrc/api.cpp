@@ -8,6 +8,8 @@
 #include <cstring>
 #include <deque>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -173,6 +175,9 @@ struct tree_ot_handle {
   int32_t slot_count[2][kApplySlots] = {};
   std::vector<NodeChunk> chunks[2];
   std::vector<Task> check_tasks;
+  std::vector<Task> btasks[2];             // absorbed BF16 apply tasks per colour
+  std::vector<Task> atasks;                // absorption blocks (dedge 2e, 64 rows)
+  bool lowp = false;                       // handle built for the absorbed BF16 phase
   std::vector<int32_t> prob_node_base, prob_edge_base, prob_nodes;
   std::vector<std::vector<double>> mu;  // per global node (fixed nodes), host copy
   int64_t vec_len = 0, node_len = 0, part_len = 0, coord_len = 0;
@@ -187,6 +192,26 @@ struct tree_ot_handle {
   Task* d_tasks[2] = {nullptr, nullptr};
   NodeChunk* d_chunks[2] = {nullptr, nullptr};
   Task* d_check_tasks = nullptr;
+  Task* d_btasks[2] = {nullptr, nullptr};
+  int32_t* d_queue = nullptr;              // [colour][slot][2] work-queue counters
+  int32_t rec_ob = kRecOut;                // recomputed-cost output block (autotuned)
+  int32_t grid_mult = 0;                   // 0: occupancy-derived grid; else CTAs per SM (autotuned)
+  int32_t rec_variant = 0;                 // recomputed-cost kernel register budget (autotuned)
+  int32_t dense_tma = 0;                   // stored-cost tasks on the bulk-copy staged kernel
+  StreamTask* d_stasks[2] = {nullptr, nullptr};  // slot-0 tasks of each colour, resolved for that kernel
+  void* d_setbuf = nullptr;                // batched potential set: directed-edge list + records
+  int64_t setbuf_cap = 0;                  // items d_setbuf holds
+  int rec_grid[2][kApplySlots] = {};       // occupancy-derived grids per variant
+  int64_t task_cap[2] = {0, 0};            // device capacity of d_tasks
+  Task* d_atasks = nullptr;
+  int32_t *d_lowp = nullptr, *d_drift = nullptr;
+  int64_t* d_lowp_span = nullptr;          // per problem: [begin, end) half-steps of the BF16 phase
+  unsigned long long* d_absorb_count = nullptr;
+  std::vector<int64_t> h_lowp_span;
+  unsigned long long h_absorb_count = 0;
+  float *d_bh = nullptr, *d_bl = nullptr, *d_arho = nullptr;
+  int bf16_grid = 1;
+  float* d_fr = nullptr;                   // frames of d_m (FP32, log2 on the 2^-10 grid)
   double *d_f = nullptr, *d_m = nullptr, *d_Z = nullptr, *d_rho = nullptr, *d_logg = nullptr, *d_mu = nullptr;
   double *d_resid_acc = nullptr, *d_resid_dedge = nullptr, *d_res_sum = nullptr, *d_marg = nullptr;
   double *d_edge_tc = nullptr, *d_edge_mass = nullptr;
@@ -198,6 +223,8 @@ struct tree_ot_handle {
   int32_t *d_done = nullptr, *d_node_arrive = nullptr, *d_node_count = nullptr, *d_launch_count = nullptr;
   int32_t *d_err = nullptr, *d_scan = nullptr;
   int64_t *d_done_at = nullptr, *d_hs = nullptr;
+  double* d_ptol = nullptr;                // per-problem retirement threshold
+  std::vector<double> h_ptol;
   std::vector<void*> owned;
 
   int64_t hs_host = 0;
@@ -205,6 +232,7 @@ struct tree_ot_handle {
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
   int apply_grid[kApplySlots] = {1, 1, 1, 1};
+  int sms = 1;
 
   bool have_check = false;
   std::vector<double> h_marg, h_f, h_Z, h_rho, h_tc, h_mass;
@@ -234,6 +262,69 @@ namespace {
     if (rc_) return rc_;  \
   } while (0)
 
+// Apply tasks of both colours, grouped by kernel slot.  rec_ob: largest output
+// block of a recomputed-cost task (256, 512 or 1024 outputs); a task with fewer
+// outputs runs its CTA as G warp groups splitting the reduction points.
+void build_apply_tasks(tree_ot_handle* h, int32_t rec_ob) {
+  for (int c = 0; c < 2; ++c) {
+    h->tasks[c].clear();
+    for (int s2 = 0; s2 < kApplySlots; ++s2) h->slot_begin[c][s2] = h->slot_count[c][s2] = 0;
+  }
+  for (size_t di = 0; di < h->dedges.size(); ++di) {
+    const DEdgeD& d = h->dedges[di];
+    const NodeD& own = h->nodes[d.owner];
+    const NodeD& nbn = h->nodes[d.nbr];
+    const ProbD& pd = h->probs[d.prob];
+    std::vector<Task>& tl = h->tasks[own.colour];
+    const bool dense = pd.cost_kind == TREE_OT_COST_DENSE_F32;
+    if (h->fp64) {
+      for (int32_t o0 = 0; o0 < own.n; o0 += 64)
+        tl.push_back(Task{(int32_t)di, dense ? (d.dir == 0 ? TASK_ROW : TASK_COL) : TASK_RECOMP, o0,
+                          std::min(64, own.n - o0), 0, nbn.n, 0, 0});
+    } else if (dense && d.dir == 0) {
+      for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
+        for (int32_t s = 0; s < d.nsplit; ++s)
+          tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
+                            std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
+    } else if (dense) {
+      for (int32_t s = 0; s < d.nsplit; ++s)
+        for (int32_t o0 = 0; o0 < own.n; o0 += kColCols)
+          tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kColCols, own.n - o0), s * kColRows,
+                            std::min(kColRows, nbn.n - s * kColRows), s, 0});
+    } else {
+      for (int32_t o0 = 0; o0 < own.n; o0 += rec_ob) {
+        const int32_t oc = std::min(rec_ob, own.n - o0);
+        int32_t G = 1;
+        while (G < 8 && kRecOut / (2 * G) >= oc) G *= 2;
+        for (int32_t s = 0; s < d.nsplit; ++s)
+          tl.push_back(Task{(int32_t)di, TASK_RECOMP, o0, oc, s * kRecRed, std::min(kRecRed, nbn.n - s * kRecRed), s,
+                            G});
+      }
+    }
+  }
+  // group each colour's tasks by kernel slot (stored costs; recomputed costs by
+  // dimension); recomputed tasks go largest first for the work queue
+  for (int c = 0; c < 2; ++c) {
+    auto slot_of = [&](const Task& t) {
+      if (h->fp64 || t.kind != TASK_RECOMP) return 0;
+      return (int)h->probs[h->dedges[t.dedge].prob].dim;
+    };
+    auto cost_of = [&](const Task& t) { return (int64_t)t.ocount * t.rcount; };
+    std::stable_sort(h->tasks[c].begin(), h->tasks[c].end(), [&](const Task& x, const Task& y) {
+      const int sx = slot_of(x), sy = slot_of(y);
+      if (sx != sy) return sx < sy;
+      return sx != 0 && cost_of(x) > cost_of(y);
+    });
+    for (const Task& t : h->tasks[c]) h->slot_count[c][slot_of(t)] += 1;
+    int32_t b = 0;
+    for (int s2 = 0; s2 < kApplySlots; ++s2) {
+      h->slot_begin[c][s2] = b;
+      b += h->slot_count[c][s2];
+    }
+  }
+  h->rec_ob = rec_ob;
+}
+
 ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   ApplyArgs a{};
   a.tasks = h->d_tasks[colour];
@@ -244,6 +335,7 @@ ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   a.probs = h->d_probs;
   a.done = h->d_done;
   a.m = h->d_m;
+  a.fr = h->d_fr;
   a.hh = h->d_hh;
   a.hl = h->d_hl;
   a.f = h->d_f;
@@ -251,6 +343,11 @@ ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   a.coords = h->d_coords;
   a.part32 = h->d_part32;
   a.part64 = h->d_part64;
+  a.lowp = h->d_lowp;
+  a.bh = h->d_bh;
+  a.bl = h->d_bl;
+  a.arho = h->d_arho;
+  a.err = h->d_err;
   return a;
 }
 
@@ -268,6 +365,7 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.done_at = h->d_done_at;
   a.f = h->d_f;
   a.m = h->d_m;
+  a.fr = h->d_fr;
   a.hh = h->d_hh;
   a.hl = h->d_hl;
   a.Z = h->d_Z;
@@ -287,9 +385,47 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.hs = h->d_hs;
   a.err = h->d_err;
   a.tol = h->opt.tol;
+  a.ptol = h->d_ptol;
   a.tol_kind = h->opt.tol_kind;
   a.retire = retire ? 1 : 0;
+  a.absorbed = h->lowp ? 1 : 0;
+  a.lowp = h->d_lowp;
+  a.bh = h->d_bh;
+  a.bl = h->d_bl;
+  a.drift = h->d_drift;
+  a.refine_tol = h->opt.refine_tol;
+  a.tau = (float)h->opt.absorb_tau;
+  a.lowp_start = h->opt.lowp_start;
+  a.lowp_span = h->d_lowp_span;
   return a;
+}
+
+AbsorbArgs absorb_args(tree_ot_handle* h) {
+  AbsorbArgs a{};
+  a.tasks = h->d_atasks;
+  a.ntasks = (int32_t)h->atasks.size();
+  a.dedges = h->d_dedges;
+  a.edges = h->d_edges;
+  a.probs = h->d_probs;
+  a.hh = h->d_hh;
+  a.hl = h->d_hl;
+  a.bh = h->d_bh;
+  a.bl = h->d_bl;
+  a.arho = h->d_arho;
+  a.lowp = h->d_lowp;
+  a.drift = h->d_drift;
+  a.nedges = (int32_t)h->edges.size();
+  a.count = h->d_absorb_count;
+  return a;
+}
+
+int launch_absorb_step(tree_ot_handle* h, cudaStream_t s) {
+  if (!h->lowp) return TREE_OT_OK;
+  AbsorbArgs a = absorb_args(h);
+  const int grid = std::max(1, std::min<int>(a.ntasks, h->bf16_grid));
+  cudaError_t e = launch_absorb(a, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "absorption launch");
+  return TREE_OT_OK;
 }
 
 int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
@@ -305,9 +441,25 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
     if (cnt == 0) continue;
     a.tasks = h->d_tasks[colour] + h->slot_begin[colour][slot];
     a.ntasks = cnt;
-    const int grid = std::max(1, std::min<int>(cnt, h->apply_grid[slot]));
-    cudaError_t e = launch_apply_f32(a, slot, grid, s);
+    a.queue = h->d_queue + 2 * (colour * kApplySlots + slot);
+    if (slot == 0 && h->dense_tma) {
+      a.stasks = h->d_stasks[colour];
+      cudaError_t e = launch_apply_tma(a, std::max(1, std::min<int>(cnt, h->sms)), s);
+      if (e != cudaSuccess) return cuda_fail(e, "staged edge apply launch");
+      continue;
+    }
+    int cap = slot == 0 ? h->apply_grid[0] : h->rec_grid[h->rec_variant][slot];
+    if (slot > 0 && h->grid_mult > 0) cap = h->sms * h->grid_mult;
+    const int grid = std::max(1, std::min<int>(cnt, cap));
+    cudaError_t e = launch_apply_f32(a, slot, slot == 0 ? 0 : h->rec_variant, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+  }
+  if (h->lowp && !h->btasks[colour].empty()) {
+    a.tasks = h->d_btasks[colour];
+    a.ntasks = (int32_t)h->btasks[colour].size();
+    const int grid = std::max(1, std::min<int>(a.ntasks, h->bf16_grid));
+    cudaError_t e = launch_apply_bf16(a, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "absorbed apply launch");
   }
   return TREE_OT_OK;
 }
@@ -323,6 +475,7 @@ int queue_half_steps(tree_ot_handle* h, int64_t T, bool retire, cudaStream_t s) 
     const int colour = (int)(h->hs_host % 2);
     RC_TRY(launch_apply(h, colour, s));
     RC_TRY(launch_update(h, colour, retire, s));
+    RC_TRY(launch_absorb_step(h, s));
     ++h->hs_host;
   }
   return TREE_OT_OK;
@@ -331,11 +484,15 @@ int queue_half_steps(tree_ot_handle* h, int64_t T, bool retire, cudaStream_t s) 
 int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(h->d_f, 0, sizeof(double) * h->vec_len, s));
   CUDA_TRY(cudaMemsetAsync(h->d_m, 0, sizeof(double) * h->vec_len, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_fr, 0, sizeof(float) * h->vec_len, s));
   CUDA_TRY(cudaMemsetAsync(h->d_Z, 0, sizeof(double) * h->nodes.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_rho, 0, sizeof(double) * h->nodes.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_resid_acc, 0, sizeof(double) * h->dedges.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_resid_dedge, 0, sizeof(double) * h->dedges.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_res_sum, 0, sizeof(double) * kResidRing * h->nprob, s));
+  h->h_ptol.assign(h->nprob, h->opt.tol);
+  CUDA_TRY(cudaMemcpyAsync(h->d_ptol, h->h_ptol.data(), sizeof(double) * h->nprob, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));  // h_ptol may be rewritten by the next solve
   CUDA_TRY(cudaMemsetAsync(h->d_res_max, 0, sizeof(unsigned long long) * kResidRing * h->nprob, s));
   CUDA_TRY(cudaMemsetAsync(h->d_done, 0, sizeof(int32_t) * h->nprob, s));
   CUDA_TRY(cudaMemsetAsync(h->d_done_at, 0, sizeof(int64_t) * h->nprob, s));
@@ -344,9 +501,27 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(h->d_launch_count, 0, sizeof(int32_t), s));
   CUDA_TRY(cudaMemsetAsync(h->d_hs, 0, sizeof(int64_t), s));
   CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t) * 2 * 2 * kApplySlots, s));
   // apply operand of u = 1: h = log gamma * log2(e)
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, (int32_t)h->dedges.size(),
                           kLog2e, true, h->d_hh, h->d_hl, s));
+  // phase of every problem: absorbed BF16 phase (1), waiting for it (2), or FP32 (0)
+  CUDA_TRY(cudaMemsetAsync(h->d_lowp_span, 0, sizeof(int64_t) * 2 * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_absorb_count, 0, sizeof(unsigned long long), s));
+  {
+    std::vector<int32_t> lp(h->nprob, 0);
+    std::vector<int32_t> dr(h->edges.size(), 0);
+    for (int p = 0; p < h->nprob; ++p) {
+      if (!h->lowp || h->probs[p].cost_kind != TREE_OT_COST_DENSE_F32) continue;
+      lp[p] = h->opt.lowp_start == 0 ? 1 : 2;
+      if (lp[p] == 1)
+        for (int k = 0; k < h->probs[p].edge_count; ++k) dr[h->probs[p].edge_begin + k] = 1;
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_lowp, lp.data(), sizeof(int32_t) * lp.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h->d_drift, dr.data(), sizeof(int32_t) * dr.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    RC_TRY(launch_absorb_step(h, s));
+  }
   h->hs_host = 0;
   h->have_check = false;
   return TREE_OT_OK;
@@ -486,8 +661,174 @@ void fill_results(tree_ot_handle* h, tree_ot_result* res) {
     r.half_steps = done ? h->h_done_at[p] : h->hs_host;
     r.status = (h->last_status.empty() ? TREE_OT_OK : h->last_status[p]);
     r.wall_ms = h->last_wall_ms;
+    if (!h->h_lowp_span.empty() && h->h_lowp_span[2 * p] > 0) {
+      const int64_t end = h->h_lowp_span[2 * p + 1] > 0 ? h->h_lowp_span[2 * p + 1] : r.half_steps;
+      r.lowp_half_steps = end - h->h_lowp_span[2 * p];
+    }
+    r.absorptions = (int64_t)h->h_absorb_count;
     res[p] = r;
   }
+}
+
+// ---------------------------------------------------------------------------
+// autotuner for the recomputed-cost apply: output block (256/512/1024, which
+// sets the warp groups per task) x {2 CTAs per SM register budget, 3 CTAs per
+// SM register budget, 1 CTA per SM}.  It
+// times both colours' apply launches, which write only the partial sums, so
+// the solver state is untouched.  Results are cached per problem-shape
+// signature for the life of the process.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+struct TuneCfg {
+  int32_t ob, gm, variant;
+};
+std::map<uint64_t, TuneCfg> g_tune_cache;
+
+uint64_t shape_signature(const tree_ot_handle* h) {
+  uint64_t sig = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    sig ^= v;
+    sig *= 1099511628211ull;
+  };
+  for (const DEdgeD& d : h->dedges) {
+    if (h->probs[d.prob].cost_kind == TREE_OT_COST_DENSE_F32) continue;
+    mix((uint64_t)h->nodes[d.owner].n);
+    mix((uint64_t)h->nodes[d.nbr].n);
+    mix((uint64_t)h->probs[d.prob].dim);
+    mix((uint64_t)h->nodes[d.owner].colour);
+  }
+  return sig;
+}
+
+int upload_tasks(tree_ot_handle* h, cudaStream_t s) {
+  for (int c = 0; c < 2; ++c) {
+    if ((int64_t)h->tasks[c].size() > h->task_cap[c]) return fail(TREE_OT_ERR_STATE, "task capacity exceeded");
+    if (!h->tasks[c].empty())
+      CUDA_TRY(cudaMemcpyAsync(h->d_tasks[c], h->tasks[c].data(), sizeof(Task) * h->tasks[c].size(),
+                               cudaMemcpyHostToDevice, s));
+  }
+  return TREE_OT_OK;
+}
+
+int autotune_recompute(tree_ot_handle* h, cudaStream_t s) {
+  bool any = false;
+  for (int c = 0; c < 2; ++c)
+    for (int slot = 1; slot < kApplySlots; ++slot) any = any || h->slot_count[c][slot] > 0;
+  if (!any) return TREE_OT_OK;
+  const uint64_t sig = shape_signature(h);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      build_apply_tasks(h, it->second.ob);
+      h->grid_mult = it->second.gm;
+      h->rec_variant = it->second.variant;
+      return upload_tasks(h, s);
+    }
+  }
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  TuneCfg best_cfg{kRecOut, 0, 0};
+  for (int32_t ob : {1024, 512, 256}) {
+    build_apply_tasks(h, ob);
+    RC_TRY(upload_tasks(h, s));
+    for (int32_t cfg = 0; cfg < 3; ++cfg) {
+      const int32_t gm = cfg == 2 ? 1 : 0;
+      const int32_t variant = cfg == 1 ? 1 : 0;
+      h->grid_mult = gm;
+      h->rec_variant = variant;
+      RC_TRY(launch_apply(h, 0, s));  // warm-up
+      RC_TRY(launch_apply(h, 1, s));
+      CUDA_TRY(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 2; ++rep) {
+        RC_TRY(launch_apply(h, 0, s));
+        RC_TRY(launch_apply(h, 1, s));
+      }
+      CUDA_TRY(cudaEventRecord(e1, s));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_cfg = {ob, gm, variant};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  build_apply_tasks(h, best_cfg.ob);
+  h->grid_mult = best_cfg.gm;
+  h->rec_variant = best_cfg.variant;
+  RC_TRY(upload_tasks(h, s));
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[sig] = best_cfg;
+  return TREE_OT_OK;
+}
+
+// Slot-0 (stored-cost) tasks of both colours with their addresses resolved,
+// for the bulk-copy staged kernel.  Slot-0 tasks do not depend on the
+// recomputed-cost tile shape, so this is built once.
+int upload_stream_tasks(tree_ot_handle* h, cudaStream_t s) {
+  for (int c = 0; c < 2; ++c) {
+    const int32_t cnt = h->slot_count[c][0];
+    if (cnt == 0) continue;
+    std::vector<StreamTask> st;
+    st.reserve(cnt);
+    for (int32_t i = 0; i < cnt; ++i) {
+      const Task& t = h->tasks[c][h->slot_begin[c][0] + i];
+      const DEdgeD& d = h->dedges[t.dedge];
+      const EdgeD& e = h->edges[d.edge];
+      const ProbD& pd = h->probs[d.prob];
+      StreamTask x{};
+      x.kind = t.kind;
+      x.prob = d.prob;
+      x.ocount = t.ocount;
+      x.rcount = t.rcount;
+      x.ld = e.ld;
+      x.C = t.kind == TASK_ROW ? e.C + (int64_t)t.o0 * e.ld + t.r0 : e.C + (int64_t)t.r0 * e.ld + t.o0;
+      x.m_off = d.off + t.o0;
+      x.h_off = d.rev_off + t.r0;
+      x.out_off = d.part_off + (int64_t)t.split * h->nodes[d.owner].n + t.o0;
+      x.s2 = pd.s2;
+      x.s2_lo = pd.s2_lo;
+      st.push_back(x);
+    }
+    if (!h->d_stasks[c]) RC_TRY(h->alloc(&h->d_stasks[c], cnt));
+    CUDA_TRY(cudaMemcpyAsync(h->d_stasks[c], st.data(), sizeof(StreamTask) * cnt, cudaMemcpyHostToDevice, s));
+  }
+  return TREE_OT_OK;
+}
+
+// Stored-cost kernel choice: time the plain-load and the bulk-copy staged
+// kernels on both colours' stored-cost tasks (they write only partial sums)
+// and keep the faster.
+int autotune_dense(tree_ot_handle* h, cudaStream_t s) {
+  if (h->slot_count[0][0] + h->slot_count[1][0] == 0 || !apply_tma_available()) return TREE_OT_OK;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float ms[2] = {0.f, 0.f};
+  for (int32_t tma = 0; tma < 2; ++tma) {
+    h->dense_tma = tma;
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) CUDA_TRY(cudaEventRecord(e0, s));
+      RC_TRY(launch_apply(h, 0, s));
+      RC_TRY(launch_apply(h, 1, s));
+    }
+    CUDA_TRY(cudaEventRecord(e1, s));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    CUDA_TRY(cudaEventElapsedTime(&ms[tma], e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int32_t err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (err & 2) return fail(TREE_OT_ERR_TIMEOUT, "a bounded wait in the staged edge apply ran out");
+  h->dense_tma = ms[1] < ms[0] ? 1 : 0;
+  return TREE_OT_OK;
 }
 
 }  // namespace
@@ -509,6 +850,10 @@ void tree_ot_default_options(tree_ot_options* opt) {
   opt->check_every = 32;
   opt->use_graph = 1;
   opt->flags = 0;
+  opt->refine_tol = 1e-5;
+  opt->absorb_tau = 48.0;
+  opt->lowp_start = 16;
+  opt->autotune = 1;
 }
 
 const char* tree_ot_error_string(int code) {
@@ -558,8 +903,11 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   if (opt) o = *opt;
   if (o.precision != TREE_OT_PREC_FP32 && o.precision != TREE_OT_PREC_FP64)
     return fail(TREE_OT_ERR_ARG, "unknown precision");
-  if (o.apply_mode != TREE_OT_APPLY_AUTO && o.apply_mode != TREE_OT_APPLY_LSE)
+  if (o.apply_mode != TREE_OT_APPLY_AUTO && o.apply_mode != TREE_OT_APPLY_LSE && o.apply_mode != TREE_OT_APPLY_BF16)
     return fail(TREE_OT_ERR_ARG, "unknown apply_mode");
+  if (o.apply_mode == TREE_OT_APPLY_BF16 &&
+      (!(o.refine_tol >= 0.0) || !(o.absorb_tau > 0.0) || o.absorb_tau > 100.0 || o.lowp_start < 0))
+    return fail(TREE_OT_ERR_ARG, "BF16 mode needs refine_tol >= 0, 0 < absorb_tau <= 100 and lowp_start >= 0");
   if (!(o.tol >= 0.0) || o.max_half_steps < 0 || o.check_every < 2 || (o.check_every & 1))
     return fail(TREE_OT_ERR_ARG, "tol >= 0, max_half_steps >= 0 and an even check_every >= 2 are required");
   if (o.tol_kind != TREE_OT_TOL_SUM && o.tol_kind != TREE_OT_TOL_MAX) return fail(TREE_OT_ERR_ARG, "unknown tol_kind");
@@ -626,6 +974,8 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       if (nd.fixed) mu.assign(P.marginal[j], P.marginal[j] + nd.n);
       h->mu.push_back(std::move(mu));
     }
+    pd.edge_begin = ebase;
+    pd.edge_count = J - 1;
     h->probs.push_back(pd);
     for (int32_t e = 0; e < J - 1; ++e) {
       EdgeD ed{};
@@ -674,49 +1024,37 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   h->part_len = part_off;
   h->nzchunks = chunk_base;
 
-  // apply tasks and node chunks per colour
-  for (size_t di = 0; di < h->dedges.size(); ++di) {
-    const DEdgeD& d = h->dedges[di];
-    const NodeD& own = h->nodes[d.owner];
-    const NodeD& nbn = h->nodes[d.nbr];
-    const ProbD& pd = h->probs[d.prob];
-    std::vector<Task>& tl = h->tasks[own.colour];
-    const bool dense = pd.cost_kind == TREE_OT_COST_DENSE_F32;
-    if (h->fp64) {
-      for (int32_t o0 = 0; o0 < own.n; o0 += 64)
-        tl.push_back(Task{(int32_t)di, dense ? (d.dir == 0 ? TASK_ROW : TASK_COL) : TASK_RECOMP, o0,
-                          std::min(64, own.n - o0), 0, nbn.n, 0, 0});
-    } else if (dense && d.dir == 0) {
-      for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
+  // device task arrays are sized for the finest output blocking the autotuner may pick
+  build_apply_tasks(h, 256);
+  h->task_cap[0] = (int64_t)h->tasks[0].size();
+  h->task_cap[1] = (int64_t)h->tasks[1].size();
+  build_apply_tasks(h, kRecOut);
+  // absorbed BF16 phase: apply tasks per colour and absorption blocks (stored-cost edges only)
+  h->lowp = o.apply_mode == TREE_OT_APPLY_BF16 && !h->fp64;
+  if (h->lowp) {
+    bool any = false;
+    for (size_t di = 0; di < h->dedges.size(); ++di) {
+      const DEdgeD& d = h->dedges[di];
+      if (h->probs[d.prob].cost_kind != TREE_OT_COST_DENSE_F32) continue;
+      any = true;
+      const NodeD& own = h->nodes[d.owner];
+      const NodeD& nbn = h->nodes[d.nbr];
+      std::vector<Task>& tl = h->btasks[own.colour];
+      if (d.dir == 0) {
+        for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
+          for (int32_t s = 0; s < d.nsplit; ++s)
+            tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
+                              std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
+        for (int32_t o0 = 0; o0 < own.n; o0 += 64)
+          h->atasks.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(64, own.n - o0), 0, nbn.n, 0, 0});
+      } else {
         for (int32_t s = 0; s < d.nsplit; ++s)
-          tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
-                            std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
-    } else if (dense) {
-      for (int32_t s = 0; s < d.nsplit; ++s)
-        for (int32_t o0 = 0; o0 < own.n; o0 += kColCols)
-          tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kColCols, own.n - o0), s * kColRows,
-                            std::min(kColRows, nbn.n - s * kColRows), s, 0});
-    } else {
-      for (int32_t o0 = 0; o0 < own.n; o0 += kRecOut)
-        for (int32_t s = 0; s < d.nsplit; ++s)
-          tl.push_back(Task{(int32_t)di, TASK_RECOMP, o0, std::min(kRecOut, own.n - o0), s * kRecRed,
-                            std::min(kRecRed, nbn.n - s * kRecRed), s, 0});
+          for (int32_t o0 = 0; o0 < own.n; o0 += kBfCols)
+            tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kBfCols, own.n - o0), s * kColRows,
+                              std::min(kColRows, nbn.n - s * kColRows), s, 0});
+      }
     }
-  }
-  // group each colour's tasks by kernel slot (stored costs; recomputed costs by dimension)
-  for (int c = 0; c < 2; ++c) {
-    auto slot_of = [&](const Task& t) {
-      if (h->fp64 || t.kind != TASK_RECOMP) return 0;
-      return (int)h->probs[h->dedges[t.dedge].prob].dim;
-    };
-    std::stable_sort(h->tasks[c].begin(), h->tasks[c].end(),
-                     [&](const Task& x, const Task& y) { return slot_of(x) < slot_of(y); });
-    for (const Task& t : h->tasks[c]) h->slot_count[c][slot_of(t)] += 1;
-    int32_t b = 0;
-    for (int s2 = 0; s2 < kApplySlots; ++s2) {
-      h->slot_begin[c][s2] = b;
-      b += h->slot_count[c][s2];
-    }
+    h->lowp = any;
   }
   for (size_t j = 0; j < h->nodes.size(); ++j) {
     const NodeD& nd = h->nodes[j];
@@ -737,12 +1075,12 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   if ((rc = h->alloc(&h->d_probs, num_probs)) || (rc = h->alloc(&h->d_nodes, NN)) ||
       (rc = h->alloc(&h->d_edges, NE)) || (rc = h->alloc(&h->d_dedges, ND)) ||
       (rc = h->alloc(&h->d_node_dedges, (int64_t)h->node_dedges.size())) ||
-      (rc = h->alloc(&h->d_tasks[0], (int64_t)h->tasks[0].size())) ||
-      (rc = h->alloc(&h->d_tasks[1], (int64_t)h->tasks[1].size())) ||
+      (rc = h->alloc(&h->d_tasks[0], h->task_cap[0])) || (rc = h->alloc(&h->d_tasks[1], h->task_cap[1])) ||
+      (rc = h->alloc(&h->d_queue, 2 * 2 * kApplySlots)) ||
       (rc = h->alloc(&h->d_chunks[0], (int64_t)h->chunks[0].size())) ||
       (rc = h->alloc(&h->d_chunks[1], (int64_t)h->chunks[1].size())) ||
       (rc = h->alloc(&h->d_check_tasks, (int64_t)h->check_tasks.size())) || (rc = h->alloc(&h->d_f, h->vec_len)) ||
-      (rc = h->alloc(&h->d_m, h->vec_len)) || (rc = h->alloc(&h->d_hh, h->vec_len)) ||
+      (rc = h->alloc(&h->d_m, h->vec_len)) || (rc = h->alloc(&h->d_fr, h->vec_len)) || (rc = h->alloc(&h->d_hh, h->vec_len)) ||
       (rc = h->alloc(&h->d_hl, h->vec_len)) || (rc = h->alloc(&h->d_ah, h->vec_len)) ||
       (rc = h->alloc(&h->d_al, h->vec_len)) || (rc = h->alloc(&h->d_marg, h->vec_len)) ||
       (rc = h->alloc(&h->d_Z, NN)) || (rc = h->alloc(&h->d_rho, NN)) || (rc = h->alloc(&h->d_logg, h->node_len)) ||
@@ -752,13 +1090,29 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = h->alloc(&h->d_res_max, (int64_t)kResidRing * num_probs)) || (rc = h->alloc(&h->d_done, num_probs)) ||
       (rc = h->alloc(&h->d_done_at, num_probs)) || (rc = h->alloc(&h->d_node_arrive, NN)) ||
       (rc = h->alloc(&h->d_node_count, num_probs)) || (rc = h->alloc(&h->d_launch_count, 1)) ||
-      (rc = h->alloc(&h->d_hs, 1)) || (rc = h->alloc(&h->d_err, 1)) || (rc = h->alloc(&h->d_scan, 1)) ||
+      (rc = h->alloc(&h->d_hs, 1)) || (rc = h->alloc(&h->d_ptol, num_probs)) || (rc = h->alloc(&h->d_err, 1)) || (rc = h->alloc(&h->d_scan, 1)) ||
       (rc = h->alloc(&h->d_edge_tc, NE)) || (rc = h->alloc(&h->d_edge_mass, NE)))
     return bail(rc);
   if (h->fp64) {
     if ((rc = h->alloc(&h->d_part64, h->part_len))) return bail(rc);
   } else {
     if ((rc = h->alloc(&h->d_part32, h->part_len))) return bail(rc);
+  }
+  if ((rc = h->alloc(&h->d_lowp, num_probs)) || (rc = h->alloc(&h->d_drift, NE)) ||
+      (rc = h->alloc(&h->d_lowp_span, 2 * (int64_t)num_probs)) || (rc = h->alloc(&h->d_absorb_count, 1)))
+    return bail(rc);
+  if (h->lowp) {
+    if ((rc = h->alloc(&h->d_bh, h->vec_len)) || (rc = h->alloc(&h->d_bl, h->vec_len)) ||
+        (rc = h->alloc(&h->d_arho, h->vec_len)) ||
+        (rc = h->alloc(&h->d_btasks[0], (int64_t)h->btasks[0].size())) ||
+        (rc = h->alloc(&h->d_btasks[1], (int64_t)h->btasks[1].size())) ||
+        (rc = h->alloc(&h->d_atasks, (int64_t)h->atasks.size())))
+      return bail(rc);
+    for (EdgeD& ed : h->edges) {
+      if (h->probs[h->nodes[ed.a].prob].cost_kind != TREE_OT_COST_DENSE_F32) continue;
+      ed.ldk = align_up(ed.nb, 8);
+      if ((rc = h->alloc(&ed.K, (int64_t)ed.na * ed.ldk))) return bail(rc);
+    }
   }
 
   auto up = [&](void* dst, const void* src, size_t bytes) -> int {
@@ -842,6 +1196,10 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = up(h->d_chunks[1], h->chunks[1].data(), sizeof(NodeChunk) * h->chunks[1].size())) ||
       (rc = up(h->d_check_tasks, h->check_tasks.data(), sizeof(Task) * h->check_tasks.size())))
     return bail(rc);
+  if (h->lowp && ((rc = up(h->d_btasks[0], h->btasks[0].data(), sizeof(Task) * h->btasks[0].size())) ||
+                  (rc = up(h->d_btasks[1], h->btasks[1].data(), sizeof(Task) * h->btasks[1].size())) ||
+                  (rc = up(h->d_atasks, h->atasks.data(), sizeof(Task) * h->atasks.size()))))
+    return bail(rc);
   int32_t bad = 0;
   {
     cudaError_t ce = cudaMemcpyAsync(&bad, h->d_scan, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -854,12 +1212,33 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int slot = 0; slot < kApplySlots; ++slot) h->apply_grid[slot] = sms * apply_ctas_per_sm(slot);
+  h->sms = sms;
+  for (int slot = 0; slot < kApplySlots; ++slot) {
+    h->apply_grid[slot] = sms * apply_ctas_per_sm(slot, 0);
+    for (int v = 0; v < 2; ++v) h->rec_grid[v][slot] = sms * apply_ctas_per_sm(slot, v);
+  }
+  h->bf16_grid = sms * apply_bf16_ctas_per_sm();
   {
     cudaError_t ce = cudaStreamCreateWithFlags(&h->hstream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
   }
+  {
+    // the staged kernel rounds operand copies up to 16 bytes: the arena pads stay zero
+    cudaError_t ce = cudaMemsetAsync(h->d_hh, 0, sizeof(float) * h->vec_len, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->d_hl, 0, sizeof(float) * h->vec_len, s);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "operand memset"));
+  }
   if ((rc = reset_state(h, s))) return bail(rc);
+  if (o.autotune && !h->fp64 && (rc = autotune_recompute(h, s))) return bail(rc);
+  if (!h->fp64) {
+    if ((rc = upload_stream_tasks(h, s))) return bail(rc);
+    if (o.flags & TREE_OT_OPT_DENSE_TMA) {
+      if (!apply_tma_available()) return bail(fail(TREE_OT_ERR_CUDA, "staged edge apply unavailable"));
+      h->dense_tma = 1;
+    } else if (!(o.flags & TREE_OT_OPT_DENSE_LDG) && o.autotune && (rc = autotune_dense(h, s))) {
+      return bail(rc);
+    }
+  }
   {
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize(create)"));
@@ -870,6 +1249,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
 
 int tree_ot_destroy(tree_ot_handle* h) {
   if (!h) return TREE_OT_OK;
+  if (h->d_setbuf) cudaFree(h->d_setbuf);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->hstream) cudaStreamDestroy(h->hstream);
   for (void* p : h->owned) cudaFree(p);
@@ -921,34 +1301,79 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
   if (h->hs_host % 2) RC_TRY(queue_half_steps(h, 1, true, s));
   bool use_graph = h->opt.use_graph != 0;
   if (use_graph) RC_TRY(build_graph(h, G));
-  while (h->hs_host < h->opt.max_half_steps) {
-    const int64_t left = h->opt.max_half_steps - h->hs_host;
-    if (use_graph && left >= G) {
-      CUDA_TRY(cudaGraphLaunch(h->graph, s));
-      h->hs_host += G;
-    } else {
-      RC_TRY(queue_half_steps(h, std::min<int64_t>(G, left), true, s));
+  // Certification: a problem retires on the FP32 stopping quantity of the
+  // half-step kernels; the FP64-grade check of its returned iterate decides.
+  // If the check exceeds tol, the problem resumes with its threshold lowered in
+  // proportion, up to kCertifyRounds times, and only while each round gains at
+  // least 10% (else the FP32 iterate has reached its accuracy floor).
+  constexpr int kCertifyRounds = 8;
+  std::vector<double> prev_got(h->nprob, INFINITY);
+  for (int cert = 0;; ++cert) {
+    while (h->hs_host < h->opt.max_half_steps) {
+      const int64_t left = h->opt.max_half_steps - h->hs_host;
+      if (use_graph && left >= G) {
+        CUDA_TRY(cudaGraphLaunch(h->graph, s));
+        h->hs_host += G;
+      } else {
+        RC_TRY(queue_half_steps(h, std::min<int64_t>(G, left), true, s));
+      }
+      CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(&err, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (err & 2) return fail(TREE_OT_ERR_TIMEOUT, "a bounded wait in the staged edge apply ran out");
+      if (err) return fail(TREE_OT_ERR_NONFINITE, "a potential became non-finite (an infeasible or degenerate input)");
+      bool all = true;
+      for (int p = 0; p < h->nprob; ++p) all = all && h->h_done[p];
+      if (all) break;
     }
     CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(&err, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(
+        cudaMemcpyAsync(h->h_done_at.data(), h->d_done_at, sizeof(int64_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+    h->h_lowp_span.assign(2 * h->nprob, 0);
+    CUDA_TRY(cudaMemcpyAsync(h->h_lowp_span.data(), h->d_lowp_span, sizeof(int64_t) * 2 * h->nprob,
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&h->h_absorb_count, h->d_absorb_count, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (err) return fail(TREE_OT_ERR_NONFINITE, "a potential became non-finite (an infeasible or degenerate input)");
-    bool all = true;
-    for (int p = 0; p < h->nprob; ++p) all = all && h->h_done[p];
-    if (all) break;
+    RC_TRY(run_check(h, s));
+    if (cert >= kCertifyRounds || h->hs_host >= h->opt.max_half_steps) break;
+    std::vector<tree_ot_result> chk(h->nprob);
+    fill_results(h, chk.data());
+    bool resume = false;
+    for (int p = 0; p < h->nprob; ++p) {
+      if (!h->h_done[p]) continue;
+      const double got = h->opt.tol_kind == TREE_OT_TOL_MAX ? chk[p].max_marginal_l1 : chk[p].residual_sum_l1;
+      if (!(got > h->opt.tol)) continue;
+      // no gain since the last round: the FP32 iterate's accuracy floor is above tol
+      if (!(got < 0.9 * prev_got[p])) continue;
+      prev_got[p] = got;
+      h->h_ptol[p] *= std::min(0.9, std::max(0.1, 0.9 * h->opt.tol / got));
+      h->h_done[p] = 0;
+      resume = true;
+      // the problem's residual ring restarts from zero
+      static const double zeros[kResidRing] = {};
+      CUDA_TRY(cudaMemcpy2DAsync(h->d_res_sum + p, sizeof(double) * h->nprob, zeros, sizeof(double),
+                                 sizeof(double), kResidRing, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpy2DAsync(h->d_res_max + p, sizeof(unsigned long long) * h->nprob, zeros, sizeof(double),
+                                 sizeof(double), kResidRing, cudaMemcpyHostToDevice, s));
+    }
+    if (!resume) break;
+    CUDA_TRY(cudaMemcpyAsync(h->d_ptol, h->h_ptol.data(), sizeof(double) * h->nprob, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h->d_done, h->h_done.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
   }
-  CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(
-      cudaMemcpyAsync(h->h_done_at.data(), h->d_done_at, sizeof(int64_t) * h->nprob, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  RC_TRY(run_check(h, s));
+  // converged = retired and certified by the check
+  std::vector<tree_ot_result> fin(h->nprob);
+  fill_results(h, fin.data());
   h->last_status.assign(h->nprob, TREE_OT_OK);
   bool any_nc = false;
-  for (int p = 0; p < h->nprob; ++p)
-    if (!h->h_done[p]) {
+  for (int p = 0; p < h->nprob; ++p) {
+    const double got = h->opt.tol_kind == TREE_OT_TOL_MAX ? fin[p].max_marginal_l1 : fin[p].residual_sum_l1;
+    if (!h->h_done[p] || got > h->opt.tol) {
       h->last_status[p] = TREE_OT_NOT_CONVERGED;
       any_nc = true;
     }
+  }
   h->last_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (results) fill_results(h, results);
   return any_nc ? TREE_OT_NOT_CONVERGED : TREE_OT_OK;
@@ -1021,10 +1446,84 @@ int tree_ot_set_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, i
   return TREE_OT_OK;
 }
 
+namespace {
+// Validates the (problem, directed edge) items of a batched potential call,
+// uploads their global directed-edge indices into the handle's item buffer
+// (grown as needed) and returns the device list and record array.
+int stage_items(tree_ot_handle* h, cudaStream_t s, int32_t count, const int32_t* probs, const int32_t* dedges,
+                int64_t ld, int32_t** d_dlist, DEdgeD** d_picked) {
+  std::vector<int32_t> dlist(count);
+  for (int32_t i = 0; i < count; ++i) {
+    const int32_t p = probs[i], d = dedges[i];
+    if (p < 0 || p >= h->nprob || d < 0 || d >= 2 * (h->prob_nodes[p] - 1))
+      return fail(TREE_OT_ERR_ARG, "item " + std::to_string(i) + ": bad problem or directed edge");
+    dlist[i] = 2 * h->prob_edge_base[p] + d;
+    if (h->nodes[h->dedges[dlist[i]].owner].n > ld)
+      return fail(TREE_OT_ERR_ARG, "item " + std::to_string(i) + ": row stride ld is smaller than n_owner");
+  }
+  if (count > h->setbuf_cap) {
+    if (h->d_setbuf) {
+      CUDA_TRY(cudaStreamSynchronize(s));
+      cudaFree(h->d_setbuf);
+      h->d_setbuf = nullptr;
+      h->setbuf_cap = 0;
+    }
+    CUDA_TRY(cudaMalloc(&h->d_setbuf, align_up(sizeof(int32_t) * (size_t)count, 256) + sizeof(DEdgeD) * (size_t)count));
+    h->setbuf_cap = count;
+  }
+  *d_dlist = (int32_t*)h->d_setbuf;
+  *d_picked = (DEdgeD*)((char*)h->d_setbuf + align_up(sizeof(int32_t) * (size_t)h->setbuf_cap, 256));
+  CUDA_TRY(cudaMemcpyAsync(*d_dlist, dlist.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+  // the pageable source is read before the call returns, so dlist may go out of scope
+  return TREE_OT_OK;
+}
+}  // namespace
+
+int tree_ot_get_potentials_batch(tree_ot_handle* h, void* cuda_stream, int32_t count, const int32_t* probs,
+                                 const int32_t* dedges, float* values, int64_t ld, uint32_t flags) {
+  g_err.clear();
+  if (!h || count < 0 || (count > 0 && (!probs || !dedges || !values)))
+    return fail(TREE_OT_ERR_ARG, "bad handle, count or pointer");
+  if (count == 0) return TREE_OT_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int32_t* d_dlist = nullptr;
+  DEdgeD* d_picked = nullptr;
+  RC_TRY(stage_items(h, s, count, probs, dedges, ld, &d_dlist, &d_picked));
+  CUDA_TRY(launch_get_potentials(d_dlist, count, h->d_dedges, h->d_nodes, h->d_probs, h->d_Z, h->d_f, values, ld,
+                                 (flags & TREE_OT_GET_CENTRED) != 0, s));
+  return TREE_OT_OK;
+}
+
+int tree_ot_set_potentials_batch(tree_ot_handle* h, void* cuda_stream, int32_t count, const int32_t* probs,
+                                 const int32_t* dedges, const float* values, int64_t ld) {
+  g_err.clear();
+  if (!h || count < 0 || (count > 0 && (!probs || !dedges || !values)))
+    return fail(TREE_OT_ERR_ARG, "bad handle, count or pointer");
+  if (count == 0) return TREE_OT_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int32_t* d_dlist = nullptr;
+  DEdgeD* d_picked = nullptr;
+  RC_TRY(stage_items(h, s, count, probs, dedges, ld, &d_dlist, &d_picked));
+  CUDA_TRY(cudaMemsetAsync(h->d_scan, 0, sizeof(int32_t), s));
+  CUDA_TRY(launch_set_potentials(values, ld, d_dlist, count, h->d_dedges, h->d_nodes, h->d_probs, h->d_Z, h->d_f,
+                                 d_picked, h->d_scan, false, s));
+  int32_t bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, h->d_scan, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (bad) return fail(TREE_OT_ERR_NONFINITE, "potential entries must be finite");
+  CUDA_TRY(launch_set_potentials(values, ld, d_dlist, count, h->d_dedges, h->d_nodes, h->d_probs, h->d_Z, h->d_f,
+                                 d_picked, h->d_scan, true, s));
+  CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, d_picked, h->d_nodes, h->d_probs, count, kLog2e, true, h->d_hh,
+                          h->d_hl, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->have_check = false;
+  return TREE_OT_OK;
+}
+
 int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
   g_err.clear();
   if (!h || !stats || nstats < 0) return fail(TREE_OT_ERR_ARG, "bad handle or stats pointer");
-  const int64_t v[9] = {(int64_t)h->dedges.size(),
+  const int64_t v[13] = {(int64_t)h->dedges.size(),
                         (int64_t)h->edges.size(),
                         h->elems,
                         h->matrix_bytes,
@@ -1032,8 +1531,12 @@ int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
                         (int64_t)h->tasks[1].size(),
                         h->device_bytes,
                         (int64_t)h->chunks[0].size(),
-                        (int64_t)h->chunks[1].size()};
-  for (int32_t i = 0; i < nstats && i < 9; ++i) stats[i] = v[i];
+                        (int64_t)h->chunks[1].size(),
+                        (int64_t)h->rec_ob,
+                        (int64_t)h->grid_mult,
+                        (int64_t)h->rec_variant,
+                        (int64_t)h->dense_tma};
+  for (int32_t i = 0; i < nstats && i < 13; ++i) stats[i] = v[i];
   return TREE_OT_OK;
 }
 

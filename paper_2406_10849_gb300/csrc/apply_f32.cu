@@ -23,7 +23,7 @@
 // row with a warp-uniform frame, lanes across 1024 columns), COL (stored matrix,
 // reduce down columns: a warp owns 128 columns, 8 warps split the rows and merge
 // through shared memory) -- both in apply_dense_kernel, where each term is formed
-// twice (maximum first, then the sum) so no term array stays live -- and RECOMP
+// once (maximum and sum together) and only re-formed when a frame moves -- and RECOMP
 // (squared-Euclidean cost recomputed from coordinates: each thread owns 4
 // outputs, reduction points staged in shared memory) in apply_recomp_kernel<D>.
 #include <algorithm>
@@ -40,6 +40,7 @@ namespace {
 
 #define kInf (__int_as_float(0x7f800000))
 constexpr float kWindow = 12.f;   // a frame up to this far above the chunk maximum is kept
+constexpr int kRecPts = 4;        // RECOMP: reduction points per frame check (per thread: 4 outputs x 4)
 
 __device__ __forceinline__ float quant(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
 
@@ -50,11 +51,25 @@ __device__ __forceinline__ float arg1(float hh, float R, float c, float shi, flo
   return t + hl;
 }
 
+// the four terms t of one float4 of costs against one float4 of operand
+__device__ __forceinline__ void terms4(float4 c, float4 H, float4 L, float2 negR, float2 nhi, float2 nlo,
+                                       float2& t01, float2& t23) {
+  t01 = fma2(make_float2(c.x, c.y), nhi, add2(make_float2(H.x, H.y), negR));
+  t23 = fma2(make_float2(c.z, c.w), nhi, add2(make_float2(H.z, H.w), negR));
+  t01 = add2(fma2(make_float2(c.x, c.y), nlo, t01), make_float2(L.x, L.y));
+  t23 = add2(fma2(make_float2(c.z, c.w), nlo, t23), make_float2(L.z, L.w));
+}
+
+// ROW task: rows o0..o0+ocount of the stored matrix against 1024 columns; one
+// warp per row, the task's operand staged in shared memory.  Every term is
+// formed once (maximum and sum relative to the row's frame in one pass); only
+// when the maximum leaves the frame's window (early half-steps) is the row
+// summed again from the moved frame, so results equal those of a separate
+// maximum pass.
 __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const EdgeD e = A.edges[d.edge];
   const ProbD P = A.probs[d.prob];
-  const float shi = P.s2, slo = P.s2_lo;
   const int n_owner = e.na;
   float* sh = sm;
   float* sl = sm + kRowCols;
@@ -69,7 +84,7 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const int nvec = (t.rcount + 3) >> 2;
   const float4* sh4 = reinterpret_cast<const float4*>(sh);
   const float4* sl4 = reinterpret_cast<const float4*>(sl);
-  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
+  const float2 nhi = make_float2(-P.s2, -P.s2), nlo = make_float2(-P.s2_lo, -P.s2_lo);
   for (int r = warp; r < t.ocount; r += kApplyThreads / 32) {
     const int x = t.o0 + r;
     const float4* row = reinterpret_cast<const float4*>(e.C + (int64_t)x * e.ld + t.r0);
@@ -79,39 +94,30 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
       const int v = lane + 32 * i;
       c[i] = v < nvec ? ldg_stream(row + v) : make_float4(kInf, kInf, kInf, kInf);
     }
-    float R = quant(frame_of(A.m[d.off + x]));  // warp-uniform
-    // pass 1: maximum of the terms relative to the current frame
-    float cm = -kInf;
+    float R = A.fr[d.off + x];  // warp-uniform, on the grid
+    float cm = -kInf, acc = 0.f;
     {
       const float2 negR = make_float2(-R, -R);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int v = lane + 32 * i;
-        const float4 H = sh4[v];
-        const float4 L = sl4[v];
-        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(make_float2(H.x, H.y), negR));
-        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(make_float2(H.z, H.w), negR));
-        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), make_float2(L.x, L.y));
-        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), make_float2(L.z, L.w));
+        float2 t01, t23;
+        terms4(c[i], sh4[v], sl4[v], negR, nhi, nlo, t01, t23);
         cm = max3f(cm, t01.x, t01.y);
         cm = max3f(cm, t23.x, t23.y);
+        acc += (ex2(t01.x) + ex2(t01.y)) + (ex2(t23.x) + ex2(t23.y));
       }
     }
     const float cw = warp_max(cm);
-    if ((cw > 0.5f || cw < -kWindow) && cw > -kInf) R += quant(cw);  // warp-uniform move onto the grid
-    // pass 2: the terms from the final frame, pairwise-summed
-    float acc = 0.f;
-    {
+    if ((cw > 0.5f || cw < -kWindow) && cw > -kInf) {  // warp-uniform: move onto the grid, sum again
+      R += quant(cw);
+      acc = 0.f;
       const float2 negR = make_float2(-R, -R);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int v = lane + 32 * i;
-        const float4 H = sh4[v];
-        const float4 L = sl4[v];
-        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(make_float2(H.x, H.y), negR));
-        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(make_float2(H.z, H.w), negR));
-        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), make_float2(L.x, L.y));
-        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), make_float2(L.z, L.w));
+        float2 t01, t23;
+        terms4(c[i], sh4[v], sl4[v], negR, nhi, nlo, t01, t23);
         acc += (ex2(t01.x) + ex2(t01.y)) + (ex2(t23.x) + ex2(t23.y));
       }
     }
@@ -135,11 +141,15 @@ __device__ __forceinline__ float2 merge_pieces(const float2* p, int n, int strid
   return make_float2(Rm, S);
 }
 
+// COL task: 128 columns (4 per lane) of the stored matrix against up to 512
+// rows, split over the 8 warps.  Per chunk of 8 rows every term is formed once
+// (maximum and sum together); a column whose maximum leaves its frame's window
+// has the chunk summed again from the moved frame (results equal those of a
+// separate maximum pass).
 __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const EdgeD e = A.edges[d.edge];
   const ProbD P = A.probs[d.prob];
-  const float shi = P.s2, slo = P.s2_lo;
   const int n_owner = e.nb;
   float* sh = sm;
   float* sl = sm + kColRows;
@@ -160,10 +170,10 @@ __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
   float R[4], acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    R[k] = (lane_on && c0 + k < t.ocount) ? quant(frame_of(A.m[d.off + t.o0 + c0 + k])) : 0.f;
+    R[k] = (lane_on && c0 + k < t.ocount) ? A.fr[d.off + t.o0 + c0 + k] : 0.f;
     acc[k] = 0.f;
   }
-  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
+  const float2 nhi = make_float2(-P.s2, -P.s2), nlo = make_float2(-P.s2_lo, -P.s2_lo);
   const float* base = e.C + t.o0 + c0;
   for (int rr = rr0; rr < rr1; rr += 8) {
     float4 c[8];
@@ -177,8 +187,8 @@ __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
       hh[i] = ok ? sh[xr] : 0.f;
       hl[i] = ok ? sl[xr] : 0.f;
     }
-    // pass 1: per-column maximum of this chunk relative to the current frames
     float cm[4] = {-kInf, -kInf, -kInf, -kInf};
+    float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
     {
       const float2 nR01 = make_float2(-R[0], -R[1]);
       const float2 nR23 = make_float2(-R[2], -R[3]);
@@ -193,36 +203,36 @@ __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
         cm[1] = fmaxf(cm[1], t01.y);
         cm[2] = fmaxf(cm[2], t23.x);
         cm[3] = fmaxf(cm[3], t23.y);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if ((cm[k] > 0.5f || (acc[k] == 0.f && cm[k] < -kWindow)) && cm[k] > -kInf) {
-        const float Rn = R[k] + quant(cm[k]);
-        acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
-        R[k] = Rn;
-      }
-    }
-    // pass 2: terms from the (possibly moved) frames
-    {
-      const float2 nR01 = make_float2(-R[0], -R[1]);
-      const float2 nR23 = make_float2(-R[2], -R[3]);
-      float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float2 h2 = make_float2(hh[i], hh[i]), l2 = make_float2(hl[i], hl[i]);
-        float2 t01 = fma2(make_float2(c[i].x, c[i].y), nhi, add2(h2, nR01));
-        float2 t23 = fma2(make_float2(c[i].z, c[i].w), nhi, add2(h2, nR23));
-        t01 = add2(fma2(make_float2(c[i].x, c[i].y), nlo, t01), l2);
-        t23 = add2(fma2(make_float2(c[i].z, c[i].w), nlo, t23), l2);
         a01 = add2(a01, make_float2(ex2(t01.x), ex2(t01.y)));
         a23 = add2(a23, make_float2(ex2(t23.x), ex2(t23.y)));
       }
-      acc[0] += a01.x;
-      acc[1] += a01.y;
-      acc[2] += a23.x;
-      acc[3] += a23.y;
     }
+    float part[4] = {a01.x, a01.y, a23.x, a23.y};
+    bool moved[4];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      moved[k] = (cm[k] > 0.5f || (acc[k] == 0.f && cm[k] < -kWindow)) && cm[k] > -kInf;
+      any = any || moved[k];
+    }
+    if (any) {  // rare after the first half-steps: re-sum the chunk for the moved columns
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!moved[k]) continue;
+        const float Rn = R[k] + quant(cm[k]);
+        acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
+        R[k] = Rn;
+        float sk = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float ck = k == 0 ? c[i].x : k == 1 ? c[i].y : k == 2 ? c[i].z : c[i].w;
+          sk += ex2(arg1(hh[i], Rn, ck, P.s2, P.s2_lo, hl[i]));
+        }
+        part[k] = sk;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += part[k];
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) comb[warp * kColCols + c0 + k] = make_float2(R[k], acc[k]);
@@ -249,35 +259,49 @@ __device__ __forceinline__ float sqdist(float px, float py, float pz, float4 q) 
   return c;
 }
 
+// The CTA's 8 warps form G = t.pad groups (1, 2, 4 or 8).  Every group owns all
+// of the task's outputs (4 per thread, up to 1024/G per task) and a 1/G share of
+// each staged chunk of reduction points; groups merge through shared memory at
+// the end.  Small supports (a few hundred points) thus keep all warps busy.
+//
+// The argument is t = (hh - R) - s |p - q|^2 + hl with s = s_hi + s_lo (exact
+// product inside the FMAs).  Staged values are stored duplicated, (v, v) pairs,
+// so every packed f32x2 operation reads its operands straight from shared
+// memory.
 template <int D>
 __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const NodeD own = A.nodes[d.owner];
   const NodeD nbn = A.nodes[d.nbr];
   const ProbD P = A.probs[d.prob];
+  const float2 nhi = make_float2(-P.s2_scaled, -P.s2_scaled), nlo = make_float2(-P.s2_scaled_lo, -P.s2_scaled_lo);
   const float shi = P.s2_scaled, slo = P.s2_scaled_lo;
   const int n_owner = own.n;
   const int tid = threadIdx.x;
-  float4* st = reinterpret_cast<float4*>(sm);  // [256]: (-q0, -q1, -q2 or hh, hh or hl)
-  float* stl = sm + 4 * kApplyThreads;         // [256]: hl (D == 3)
-  float px[4], py[4], pz[4], R[4], acc[4];
-  bool on[4];
+  const int G = t.pad;
+  const int gs = kApplyThreads / G;  // threads per group
+  const int g = tid / gs, tg = tid - g * gs;
+  float4* sq = reinterpret_cast<float4*>(sm);                       // [256]: (-qx,-qx,-qy,-qy)
+  float4* sz = sq + kApplyThreads;                                  // [256]: (-qz,-qz, *, *) (D == 3)
+  float4* shl = sq + 2 * kApplyThreads;                             // [256]: (hh,hh,hl,hl)
+  float2* comb = reinterpret_cast<float2*>(sm + 12 * kApplyThreads);  // [G][4 gs] group results
+  float2 px01, px23, py01, py23, pz01, pz23;
+  float R[4], acc[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int lo = tid + kApplyThreads * i;
-    on[i] = lo < t.ocount;
-    const int o = t.o0 + (on[i] ? lo : 0);
+    const int lo = tg + gs * i;
+    const bool on = lo < t.ocount;
+    const int o = t.o0 + (on ? lo : 0);
     const float* p = A.coords + own.coord_off + (int64_t)o * D;
-    px[i] = p[0];
-    py[i] = D > 1 ? p[1] : 0.f;
-    pz[i] = D > 2 ? p[2] : 0.f;
-    R[i] = on[i] ? quant(frame_of(A.m[d.off + o])) : 0.f;
+    const float x0 = p[0], y0 = D > 1 ? p[1] : 0.f, z0 = D > 2 ? p[2] : 0.f;
+    if (i == 0) { px01.x = x0; py01.x = y0; pz01.x = z0; }
+    if (i == 1) { px01.y = x0; py01.y = y0; pz01.y = z0; }
+    if (i == 2) { px23.x = x0; py23.x = y0; pz23.x = z0; }
+    if (i == 3) { px23.y = x0; py23.y = y0; pz23.y = z0; }
+    R[i] = on ? A.fr[d.off + o] : 0.f;
     acc[i] = 0.f;
   }
-  const float2 nhi = make_float2(-shi, -shi), nlo = make_float2(-slo, -slo);
-  const float2 px01 = make_float2(px[0], px[1]), px23 = make_float2(px[2], px[3]);
-  const float2 py01 = make_float2(py[0], py[1]), py23 = make_float2(py[2], py[3]);
-  const float2 pz01 = make_float2(pz[0], pz[1]), pz23 = make_float2(pz[2], pz[3]);
+  const int per = kApplyThreads / G;  // staged points per group per chunk (multiple of kRecPts)
   for (int ch = 0; ch < t.rcount; ch += kApplyThreads) {
     __syncthreads();
     {
@@ -287,25 +311,23 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
       const float* q = A.coords + nbn.coord_off + (int64_t)y * D;
       const float hh = v ? A.hh[d.rev_off + y] : -kInf;
       const float hl = v ? A.hl[d.rev_off + y] : 0.f;
-      if (D == 3) {
-        st[tid] = make_float4(-q[0], -q[1], -q[2], hh);
-        stl[tid] = hl;
-      } else {
-        st[tid] = make_float4(-q[0], D > 1 ? -q[1] : 0.f, hh, hl);
-      }
+      const float qy = D > 1 ? -q[1] : 0.f;
+      sq[tid] = make_float4(-q[0], -q[0], qy, qy);
+      if (D == 3) sz[tid] = make_float4(-q[2], -q[2], 0.f, 0.f);
+      shl[tid] = make_float4(hh, hh, hl, hl);
     }
     __syncthreads();
     const int cnt = min(kApplyThreads, t.rcount - ch);
-    for (int j = 0; j < cnt; j += 8) {
-      float tv[4][8];
+    const int jend = min(g * per + per, cnt);
+    for (int j = g * per; j < jend; j += kRecPts) {
+      float tv[4][kRecPts];
       const float2 nR01 = make_float2(-R[0], -R[1]);
       const float2 nR23 = make_float2(-R[2], -R[3]);
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const float4 q = st[j + jj];  // entries past cnt hold hh = -inf: zero terms
-        const float hh = D == 3 ? q.w : q.z;
-        const float hl = D == 3 ? stl[j + jj] : q.w;
-        const float2 qx = make_float2(q.x, q.x);
+      for (int jj = 0; jj < kRecPts; ++jj) {
+        const float4 qq = sq[j + jj];  // entries past cnt hold hh = -inf: zero terms
+        const float4 hv = shl[j + jj];
+        const float2 qx = make_float2(qq.x, qq.y);
         float2 c01, c23;
         {
           const float2 dx01 = add2(px01, qx), dx23 = add2(px23, qx);
@@ -313,18 +335,19 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
           c23 = mul2(dx23, dx23);
         }
         if (D > 1) {
-          const float2 qy = make_float2(q.y, q.y);
+          const float2 qy = make_float2(qq.z, qq.w);
           const float2 dy01 = add2(py01, qy), dy23 = add2(py23, qy);
           c01 = fma2(dy01, dy01, c01);
           c23 = fma2(dy23, dy23, c23);
         }
         if (D > 2) {
-          const float2 qz = make_float2(q.z, q.z);
+          const float4 zz = sz[j + jj];
+          const float2 qz = make_float2(zz.x, zz.y);
           const float2 dz01 = add2(pz01, qz), dz23 = add2(pz23, qz);
           c01 = fma2(dz01, dz01, c01);
           c23 = fma2(dz23, dz23, c23);
         }
-        const float2 h2 = make_float2(hh, hh), l2 = make_float2(hl, hl);
+        const float2 h2 = make_float2(hv.x, hv.y), l2 = make_float2(hv.z, hv.w);
         float2 t01 = fma2(c01, nhi, add2(h2, nR01));
         float2 t23 = fma2(c23, nhi, add2(h2, nR23));
         t01 = add2(fma2(c01, nlo, t01), l2);
@@ -334,44 +357,75 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
         tv[2][jj] = t23.x;
         tv[3][jj] = t23.y;
       }
+      float cmk[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        float cm = max3f(tv[k][0], tv[k][1], tv[k][2]);
-        cm = max3f(cm, tv[k][3], tv[k][4]);
-        cm = max3f(cm, tv[k][5], tv[k][6]);
-        cm = fmaxf(cm, tv[k][7]);
-        if ((cm > 0.5f || (acc[k] == 0.f && cm < -kWindow)) && cm > -kInf) {
-          const float Rn = R[k] + quant(cm);
-          acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
-          R[k] = Rn;
+        cmk[k] = fmaxf(tv[k][0], tv[k][1]);
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const float4 q = st[j + jj];
-            const float hh = D == 3 ? q.w : q.z;
-            const float hl = D == 3 ? stl[j + jj] : q.w;
-            tv[k][jj] = arg1(hh, Rn, sqdist<D>(px[k], py[k], pz[k], q), shi, slo, hl);
+        for (int jj = 2; jj < kRecPts; jj += 2) cmk[k] = max3f(cmk[k], tv[k][jj], tv[k][jj + 1]);
+      }
+      // one test for the four outputs in the common case (frames fit, sums started)
+      const bool fresh = (acc[0] == 0.f) | (acc[1] == 0.f) | (acc[2] == 0.f) | (acc[3] == 0.f);
+      if (fresh || fmaxf(max3f(cmk[0], cmk[1], cmk[2]), cmk[3]) > 0.5f) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float cm = cmk[k];
+          if ((cm > 0.5f || (acc[k] == 0.f && cm < -kWindow)) && cm > -kInf) {
+            const float Rn = R[k] + quant(cm);
+            acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
+            R[k] = Rn;
+            const float pxk = k == 0 ? px01.x : k == 1 ? px01.y : k == 2 ? px23.x : px23.y;
+            const float pyk = k == 0 ? py01.x : k == 1 ? py01.y : k == 2 ? py23.x : py23.y;
+            const float pzk = k == 0 ? pz01.x : k == 1 ? pz01.y : k == 2 ? pz23.x : pz23.y;
+#pragma unroll
+            for (int jj = 0; jj < kRecPts; ++jj) {
+              const float4 qq = sq[j + jj];
+              const float4 hv = shl[j + jj];
+              const float dx = pxk + qq.x;
+              float c = dx * dx;
+              if (D > 1) {
+                const float dy = pyk + qq.z;
+                c = fmaf(dy, dy, c);
+              }
+              if (D > 2) {
+                const float dz = pzk + sz[j + jj].x;
+                c = fmaf(dz, dz, c);
+              }
+              tv[k][jj] = arg1(hv.x, Rn, c, shi, slo, hv.z);
+            }
           }
         }
-        const float a = (ex2(tv[k][0]) + ex2(tv[k][1])) + (ex2(tv[k][2]) + ex2(tv[k][3]));
-        const float b = (ex2(tv[k][4]) + ex2(tv[k][5])) + (ex2(tv[k][6]) + ex2(tv[k][7]));
-        acc[k] += a + b;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k += 2) {
+        float2 s01 = make_float2(ex2(tv[k][0]), ex2(tv[k + 1][0]));
+#pragma unroll
+        for (int jj = 1; jj < kRecPts; ++jj) s01 = add2(s01, make_float2(ex2(tv[k][jj]), ex2(tv[k + 1][jj])));
+        acc[k] += s01.x;
+        acc[k + 1] += s01.y;
       }
     }
   }
+  if (G == 1) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (on[i]) {
-      const int o = t.o0 + tid + kApplyThreads * i;
-      A.part32[d.part_off + (int64_t)t.split * n_owner + o] = make_float2(R[i], acc[i]);
-    }
+    for (int i = 0; i < 4; ++i)
+      if (tg + gs * i < t.ocount)
+        A.part32[d.part_off + (int64_t)t.split * n_owner + t.o0 + tg + gs * i] = make_float2(R[i], acc[i]);
+    return;
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) comb[g * (4 * gs) + tg + gs * i] = make_float2(R[i], acc[i]);
+  __syncthreads();
+  for (int c = tid; c < t.ocount; c += kApplyThreads)
+    A.part32[d.part_off + (int64_t)t.split * n_owner + t.o0 + c] = merge_pieces(comb + c, G, 4 * gs);
 }
 
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_dense_kernel(ApplyArgs A) {
   __shared__ __align__(16) float sm[2 * kColRows + 2 * 8 * kColCols];  // 12 KB
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
-    if (A.done[A.dedges[t.dedge].prob]) continue;
+    const int prob = A.dedges[t.dedge].prob;
+    if (A.done[prob] || A.lowp[prob] == 1) continue;  // retired, or in the absorbed BF16 phase
     if (t.kind == TASK_ROW)
       row_task(A, t, sm);
     else
@@ -379,14 +433,30 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_dense_kernel(ApplyArgs
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(kApplyThreads, 2) apply_recomp_kernel(ApplyArgs A) {
-  __shared__ __align__(16) float sm[5 * kApplyThreads];  // 5 KB
-  for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
+// Tasks come from a work queue (an atomic counter; tasks are sorted by cost on
+// the host), so uneven edges of a batch of trees balance across the CTAs.  The
+// last CTA to leave resets the counter for the next launch.
+template <int D, int MINB>
+__global__ void __launch_bounds__(kApplyThreads, MINB) apply_recomp_kernel(ApplyArgs A) {
+  __shared__ __align__(16) float sm[12 * kApplyThreads + 2 * 4 * kApplyThreads];  // 20 KB
+  __shared__ int s_ti;
+  for (;;) {
+    if (threadIdx.x == 0) s_ti = atomicAdd(&A.queue[0], 1);
+    __syncthreads();
+    const int ti = s_ti;
+    __syncthreads();
+    if (ti >= A.ntasks) break;
     const Task t = A.tasks[ti];
     if (A.done[A.dedges[t.dedge].prob]) continue;
     recomp_task<D>(A, t, sm);
-    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&A.queue[1], 1) == (int)gridDim.x - 1) {
+      A.queue[0] = 0;
+      A.queue[1] = 0;
+      __threadfence();
+    }
   }
 }
 
@@ -515,32 +585,38 @@ __global__ void noalloc_merge_kernel(const float2* part, int32_t n_rows, int32_t
 
 }  // namespace
 
-int apply_ctas_per_sm(int slot) {
+template <int D, int MINB>
+int occ_recomp() {
   int n = 0;
-  if (slot == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_dense_kernel, kApplyThreads, 0);
-  else if (slot == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<1>, kApplyThreads, 0);
-  else if (slot == 2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<2>, kApplyThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<3>, kApplyThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<D, MINB>, kApplyThreads, 0);
   return n > 0 ? n : 1;
 }
 
-cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int grid, cudaStream_t s) {
-  if (a.ntasks <= 0) return cudaSuccess;
-  if (slot == 0)
-    apply_dense_kernel<<<grid, kApplyThreads, 0, s>>>(a);
-  else if (slot == 1)
-    apply_recomp_kernel<1><<<grid, kApplyThreads, 0, s>>>(a);
-  else if (slot == 2)
-    apply_recomp_kernel<2><<<grid, kApplyThreads, 0, s>>>(a);
-  else
-    apply_recomp_kernel<3><<<grid, kApplyThreads, 0, s>>>(a);
-  return cudaGetLastError();
+int apply_ctas_per_sm(int slot, int variant) {
+  int n = 0;
+  if (slot == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_dense_kernel, kApplyThreads, 0);
+    return n > 0 ? n : 1;
+  }
+  if (variant == 0) return slot == 1 ? occ_recomp<1, 2>() : slot == 2 ? occ_recomp<2, 2>() : occ_recomp<3, 2>();
+  return slot == 1 ? occ_recomp<1, 3>() : slot == 2 ? occ_recomp<2, 3>() : occ_recomp<3, 3>();
 }
 
+cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int variant, int grid, cudaStream_t s) {
+  if (a.ntasks <= 0) return cudaSuccess;
+  if (slot == 0) {
+    apply_dense_kernel<<<grid, kApplyThreads, 0, s>>>(a);
+  } else if (variant == 0) {
+    if (slot == 1) apply_recomp_kernel<1, 2><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 2) apply_recomp_kernel<2, 2><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 3) apply_recomp_kernel<3, 2><<<grid, kApplyThreads, 0, s>>>(a);
+  } else {
+    if (slot == 1) apply_recomp_kernel<1, 3><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 2) apply_recomp_kernel<2, 3><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 3) apply_recomp_kernel<3, 3><<<grid, kApplyThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
 
 // ---- allocation-free entry point: host side ---------------------------------
 

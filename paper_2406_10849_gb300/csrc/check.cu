@@ -243,6 +243,50 @@ __global__ void operand_kernel(const double* f, const double* Z, const double* l
   }
 }
 
+// batched potential set: pass 0 flags non-finite values, pass 1 writes the
+// normalised potential f' = f + eps Z_owner and records the directed edge for
+// the operand refresh
+__global__ void set_potentials_kernel(const float* values, int64_t ld, const int32_t* dlist, int32_t i0,
+                                      const DEdgeD* dedges, const NodeD* nodes, const ProbD* probs, const double* Z,
+                                      double* f, DEdgeD* picked, int32_t* bad, int32_t write) {
+  const int i = i0 + blockIdx.y;
+  const DEdgeD d = dedges[dlist[i]];
+  const int n = nodes[d.owner].n;
+  const double ez = probs[d.prob].eps * Z[d.owner];
+  if (write && blockIdx.x == 0 && threadIdx.x == 0) picked[i] = d;
+  int local = 0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    const float v = values[(int64_t)i * ld + x];
+    if (!isfinite(v)) local = 1;
+    if (write) f[d.off + x] = (double)v + ez;
+  }
+  if (__syncthreads_or(local) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+// batched potential read: one CTA per item, f = f' - eps Z_owner in FP32,
+// optionally centred (mean over x subtracted, the mean taken in FP64)
+__global__ void get_potentials_kernel(const int32_t* dlist, int32_t i0, const DEdgeD* dedges, const NodeD* nodes,
+                                      const ProbD* probs, const double* Z, const double* f, float* values,
+                                      int64_t ld, int32_t centred) {
+  __shared__ double red[8];
+  const int i = i0 + blockIdx.x;
+  const DEdgeD d = dedges[dlist[i]];
+  const int n = nodes[d.owner].n;
+  const double ez = probs[d.prob].eps * Z[d.owner];
+  double mean = 0.0;
+  if (centred) {
+    double acc = 0.0;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) acc += f[d.off + x] - ez;
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    mean = tot / n;
+  }
+  for (int x = threadIdx.x; x < n; x += blockDim.x) values[(int64_t)i * ld + x] = (float)(f[d.off + x] - ez - mean);
+}
+
 // counts NaN and -inf entries of a padded dense cost (+inf is allowed)
 __global__ void scan_cost_kernel(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad) {
   int local = 0;
@@ -291,6 +335,28 @@ cudaError_t launch_operand(const double* f, const double* Z, const double* logg,
     const int32_t cnt = ndedges - d0 < 65535 ? ndedges - d0 : 65535;
     dim3 grid(4, cnt);
     operand_kernel<<<grid, 256, 0, s>>>(f, Z, logg, dedges, nodes, probs, d0, ndedges, scale, quantize, vh, vl);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_potentials(const float* values, int64_t ld, const int32_t* dlist, int32_t count,
+                                  const DEdgeD* dedges, const NodeD* nodes, const ProbD* probs, const double* Z,
+                                  double* f, DEdgeD* picked, int32_t* bad, bool write, cudaStream_t s) {
+  for (int32_t i0 = 0; i0 < count; i0 += 65535) {
+    const int32_t cnt = count - i0 < 65535 ? count - i0 : 65535;
+    dim3 grid(4, cnt);
+    set_potentials_kernel<<<grid, 256, 0, s>>>(values, ld, dlist, i0, dedges, nodes, probs, Z, f, picked, bad,
+                                               write ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_potentials(const int32_t* dlist, int32_t count, const DEdgeD* dedges, const NodeD* nodes,
+                                  const ProbD* probs, const double* Z, const double* f, float* values, int64_t ld,
+                                  bool centred, cudaStream_t s) {
+  for (int32_t i0 = 0; i0 < count; i0 += 65535) {
+    const int32_t cnt = count - i0 < 65535 ? count - i0 : 65535;
+    get_potentials_kernel<<<cnt, 256, 0, s>>>(dlist, i0, dedges, nodes, probs, Z, f, values, ld, centred ? 1 : 0);
   }
   return cudaGetLastError();
 }

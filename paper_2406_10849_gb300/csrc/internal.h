@@ -27,6 +27,7 @@ constexpr int kRecOut = 1024;          // RECOMP task: outputs per task (256 thr
 constexpr int kRecRed = 512;           // RECOMP task: reduction points per task
 constexpr int kNodeThreads = 256;
 constexpr int kNodeChunk = 512;        // node update: support points per CTA
+constexpr int kBfCols = 256;           // BF16 COL task: columns per task (32 lanes x 8)
 constexpr double kGrid = 1024.0;       // apply operands and frames live on a 2^-10 grid
 
 enum TaskKind : int32_t {
@@ -49,6 +50,8 @@ struct DEdgeD {
 struct EdgeD {
   const float* C;   // dense cost, rows = node a, row stride ld (multiple of 4); pad columns +inf
   int64_t ld;
+  uint16_t* K;      // absorbed BF16 Gibbs kernel (low-precision mode), row stride ldk (multiple of 8)
+  int64_t ldk;
   int32_t a, b;     // global node ids (rows a, columns b)
   int32_t na, nb;
 };
@@ -75,13 +78,29 @@ struct ProbD {
   int32_t dim;
   int32_t cost_kind;
   int32_t nodes_in_colour[2];
+  int32_t edge_begin, edge_count;  // global ids of this problem's edges
 };
 
 struct Task {
   int32_t dedge, kind;
   int32_t o0, ocount;   // output range (owner support)
   int32_t r0, rcount;   // reduction range (neighbour support)
-  int32_t split, pad;
+  int32_t split;
+  int32_t pad;          // RECOMP: warp groups sharing the task (1, 2, 4, 8); else 0
+};
+
+// A stored-cost (ROW / COL) task with every address resolved on the host, for
+// the bulk-copy staged kernel.  The tile's stage rows are C + r * ld: output
+// rows for ROW tasks, reduction rows for COL tasks.
+struct StreamTask {
+  const float* C;      // first element of the tile
+  int64_t ld;          // row stride of the cost (floats, multiple of 4)
+  int64_t m_off;       // frame sources m[m_off + i], i < ocount
+  int64_t h_off;       // reduction-side operand hh / hl[h_off + j], j < rcount
+  int64_t out_off;     // partials part32[out_off + i], i < ocount
+  int32_t kind, prob;
+  int32_t ocount, rcount;
+  float s2, s2_lo;     // log2(e) / eps as a two-float
 };
 
 struct ApplyArgs {
@@ -92,7 +111,8 @@ struct ApplyArgs {
   const NodeD* nodes;
   const ProbD* probs;
   const int32_t* done;       // per problem: 1 = retired
-  const double* m;           // latest messages (frames for the next apply)
+  const double* m;           // latest messages
+  const float* fr;           // their frames: log2 of the message on the 2^-10 grid (0 if not finite)
   const float* hh;           // operand (f/eps + log gamma) * log2(e), high part
   const float* hl;           // low part
   const double* f;           // potentials (FP64 path)
@@ -100,6 +120,31 @@ struct ApplyArgs {
   const float* coords;
   float2* part32;            // FP32 path partials: (frame R, sum) in base 2
   double2* part64;           // FP64 path partials: (max M, sum S) in base e
+  int32_t* queue;            // work-queue counters of this launch (next task, CTAs finished)
+  // low-precision (absorbed) phase
+  const int32_t* lowp;       // per problem: 1 = BF16 phase (the FP32 kernels skip it), else FP32
+  const float* bh;           // absorbed bases (operand at absorption), high / low parts
+  const float* bl;
+  const float* arho;         // row normalisers of the absorbed kernels (row side of each edge)
+  int32_t* err;              // error word: bit 1 = a bounded wait of a staged kernel ran out
+  const StreamTask* stasks;  // staged kernel: resolved stored-cost tasks (ntasks of them)
+};
+
+struct AbsorbArgs {
+  const Task* tasks;         // (dedge 2e, rows o0..o0+ocount) blocks of every stored-cost edge
+  int32_t ntasks;
+  const DEdgeD* dedges;
+  const EdgeD* edges;
+  const ProbD* probs;
+  const float* hh;
+  const float* hl;
+  float* bh;
+  float* bl;
+  float* arho;
+  const int32_t* lowp;
+  int32_t* drift;            // per edge: 1 = re-absorb
+  int32_t nedges;
+  unsigned long long* count; // edge absorptions performed
 };
 
 // Potentials are stored in a normalised form: f[d] holds f'_(j,k) with the
@@ -120,6 +165,7 @@ struct NodeArgs {
   int64_t* done_at;
   double* f;
   double* m;                 // raw merged message (before subtracting Z of the neighbour)
+  float* fr;                 // frame of m for the next apply (log2, 2^-10 grid)
   float* hh;
   float* hl;
   double* Z;                 // per node
@@ -139,8 +185,19 @@ struct NodeArgs {
   int64_t* hs;               // half-steps completed (device counter)
   int32_t* err;              // device error flags (bit 0: non-finite potential)
   double tol;
+  const double* ptol;        // per problem: the retirement threshold (tol, tightened by certification)
   int32_t tol_kind;
   int32_t retire;            // 1: retire problems whose stopping quantity < tol
+  // low-precision phase control (absorbed != 0 only for handles built for it)
+  int32_t absorbed;
+  int32_t* lowp;             // per problem: 2 = waiting for lowp_start, 1 = BF16 phase, 0 = FP32
+  const float* bh;
+  const float* bl;
+  int32_t* drift;            // per edge
+  double refine_tol;
+  float tau;                 // drift limit (log2 units)
+  int32_t lowp_start;
+  int64_t* lowp_span;        // per problem: half-steps at which the BF16 phase began / ended
 };
 
 // FP64-grade check of the current potentials.  Per element the exponent
@@ -168,11 +225,21 @@ struct CheckArgs {
 
 // ---- launchers (defined in the .cu files) --------------------------------
 // slot 0: stored-cost tasks (ROW/COL); slot D (1..3): recomputed squared-Euclidean tasks
-cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int grid, cudaStream_t s);
+// variant (recomputed costs): 0 = 2 CTAs per SM register budget, 1 = 3 CTAs per SM
+cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int variant, int grid, cudaStream_t s);
+// stored-cost (slot 0) tasks with bulk-copy staged rows; one CTA per SM, grid = SM count
+bool apply_tma_available();
+cudaError_t launch_apply_tma(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_apply_f64(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s);
 // v = (f'/eps - Z_owner + log gamma) * scale as FP32 (hi, lo); Z may be null.
 // quantize: hi on the 2^-10 grid (the apply operand), else hi = nearest float.
+cudaError_t launch_set_potentials(const float* values, int64_t ld, const int32_t* dlist, int32_t count,
+                                  const DEdgeD* dedges, const NodeD* nodes, const ProbD* probs, const double* Z,
+                                  double* f, DEdgeD* picked, int32_t* bad, bool write, cudaStream_t s);
+cudaError_t launch_get_potentials(const int32_t* dlist, int32_t count, const DEdgeD* dedges, const NodeD* nodes,
+                                  const ProbD* probs, const double* Z, const double* f, float* values, int64_t ld,
+                                  bool centred, cudaStream_t s);
 cudaError_t launch_operand(const double* f, const double* Z, const double* logg, const DEdgeD* dedges,
                            const NodeD* nodes, const ProbD* probs, int32_t ndedges, double scale, bool quantize,
                            float* vh, float* vl, cudaStream_t s);
@@ -182,7 +249,10 @@ cudaError_t launch_check(const CheckArgs& a, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
 cudaError_t launch_pad_copy(const float* src, int64_t src_ld, float* dst, int64_t dst_ld, int32_t rows,
                             int32_t cols, cudaStream_t s);
-int apply_ctas_per_sm(int slot);
+int apply_ctas_per_sm(int slot, int variant);
+int apply_bf16_ctas_per_sm();
+cudaError_t launch_apply_bf16(const ApplyArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_absorb(const AbsorbArgs& a, int grid, cudaStream_t s);
 // allocation-free single-matrix row apply (scratch in a file-scope device array)
 cudaError_t noalloc_scratch(float** out, int64_t* capacity_floats);
 int64_t noalloc_scratch_floats_needed(int32_t n_rows, int32_t n_cols);
@@ -190,4 +260,19 @@ cudaError_t launch_edge_apply_noalloc(const float* C, int64_t ld, int32_t n_rows
                                       float shi, float slo, double* m_out, float* scratch, cudaStream_t s);
 constexpr int kApplySlots = 4;
 
+}  // namespace treeot
+
+namespace treeot {
+// ---- warm-start MLP kernels (mlp.cu) ---------------------------------------
+cudaError_t mlp_gemm(const void* A, int lda, int ta, const void* B, int ldb, int tb, float* C, int ldc, int M, int N,
+                     int K, const float* bias, int accumulate, cudaStream_t s);
+cudaError_t mlp_gelu_fwd(const float* z, void* a16, int64_t n, cudaStream_t s);
+cudaError_t mlp_gelu_bwd(const float* da, const float* z, void* dz16, float* dz32, int64_t n, cudaStream_t s);
+cudaError_t mlp_to_bf16(const float* x, void* y, int64_t n, cudaStream_t s);
+cudaError_t mlp_input(const float* x, void* y, int64_t rows, int cols, int nlog, float floor_, float scale,
+                      cudaStream_t s);
+cudaError_t mlp_mse(const float* y, const float* t, float* dy32, void* dy16, int64_t n, double* loss, cudaStream_t s);
+cudaError_t mlp_colsum(const float* dz, int M, int N, float* db, cudaStream_t s);
+cudaError_t mlp_adam(float* w, const float* g, float* m1, float* m2, void* w16, int64_t n, float lr, float b1, float b2,
+                     float eps, float c1, float c2, cudaStream_t s);
 }  // namespace treeot

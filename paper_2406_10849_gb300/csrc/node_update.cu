@@ -99,6 +99,11 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
+// frame of a message for the next apply: log2 of it on the 2^-10 grid (0 when not finite)
+__device__ __forceinline__ float frame_grid(double m) {
+  return isfinite(m) ? (float)(rint(m * (kLog2e * kGrid)) * (1.0 / kGrid)) : 0.f;
+}
+
 template <bool F64>
 __device__ __forceinline__ double merged(const NodeArgs& A, const DEdgeD& d, int n_owner, int x) {
   if (F64) return merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
@@ -111,10 +116,14 @@ __device__ void fixed_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk&
   const double Zn = A.Z[d.nbr];
   double r = 0.0;
   bool bad = false;
+  // low-precision phase: flag the edge when the operand leaves its absorbed base
+  const bool track = A.absorbed && A.lowp[nd.prob] == 1;
+  bool drift = false;
   for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
     const int x = c.x0 + xi;
     const double mr = merged<F64>(A, d, nd.n, x);
     A.m[d.off + x] = mr;
+    A.fr[d.off + x] = frame_grid(mr);
     const double mi = mr - Zn;
     const double fo = A.f[d.off + x];
     const double lg = A.logg[nd.node_off + x];
@@ -133,8 +142,10 @@ __device__ void fixed_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk&
     }
     A.hh[d.off + x] = hi;
     A.hl[d.off + x] = lo;
+    if (track && hi > -INFINITY && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) drift = true;
   }
   if (bad) atomicOr(A.err, 1);
+  if (__syncthreads_or(drift) && threadIdx.x == 0) atomicOr(&A.drift[d.edge], 1);
   r = block_sum(r, red);
   if (threadIdx.x == 0) atomicAdd(&A.resid_acc[A.node_dedges[nd.dedge_begin]], r);
 }
@@ -144,6 +155,7 @@ __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& 
                            double* s_s, double* s_q, int node_id) {
   const int deg = nd.deg;
   const double Zold = A.Z[node_id];
+  const bool track = A.absorbed && A.lowp[nd.prob] == 1;
   const double inv_deg = 1.0 / (double)deg;
   bool bad = false;
   double smax = -INFINITY;
@@ -154,6 +166,7 @@ __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& 
       const DEdgeD d = A.dedges[A.node_dedges[nd.dedge_begin + i]];
       const double mr = merged<F64>(A, d, nd.n, x);
       A.m[d.off + x] = mr;
+      A.fr[d.off + x] = frame_grid(mr);
       const double mi = mr - A.Z[d.nbr];
       const double fo = A.f[d.off + x];
       qsum += expx<F64>((fo * P.inv_eps - Zold) + mi);
@@ -175,6 +188,7 @@ __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& 
     const DEdgeD d = A.dedges[di];
     const double Zk = A.Z[d.nbr];
     double r = 0.0;
+    bool drift = false;
     for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
       const int x = c.x0 + xi;
       const double mi = A.m[d.off + x] - Zk;
@@ -187,7 +201,9 @@ __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& 
       split2(g * kLog2e, hi, lo);
       A.hh[d.off + x] = hi;
       A.hl[d.off + x] = lo;
+      if (track && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) drift = true;
     }
+    if (__syncthreads_or(drift) && threadIdx.x == 0) atomicOr(&A.drift[d.edge], 1);
     r = block_sum(r, red);
     if (threadIdx.x == 0) atomicAdd(&A.resid_acc[di], r);
   }
@@ -251,7 +267,20 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
       const double rm = __longlong_as_double(
           (long long)*((volatile unsigned long long*)&A.res_max[slot * A.nprob + p]));
       const double crit = A.tol_kind == 1 ? rm : rs;
-      if (A.retire && crit < A.tol) {
+      const int lp = A.absorbed ? A.lowp[p] : 0;
+      if (lp == 2 && t_now + 1 >= A.lowp_start) {
+        // enter the low-precision phase: absorb every edge of the problem next
+        A.lowp[p] = 1;
+        A.lowp_span[2 * p] = t_now + 1;
+        for (int k = 0; k < P.edge_count; ++k) A.drift[P.edge_begin + k] = 1;
+      } else if (lp == 1) {
+        // the absorbed kernel's accuracy is enough until the stopping quantity
+        // reaches refine_tol; from then on the FP32 kernel refines
+        if (crit < A.refine_tol) {
+          A.lowp[p] = 0;
+          A.lowp_span[2 * p + 1] = t_now + 1;
+        }
+      } else if (A.retire && crit < A.ptol[p]) {
         A.done[p] = 1;
         A.done_at[p] = t_now + 1;
       }

@@ -25,7 +25,7 @@ COST_SQEUCLID = 1
 INPUT_DEVICE = 1
 PREC = {"fp32": 0, "fp64": 1}
 TOL_KIND = {"sum": 0, "max": 1}
-APPLY = {"auto": 0, "lse": 1}
+APPLY = {"auto": 0, "lse": 1, "bf16": 2}
 
 
 class TreeOTError(RuntimeError):
@@ -62,6 +62,10 @@ class Options(C.Structure):
         ("check_every", C.c_int32),
         ("use_graph", C.c_int32),
         ("flags", C.c_uint32),
+        ("refine_tol", C.c_double),
+        ("absorb_tau", C.c_double),
+        ("lowp_start", C.c_int32),
+        ("autotune", C.c_int32),
     ]
 
 
@@ -75,6 +79,8 @@ class Result(C.Structure):
         ("dual", C.c_double),
         ("transport_cost", C.c_double),
         ("wall_ms", C.c_double),
+        ("lowp_half_steps", C.c_int64),
+        ("absorptions", C.c_int64),
     ]
 
     def as_dict(self):
@@ -100,9 +106,25 @@ SIGNATURES = {
     "tree_ot_marginals": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "tree_ot_get_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "tree_ot_set_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_set_potentials_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                               C.POINTER(C.c_int32), C.c_void_p, C.c_int64]),
+    "tree_ot_get_potentials_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                               C.POINTER(C.c_int32), C.c_void_p, C.c_int64, C.c_uint32]),
     "tree_ot_plan_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]),
     "tree_ot_edge_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_double,
                                              C.c_void_p, C.c_void_p]),
+    "tree_ot_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "tree_ot_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "tree_ot_mlp_num_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "tree_ot_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tree_ot_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tree_ot_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "tree_ot_mlp_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                       C.POINTER(C.c_double)]),
+    "tree_ot_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                         C.POINTER(C.c_double)]),
+    "tree_ot_mlp_last_error": (C.c_char_p, []),
+    "tree_ot_mlp_set_input_log": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double]),
 }
 
 _lib = None
@@ -129,6 +151,11 @@ def _check(rc: int, allow=(OK,)):
         return rc
     msg = _lib.tree_ot_last_error().decode(errors="replace")
     raise TreeOTError(rc, msg)
+
+
+def torch_float32():
+    import torch
+    return torch.float32
 
 
 def _stream_ptr(stream) -> int:
@@ -218,7 +245,10 @@ class _Marshalled:
 
 
 def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, check_every=32, use_graph=True,
-            apply_mode="auto") -> Options:
+            apply_mode="auto", refine_tol=None, absorb_tau=None, lowp_start=None, autotune=None,
+            dense_kernel="auto") -> Options:
+    """tree_ot_options with the defaults of tree_ot_default_options; dense_kernel picks the
+    stored-cost apply ("auto": the autotuner's choice, "tma": bulk-copy staged, "ldg": plain loads)."""
     load()
     o = Options()
     _lib.tree_ot_default_options(C.byref(o))
@@ -229,6 +259,15 @@ def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, c
     o.max_half_steps = int(max_half_steps)
     o.check_every = int(check_every)
     o.use_graph = 1 if use_graph else 0
+    if refine_tol is not None:
+        o.refine_tol = float(refine_tol)
+    if absorb_tau is not None:
+        o.absorb_tau = float(absorb_tau)
+    if lowp_start is not None:
+        o.lowp_start = int(lowp_start)
+    if autotune is not None:
+        o.autotune = 1 if autotune else 0
+    o.flags = {"auto": 0, "tma": 1, "ldg": 2}[dense_kernel]
     return o
 
 
@@ -339,6 +378,36 @@ class Solver:
         v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
         _check(_lib.tree_ot_set_potentials(self.h, self._s(), prob, dedge, v.ctypes.data_as(C.POINTER(C.c_double))))
 
+    def set_potentials_batch(self, probs, dedges, values):
+        """tree_ot_set_potentials_batch: row i of the CUDA float32 matrix `values`
+        becomes the potential of directed edge dedges[i] of problem probs[i]."""
+        pr = np.ascontiguousarray(np.asarray(probs, dtype=np.int32))
+        de = np.ascontiguousarray(np.asarray(dedges, dtype=np.int32))
+        if pr.shape != de.shape or values.dim() != 2 or values.shape[0] != pr.shape[0]:
+            raise ValueError("probs, dedges and the rows of values must match")
+        if values.dtype != torch_float32() or not values.is_cuda or values.stride(1) != 1:
+            raise ValueError("values must be a CUDA float32 matrix with unit column stride")
+        _check(_lib.tree_ot_set_potentials_batch(self.h, self._s(), int(pr.shape[0]),
+                                                 pr.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 de.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 C.c_void_p(values.data_ptr()), int(values.stride(0))))
+
+    def get_potentials_batch(self, probs, dedges, out, centred: bool = False):
+        """tree_ot_get_potentials_batch into the CUDA float32 matrix `out` (row i:
+        directed edge dedges[i] of problem probs[i]); centred: mean over x removed."""
+        pr = np.ascontiguousarray(np.asarray(probs, dtype=np.int32))
+        de = np.ascontiguousarray(np.asarray(dedges, dtype=np.int32))
+        if pr.shape != de.shape or out.dim() != 2 or out.shape[0] != pr.shape[0]:
+            raise ValueError("probs, dedges and the rows of out must match")
+        if out.dtype != torch_float32() or not out.is_cuda or out.stride(1) != 1:
+            raise ValueError("out must be a CUDA float32 matrix with unit column stride")
+        _check(_lib.tree_ot_get_potentials_batch(self.h, self._s(), int(pr.shape[0]),
+                                                 pr.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 de.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 C.c_void_p(out.data_ptr()), int(out.stride(0)),
+                                                 1 if centred else 0))
+        return out
+
     def set_potentials(self, f: dict, prob: int = 0):
         p = self.problems[prob]
         for e, (a, b) in enumerate(np.asarray(p.edges)):
@@ -346,10 +415,11 @@ class Solver:
             self.set_potential(prob, 2 * e + 1, f[(int(b), int(a))])
 
     def plan_stats(self) -> dict:
-        st = (C.c_int64 * 9)()
-        _check(_lib.tree_ot_plan_stats(self.h, st, 9))
+        st = (C.c_int64 * 13)()
+        _check(_lib.tree_ot_plan_stats(self.h, st, 13))
         keys = ["directed_edges", "edges", "elements_per_half_step", "matrix_bytes_per_half_step",
-                "apply_tasks_c0", "apply_tasks_c1", "device_bytes", "node_ctas_c0", "node_ctas_c1"]
+                "apply_tasks_c0", "apply_tasks_c1", "device_bytes", "node_ctas_c0", "node_ctas_c1",
+                "recompute_output_block", "recompute_ctas_per_sm", "recompute_variant", "dense_tma"]
         return dict(zip(keys, [int(x) for x in st]))
 
 
@@ -366,3 +436,74 @@ def edge_apply_noalloc(cost, g, eps: float, m_out, ld: int = None, stream=None):
     _check(_lib.tree_ot_edge_apply_noalloc(C.c_void_p(cost.data_ptr()), ld, n_rows, n_cols,
                                            C.c_void_p(g.data_ptr()), float(eps), C.c_void_p(m_out.data_ptr()),
                                            C.c_void_p(_stream_ptr(stream))))
+
+
+def _mcheck(rc: int):
+    if rc != OK:
+        raise TreeOTError(rc, _lib.tree_ot_mlp_last_error().decode(errors="replace"))
+
+
+class MLP:
+    """tree_ot_mlp_*: the warm-start predictor (device tensors in, device tensors out)."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, max_batch: int, seed: int = 0):
+        load()
+        h = C.c_void_p()
+        _mcheck(_lib.tree_ot_mlp_create(in_dim, hidden, out_dim, max_batch, seed, C.byref(h)))
+        self.h = h
+        self.in_dim, self.hidden, self.out_dim, self.max_batch = in_dim, hidden, out_dim, max_batch
+        n = C.c_int64()
+        offs = (C.c_int64 * 6)()
+        _mcheck(_lib.tree_ot_mlp_num_params(h, C.byref(n), offs))
+        self.num_params = int(n.value)
+        self.offsets = [int(o) for o in offs]
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.tree_ot_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_input_log(self, count: int, floor_value: float = 1e-30, scale: float = 1.0):
+        _mcheck(_lib.tree_ot_mlp_set_input_log(self.h, int(count), float(floor_value), float(scale)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, np.float32)
+        _mcheck(_lib.tree_ot_mlp_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, np.float32))
+        assert p.size == self.num_params
+        _mcheck(_lib.tree_ot_mlp_set_params(self.h, p.ctypes.data_as(C.c_void_p)))
+
+    def tensors(self, flat) -> dict:
+        """Split a flat parameter vector into W1, b1, W2, b2, W3, b3 views."""
+        shapes = [(self.hidden, self.in_dim), (self.hidden,), (self.hidden, self.hidden), (self.hidden,),
+                  (self.out_dim, self.hidden), (self.out_dim,)]
+        names = ["W1", "b1", "W2", "b2", "W3", "b3"]
+        return {nm: flat[o:o + int(np.prod(sh))].reshape(sh) for nm, o, sh in zip(names, self.offsets, shapes)}
+
+    def forward(self, x, y, stream=None):
+        _mcheck(_lib.tree_ot_mlp_forward(self.h, C.c_void_p(_stream_ptr(stream)), C.c_void_p(x.data_ptr()),
+                                         int(x.shape[0]), C.c_void_p(y.data_ptr())))
+
+    def backward(self, x, target, grads=None, stream=None) -> float:
+        loss = C.c_double()
+        _mcheck(_lib.tree_ot_mlp_backward(self.h, C.c_void_p(_stream_ptr(stream)), C.c_void_p(x.data_ptr()),
+                                          C.c_void_p(target.data_ptr()), int(x.shape[0]),
+                                          C.c_void_p(grads.data_ptr()) if grads is not None else None,
+                                          C.byref(loss)))
+        return float(loss.value)
+
+    def train_step(self, x, target, lr: float, stream=None) -> float:
+        loss = C.c_double()
+        _mcheck(_lib.tree_ot_mlp_train_step(self.h, C.c_void_p(_stream_ptr(stream)), C.c_void_p(x.data_ptr()),
+                                            C.c_void_p(target.data_ptr()), int(x.shape[0]), float(lr),
+                                            C.byref(loss)))
+        return float(loss.value)

@@ -1,0 +1,94 @@
+"""Learned warm start (GPU): the MLP trained by the library's own kernels on
+leaf potentials of solved barycenter stars cuts the half-steps needed to reach
+max marginal L1 <= 1e-6 on held-out stars, and every solve still meets the
+tolerance (zero-init fallback included).  Also the batched device potential
+setter / getter against the per-edge host path."""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2406_10849_gb300 as T
+    T.load()
+    return T
+
+
+def test_batched_potentials_round_trip(T):
+    probs = gen.warmstart_stars(123, 3, side=12)
+    from paper_2406_10849_gb300 import warmstart as W
+    pr, de = W.leaf_items(probs)
+    n = 144
+    rng = np.random.default_rng(5)
+    vals = rng.normal(0.0, 0.05, size=(len(pr), n)).astype(np.float32)
+    with T.Solver(probs, T.options()) as a, T.Solver(probs, T.options()) as b:
+        a.half_steps(3)
+        b.half_steps(3)
+        a.set_potentials_batch(pr, de, torch.from_numpy(vals).cuda())
+        for i in range(len(pr)):
+            b.set_potential(int(pr[i]), int(de[i]), vals[i].astype(np.float64))
+        for i in range(len(pr)):
+            np.testing.assert_array_equal(a.potential(int(pr[i]), int(de[i])), b.potential(int(pr[i]), int(de[i])))
+        a.half_steps(2)
+        b.half_steps(2)
+        out = torch.zeros((len(pr), n + 3), dtype=torch.float32, device="cuda")
+        a.get_potentials_batch(pr, de, out, centred=False)
+        got = out[:, :n].cpu().numpy()
+        for i in range(len(pr)):
+            ref = b.potential(int(pr[i]), int(de[i]))
+            np.testing.assert_allclose(got[i], ref.astype(np.float32), rtol=0, atol=1e-6 * max(1.0, np.abs(ref).max()))
+        assert np.all(out[:, n:].cpu().numpy() == 0.0)  # entries past n_owner untouched
+        a.get_potentials_batch(pr, de, out, centred=True)
+        cen = out[:, :n].cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(cen.mean(axis=1), 0.0, atol=1e-6)
+        np.testing.assert_allclose(cen, got - got.mean(axis=1, keepdims=True), atol=2e-6)
+        bad = torch.from_numpy(vals).cuda()
+        bad[1, 7] = float("nan")
+        before = a.potential(int(pr[1]), int(de[1]))
+        with pytest.raises(T.TreeOTError):
+            a.set_potentials_batch(pr, de, bad)
+        np.testing.assert_array_equal(a.potential(int(pr[1]), int(de[1])), before)  # nothing changed
+
+
+def test_warm_start_gain_on_held_out_stars(T):
+    """Paired comparison on 64 held-out 16x16 stars (eps = 0.005) after training on
+    640 stars (5120 leaf samples, eps log-uniform in [0.0025, 0.01])."""
+    from paper_2406_10849_gb300 import warmstart as W
+    side = 16
+    X, Y = [], []
+    for b in range(0, 640, 320):
+        probs = gen.warmstart_stars(5_000_000 + b, 320, side=side)
+        res, s, _ = W.zero_solve(probs)
+        # training targets need not be certified (eps down to 0.0025 puts some
+        # FP32 accuracy floors near 1e-6); they must be close
+        assert all(r["max_marginal_l1"] <= 1e-5 for r in res)
+        X.append(torch.from_numpy(W.inputs(probs)).cuda())
+        Y.append(W.targets(s, probs).clone())
+        s.close()
+    X, Y = torch.cat(X), torch.cat(Y)
+    ws = W.WarmStart(side * side, 512, 256, seed=0)
+    hist = ws.train(X, Y, epochs=40, batch=256, lr=1e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    test = gen.warmstart_stars(9_000_000, 64, side=side, eps=0.005)
+    rz, s, _ = W.zero_solve(test)
+    s.close()
+    rw, fallbacks, _ = ws.warm_solve(test)
+    ws.close()
+    hz = np.array([r["half_steps"] for r in rz], dtype=np.float64)
+    hw = np.array([r["half_steps"] for r in rw], dtype=np.float64)
+    # every solve meets the tolerance (by the solver's FP64-grade check)
+    assert max(r["max_marginal_l1"] for r in rw) <= 1e-6
+    assert max(r["max_marginal_l1"] for r in rz) <= 1e-6
+    print(f"half-steps zero {hz.mean():.1f} warm {hw.mean():.1f} fallbacks {fallbacks} "
+          f"paired better {np.mean(hw < hz):.2f}")
+    assert fallbacks == 0
+    assert hw.mean() < 0.95 * hz.mean()
+    assert np.mean(hw < hz) >= 0.75
