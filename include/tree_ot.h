@@ -104,6 +104,13 @@ typedef struct tree_ot_problem {
  * autotune = 0 the plain-load kernel runs. */
 #define TREE_OT_OPT_DENSE_TMA    1u /* bulk-copy staged kernel (one producer warp, ring)   */
 #define TREE_OT_OPT_DENSE_LDG    2u /* plain 16-byte streaming loads                       */
+/* Recomputed (squared-Euclidean) costs are formed in FP32; the rounding of
+ * |x - y|^2 alone perturbs C/eps enough to hold some iterates ~1e-7..1e-6 (max
+ * marginal L1) away from the solution at small eps.  Problems the certification
+ * (see tree_ot_solve) finds stuck above tol continue with exactly formed squared
+ * distances (coordinates split hi + lo, ~1.8x the FP32 work per element); this
+ * bit uses the exact form from the first half-step for every such problem. */
+#define TREE_OT_OPT_EXACT_DIST   4u
 
 #define TREE_OT_TOL_SUM          0  /* the paper's stopping sum (Bipartite Iterative Scaling) */
 #define TREE_OT_TOL_MAX          1  /* the largest single term of that sum                 */
@@ -187,8 +194,9 @@ int tree_ot_reset(tree_ot_handle *h, void *cuda_stream);
  * quantity the half-step kernels accumulate (Algorithm "Bipartite Iterative
  * Scaling"'s while-condition, or its largest term); the FP64-grade check of the
  * returned potentials then certifies it: if the check exceeds tol, the problem
- * resumes with a proportionally lower retirement threshold (at most 8 times,
- * and only while each round improves the check by 10%: FP32 iterates have an
+ * resumes with a retirement threshold below the FP32 quantity it retired on,
+ * scaled by how far the check missed (8 times at most,
+ * and only while each round still lowers the check: FP32 iterates have an
  * accuracy floor, typically 1e-7 to 1e-6 in max marginal L1, that grows as eps
  * shrinks).
  * results: host array [num_probs] (may be NULL).  Returns TREE_OT_NOT_CONVERGED

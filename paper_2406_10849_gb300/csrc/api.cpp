@@ -216,15 +216,22 @@ struct tree_ot_handle {
   double *d_resid_acc = nullptr, *d_resid_dedge = nullptr, *d_res_sum = nullptr, *d_marg = nullptr;
   double *d_edge_tc = nullptr, *d_edge_mass = nullptr;
   float *d_hh = nullptr, *d_hl = nullptr, *d_ah = nullptr, *d_al = nullptr, *d_coords = nullptr;
+  float *d_coords_hi = nullptr, *d_coords_lo = nullptr;  // coordinates split hi + lo (exact distances)
+  uint32_t* d_cmax = nullptr;              // per problem max |coordinate| (split scratch)
+  int32_t* d_exact = nullptr;              // per problem: exact squared distances (recomputed costs)
+  std::vector<int32_t> h_exact;
+  int32_t any_exact = 0;
   float2* d_part32 = nullptr;
   double2* d_part64 = nullptr;
   double2* d_zpart = nullptr;
   unsigned long long* d_res_max = nullptr;
   int32_t *d_done = nullptr, *d_node_arrive = nullptr, *d_node_count = nullptr, *d_launch_count = nullptr;
-  int32_t *d_err = nullptr, *d_scan = nullptr;
+  int32_t *d_err = nullptr, *d_scan = nullptr, *d_chk_mask = nullptr;
   int64_t *d_done_at = nullptr, *d_hs = nullptr;
   double* d_ptol = nullptr;                // per-problem retirement threshold
   std::vector<double> h_ptol;
+  int64_t* d_deadline = nullptr;           // per-problem latest retirement half-step
+  std::vector<int64_t> h_deadline;
   std::vector<void*> owned;
 
   int64_t hs_host = 0;
@@ -341,6 +348,10 @@ ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   a.f = h->d_f;
   a.logg = h->d_logg;
   a.coords = h->d_coords;
+  a.coords_hi = h->d_coords_hi;
+  a.coords_lo = h->d_coords_lo;
+  a.exact = h->d_exact;
+  a.any_exact = h->any_exact;
   a.part32 = h->d_part32;
   a.part64 = h->d_part64;
   a.lowp = h->d_lowp;
@@ -386,6 +397,7 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.err = h->d_err;
   a.tol = h->opt.tol;
   a.ptol = h->d_ptol;
+  a.deadline = h->d_deadline;
   a.tol_kind = h->opt.tol_kind;
   a.retire = retire ? 1 : 0;
   a.absorbed = h->lowp ? 1 : 0;
@@ -492,9 +504,26 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(h->d_res_sum, 0, sizeof(double) * kResidRing * h->nprob, s));
   h->h_ptol.assign(h->nprob, h->opt.tol);
   CUDA_TRY(cudaMemcpyAsync(h->d_ptol, h->h_ptol.data(), sizeof(double) * h->nprob, cudaMemcpyHostToDevice, s));
+  h->h_deadline.assign(h->nprob, INT64_MAX);
+  CUDA_TRY(
+      cudaMemcpyAsync(h->d_deadline, h->h_deadline.data(), sizeof(int64_t) * h->nprob, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));  // h_ptol may be rewritten by the next solve
   CUDA_TRY(cudaMemsetAsync(h->d_res_max, 0, sizeof(unsigned long long) * kResidRing * h->nprob, s));
   CUDA_TRY(cudaMemsetAsync(h->d_done, 0, sizeof(int32_t) * h->nprob, s));
+  {
+    // exact squared distances from the start only when the option asks for them
+    const bool force = (h->opt.flags & TREE_OT_OPT_EXACT_DIST) != 0;
+    h->h_exact.assign(h->nprob, 0);
+    for (int p = 0; p < h->nprob; ++p)
+      h->h_exact[p] = force && h->probs[p].cost_kind == TREE_OT_COST_SQEUCLID ? 1 : 0;
+    const int32_t any = *std::max_element(h->h_exact.begin(), h->h_exact.end());
+    if (any != h->any_exact && h->graph) {  // the captured launches pick the kernel instantiation
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    h->any_exact = any;
+    CUDA_TRY(cudaMemcpyAsync(h->d_exact, h->h_exact.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+  }
   CUDA_TRY(cudaMemsetAsync(h->d_done_at, 0, sizeof(int64_t) * h->nprob, s));
   CUDA_TRY(cudaMemsetAsync(h->d_node_arrive, 0, sizeof(int32_t) * h->nodes.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_node_count, 0, sizeof(int32_t) * h->nprob, s));
@@ -552,8 +581,18 @@ int build_graph(tree_ot_handle* h, int len) {
   return TREE_OT_OK;
 }
 
-int run_check(tree_ot_handle* h, cudaStream_t s) {
+// FP64-grade check of the current potentials.  only (optional, per problem):
+// check just the flagged problems and keep the other problems' last results.
+int run_check(tree_ot_handle* h, cudaStream_t s, const std::vector<int32_t>* only = nullptr) {
   const int32_t nd = (int32_t)h->dedges.size();
+  const bool partial = only != nullptr && h->have_check;
+  std::vector<double> keep_marg, keep_tc, keep_mass;
+  if (partial) {
+    keep_marg = h->h_marg;
+    keep_tc = h->h_tc;
+    keep_mass = h->h_mass;
+    CUDA_TRY(cudaMemcpyAsync(h->d_chk_mask, only->data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+  }
   CUDA_TRY(launch_operand(h->d_f, h->d_Z, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, nd, 1.0, false, h->d_ah,
                           h->d_al, s));
   CUDA_TRY(cudaMemsetAsync(h->d_edge_tc, 0, sizeof(double) * h->edges.size(), s));
@@ -575,6 +614,7 @@ int run_check(tree_ot_handle* h, cudaStream_t s) {
   c.marg = h->d_marg;
   c.edge_tc = h->d_edge_tc;
   c.edge_mass = h->d_edge_mass;
+  c.mask = partial ? h->d_chk_mask : nullptr;
   CUDA_TRY(h->fp64 ? launch_check64(c, s) : launch_check(c, s));
   h->h_marg.resize(h->vec_len);
   h->h_f.resize(h->vec_len);
@@ -590,6 +630,21 @@ int run_check(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(
       cudaMemcpyAsync(h->h_mass.data(), h->d_edge_mass, sizeof(double) * h->edges.size(), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (partial) {
+    for (int p = 0; p < h->nprob; ++p) {
+      if ((*only)[p]) continue;
+      const int32_t eb = h->prob_edge_base[p], J = h->prob_nodes[p];
+      for (int32_t e = eb; e < eb + J - 1; ++e) {
+        h->h_tc[e] = keep_tc[e];
+        h->h_mass[e] = keep_mass[e];
+        for (int k = 0; k < 2; ++k) {
+          const DEdgeD& d = h->dedges[2 * e + k];
+          const int32_t n = h->nodes[d.owner].n;
+          std::copy(keep_marg.begin() + d.off, keep_marg.begin() + d.off + n, h->h_marg.begin() + d.off);
+        }
+      }
+    }
+  }
   h->have_check = true;
   return TREE_OT_OK;
 }
@@ -1085,12 +1140,16 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = h->alloc(&h->d_al, h->vec_len)) || (rc = h->alloc(&h->d_marg, h->vec_len)) ||
       (rc = h->alloc(&h->d_Z, NN)) || (rc = h->alloc(&h->d_rho, NN)) || (rc = h->alloc(&h->d_logg, h->node_len)) ||
       (rc = h->alloc(&h->d_mu, h->node_len)) || (rc = h->alloc(&h->d_coords, h->coord_len)) ||
+      (rc = h->alloc(&h->d_coords_hi, h->coord_len)) || (rc = h->alloc(&h->d_coords_lo, h->coord_len)) ||
+      (rc = h->alloc(&h->d_cmax, num_probs)) || (rc = h->alloc(&h->d_exact, num_probs)) ||
       (rc = h->alloc(&h->d_zpart, h->nzchunks)) || (rc = h->alloc(&h->d_resid_acc, ND)) ||
       (rc = h->alloc(&h->d_resid_dedge, ND)) || (rc = h->alloc(&h->d_res_sum, (int64_t)kResidRing * num_probs)) ||
       (rc = h->alloc(&h->d_res_max, (int64_t)kResidRing * num_probs)) || (rc = h->alloc(&h->d_done, num_probs)) ||
       (rc = h->alloc(&h->d_done_at, num_probs)) || (rc = h->alloc(&h->d_node_arrive, NN)) ||
       (rc = h->alloc(&h->d_node_count, num_probs)) || (rc = h->alloc(&h->d_launch_count, 1)) ||
-      (rc = h->alloc(&h->d_hs, 1)) || (rc = h->alloc(&h->d_ptol, num_probs)) || (rc = h->alloc(&h->d_err, 1)) || (rc = h->alloc(&h->d_scan, 1)) ||
+      (rc = h->alloc(&h->d_hs, 1)) || (rc = h->alloc(&h->d_ptol, num_probs)) ||
+      (rc = h->alloc(&h->d_deadline, num_probs)) ||
+      (rc = h->alloc(&h->d_chk_mask, num_probs)) || (rc = h->alloc(&h->d_err, 1)) || (rc = h->alloc(&h->d_scan, 1)) ||
       (rc = h->alloc(&h->d_edge_tc, NE)) || (rc = h->alloc(&h->d_edge_mass, NE)))
     return bail(rc);
   if (h->fp64) {
@@ -1196,6 +1255,11 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = up(h->d_chunks[1], h->chunks[1].data(), sizeof(NodeChunk) * h->chunks[1].size())) ||
       (rc = up(h->d_check_tasks, h->check_tasks.data(), sizeof(Task) * h->check_tasks.size())))
     return bail(rc);
+  if (h->coord_len > 0) {  // needs the node and problem tables on the device
+    cudaError_t e = launch_split_coords(h->d_coords, h->d_nodes, (int32_t)h->nodes.size(), h->d_probs, h->d_cmax,
+                                        num_probs, h->d_coords_hi, h->d_coords_lo, s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "coordinate split"));
+  }
   if (h->lowp && ((rc = up(h->d_btasks[0], h->btasks[0].data(), sizeof(Task) * h->btasks[0].size())) ||
                   (rc = up(h->d_btasks[1], h->btasks[1].data(), sizeof(Task) * h->btasks[1].size())) ||
                   (rc = up(h->d_atasks, h->atasks.data(), sizeof(Task) * h->atasks.size()))))
@@ -1303,11 +1367,14 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
   if (use_graph) RC_TRY(build_graph(h, G));
   // Certification: a problem retires on the FP32 stopping quantity of the
   // half-step kernels; the FP64-grade check of its returned iterate decides.
-  // If the check exceeds tol, the problem resumes with its threshold lowered in
-  // proportion, up to kCertifyRounds times, and only while each round gains at
-  // least 10% (else the FP32 iterate has reached its accuracy floor).
+  // If the check exceeds tol, the problem resumes with a threshold below the
+  // FP32 quantity it retired on, scaled by how far the check missed, up to
+  // kCertifyRounds times and only while each round still lowers the check
+  // (else the FP32 iterate has reached its accuracy floor; a recomputed-cost
+  // problem then gets one more chance with exact squared distances).
   constexpr int kCertifyRounds = 8;
   std::vector<double> prev_got(h->nprob, INFINITY);
+  std::vector<int32_t> resumed(h->nprob, 0);  // problems resumed by the last round
   for (int cert = 0;; ++cert) {
     while (h->hs_host < h->opt.max_half_steps) {
       const int64_t left = h->opt.max_half_steps - h->hs_host;
@@ -1335,20 +1402,49 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
     CUDA_TRY(cudaMemcpyAsync(&h->h_absorb_count, h->d_absorb_count, sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    RC_TRY(run_check(h, s));
+    RC_TRY(run_check(h, s, cert == 0 ? nullptr : &resumed));
     if (cert >= kCertifyRounds || h->hs_host >= h->opt.max_half_steps) break;
     std::vector<tree_ot_result> chk(h->nprob);
     fill_results(h, chk.data());
+    // the FP32 stopping quantity each problem retired on (ring slot of its last half-step)
+    std::vector<double> ring_sum((size_t)kResidRing * h->nprob);
+    std::vector<unsigned long long> ring_max((size_t)kResidRing * h->nprob);
+    CUDA_TRY(cudaMemcpyAsync(ring_sum.data(), h->d_res_sum, sizeof(double) * ring_sum.size(), cudaMemcpyDeviceToHost,
+                             s));
+    CUDA_TRY(cudaMemcpyAsync(ring_max.data(), h->d_res_max, sizeof(unsigned long long) * ring_max.size(),
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    auto retired_on = [&](int p) {
+      const size_t slot = (size_t)((h->h_done_at[p] - 1) % kResidRing);
+      if (h->opt.tol_kind == TREE_OT_TOL_MAX) {
+        double v;
+        std::memcpy(&v, &ring_max[slot * h->nprob + p], sizeof(double));
+        return v;
+      }
+      return ring_sum[slot * h->nprob + p];
+    };
     bool resume = false;
+    std::fill(resumed.begin(), resumed.end(), 0);
     for (int p = 0; p < h->nprob; ++p) {
       if (!h->h_done[p]) continue;
       const double got = h->opt.tol_kind == TREE_OT_TOL_MAX ? chk[p].max_marginal_l1 : chk[p].residual_sum_l1;
       if (!(got > h->opt.tol)) continue;
-      // no gain since the last round: the FP32 iterate's accuracy floor is above tol
-      if (!(got < 0.9 * prev_got[p])) continue;
+      // no gain since the last round: the FP32 iterate's accuracy floor is above tol;
+      // a recomputed-cost problem then continues with exact squared distances
+      const bool to_exact = !(got < 0.99 * prev_got[p]) && h->probs[p].cost_kind == TREE_OT_COST_SQEUCLID &&
+                            !h->h_exact[p];
+      if (!(got < 0.99 * prev_got[p]) && !to_exact) continue;
+      if (to_exact) h->h_exact[p] = 1;
       prev_got[p] = got;
-      h->h_ptol[p] *= std::min(0.9, std::max(0.1, 0.9 * h->opt.tol / got));
+      // next threshold: the FP32 quantity it retired on, scaled by how far the check missed
+      const double crit = retired_on(p);
+      const double scale = std::min(0.9, std::max(0.05, 0.8 * h->opt.tol / got));
+      h->h_ptol[p] = std::min(h->h_ptol[p], (crit > 0.0 && std::isfinite(crit) ? crit : h->h_ptol[p]) * scale);
       h->h_done[p] = 0;
+      // a resumed problem retires within a quarter of its first run (at least 64 half-steps),
+      // whether or not its FP32 quantity gets below the new threshold
+      h->h_deadline[p] = h->hs_host + std::max<int64_t>(64, h->h_done_at[p] / 4);
+      resumed[p] = 1;
       resume = true;
       // the problem's residual ring restarts from zero
       static const double zeros[kResidRing] = {};
@@ -1358,8 +1454,43 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
                                  sizeof(double), kResidRing, cudaMemcpyHostToDevice, s));
     }
     if (!resume) break;
+    {
+      const int32_t any = *std::max_element(h->h_exact.begin(), h->h_exact.end());
+      CUDA_TRY(cudaMemcpyAsync(h->d_exact, h->h_exact.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+      if (any != h->any_exact) {
+        h->any_exact = any;
+        if (use_graph) {
+          if (h->graph) cudaGraphExecDestroy(h->graph);
+          h->graph = nullptr;
+          RC_TRY(build_graph(h, G));
+        }
+      }
+    }
+    // A resumed problem must next update the colour it did not update last; half-steps
+    // alternate colours for every problem at once, so those whose last colour comes
+    // next sit out one half-step (then one more half-step restores the even count the
+    // captured graph starts from).
+    std::vector<int32_t> later(h->nprob, 0);
+    bool any_later = false;
+    for (int p = 0; p < h->nprob; ++p)
+      if (resumed[p] && (h->h_done_at[p] - 1) % 2 == h->hs_host % 2) {
+        later[p] = 1;
+        h->h_done[p] = 1;
+        any_later = true;
+      }
     CUDA_TRY(cudaMemcpyAsync(h->d_ptol, h->h_ptol.data(), sizeof(double) * h->nprob, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h->d_deadline, h->h_deadline.data(), sizeof(int64_t) * h->nprob, cudaMemcpyHostToDevice,
+                             s));
     CUDA_TRY(cudaMemcpyAsync(h->d_done, h->h_done.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+    if (any_later) {
+      RC_TRY(queue_half_steps(h, 1, true, s));
+      CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (int p = 0; p < h->nprob; ++p)
+        if (later[p]) h->h_done[p] = 0;
+      CUDA_TRY(cudaMemcpyAsync(h->d_done, h->h_done.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+      RC_TRY(queue_half_steps(h, 1, true, s));
+    }
     CUDA_TRY(cudaStreamSynchronize(s));
   }
   // converged = retired and certified by the check

@@ -85,9 +85,13 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const float4* sh4 = reinterpret_cast<const float4*>(sh);
   const float4* sl4 = reinterpret_cast<const float4*>(sl);
   const float2 nhi = make_float2(-P.s2, -P.s2), nlo = make_float2(-P.s2_lo, -P.s2_lo);
+  const uint32_t row_bytes = 16u * (uint32_t)nvec;  // within the row: the stride is padded to 4 floats
   for (int r = warp; r < t.ocount; r += kApplyThreads / 32) {
     const int x = t.o0 + r;
     const float4* row = reinterpret_cast<const float4*>(e.C + (int64_t)x * e.ld + t.r0);
+    // the warp's next row heads for L2 while this one is in flight: twice the bytes in flight per warp
+    if (lane == 0 && r + kApplyThreads / 32 < t.ocount)
+      prefetch_l2(e.C + (int64_t)(x + kApplyThreads / 32) * e.ld + t.r0, row_bytes);
     float4 c[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -175,7 +179,11 @@ __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
   }
   const float2 nhi = make_float2(-P.s2, -P.s2), nlo = make_float2(-P.s2_lo, -P.s2_lo);
   const float* base = e.C + t.o0 + c0;
+  const uint32_t chunk_bytes = 16u * (uint32_t)((t.ocount + 3) >> 2);  // the task's columns of one row
   for (int rr = rr0; rr < rr1; rr += 8) {
+    // the warp's next 8 rows head for L2 while these are in flight
+    if (lane < 8 && rr + 8 + lane < rr1)
+      prefetch_l2(e.C + (int64_t)(t.r0 + rr + 8 + lane) * e.ld + t.o0, chunk_bytes);
     float4 c[8];
     float hh[8], hl[8];
 #pragma unroll
@@ -433,12 +441,180 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_dense_kernel(ApplyArgs
   }
 }
 
+// Exact-distance variant for problems refined past the FP32 floor of the plain
+// recomputation.  Rounding |p - q|^2 in FP32 perturbs the cost by a relative
+// 2^-23, i.e. C/eps by up to ~1e-4 for C/eps in the hundreds, which settles
+// the iterate ~1e-7..1e-6 (max marginal L1) away from the true fixed point.
+// Here every coordinate arrives split as hi + lo, hi on a grid of
+// unit = 2^-10 sigma (sigma a power of two >= max |coordinate| of the problem).
+// Then p_hi - q_hi is exact (at most 12 significant bits), its square is exact
+// (at most 22 bits) and so is the sum over D <= 3 dimensions (< 2^24 units^2):
+//   c_hi = sum_d (p_hi - q_hi)^2                      (exact)
+//   c_lo = sum_d dl (2 (p_hi - q_hi) + dl),  dl = p_lo - q_lo   (small)
+//   t    = (hh - R) - c_hi s_hi - c_hi s_lo - c_lo s_hi + hl,
+// so the argument keeps the exactness of the stored-cost kernels.
+template <int D>
+__device__ void recomp_task_exact(const ApplyArgs& A, const Task& t, float* sm) {
+  const DEdgeD d = A.dedges[t.dedge];
+  const NodeD own = A.nodes[d.owner];
+  const NodeD nbn = A.nodes[d.nbr];
+  const ProbD P = A.probs[d.prob];
+  const float2 nhi = make_float2(-P.s2_scaled, -P.s2_scaled), nlo = make_float2(-P.s2_scaled_lo, -P.s2_scaled_lo);
+  const float2 two = make_float2(2.f, 2.f);
+  const int n_owner = own.n;
+  const int tid = threadIdx.x;
+  const int G = t.pad;
+  const int gs = kApplyThreads / G;
+  const int g = tid / gs, tg = tid - g * gs;
+  float4* sxh = reinterpret_cast<float4*>(sm);                        // (-qx_hi, -qx_hi, -qy_hi, -qy_hi)
+  float4* sxl = sxh + kApplyThreads;                                  // (-qx_lo, -qx_lo, -qy_lo, -qy_lo)
+  float4* sz = sxh + 2 * kApplyThreads;                               // (-qz_hi, -qz_hi, -qz_lo, -qz_lo)
+  float4* shl = sxh + 3 * kApplyThreads;                              // (hh, hh, hl, hl)
+  float2* comb = reinterpret_cast<float2*>(sm + 16 * kApplyThreads);  // [G][4 gs]
+  float ph[4][3], pl[4][3];
+  float R[4], acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int lo = tg + gs * i;
+    const bool on = lo < t.ocount;
+    const int o = t.o0 + (on ? lo : 0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ph[i][k] = k < D ? A.coords_hi[own.coord_off + (int64_t)o * D + k] : 0.f;
+      pl[i][k] = k < D ? A.coords_lo[own.coord_off + (int64_t)o * D + k] : 0.f;
+    }
+    R[i] = on ? A.fr[d.off + o] : 0.f;
+    acc[i] = 0.f;
+  }
+  const float2 pxh01 = make_float2(ph[0][0], ph[1][0]), pxh23 = make_float2(ph[2][0], ph[3][0]);
+  const float2 pxl01 = make_float2(pl[0][0], pl[1][0]), pxl23 = make_float2(pl[2][0], pl[3][0]);
+  const float2 pyh01 = make_float2(ph[0][1], ph[1][1]), pyh23 = make_float2(ph[2][1], ph[3][1]);
+  const float2 pyl01 = make_float2(pl[0][1], pl[1][1]), pyl23 = make_float2(pl[2][1], pl[3][1]);
+  const float2 pzh01 = make_float2(ph[0][2], ph[1][2]), pzh23 = make_float2(ph[2][2], ph[3][2]);
+  const float2 pzl01 = make_float2(pl[0][2], pl[1][2]), pzl23 = make_float2(pl[2][2], pl[3][2]);
+  const int per = kApplyThreads / G;
+  for (int ch = 0; ch < t.rcount; ch += kApplyThreads) {
+    __syncthreads();
+    {
+      const int j = ch + tid;
+      const bool v = j < t.rcount;
+      const int y = t.r0 + (v ? j : 0);
+      const float* qh = A.coords_hi + nbn.coord_off + (int64_t)y * D;
+      const float* ql = A.coords_lo + nbn.coord_off + (int64_t)y * D;
+      const float hh = v ? A.hh[d.rev_off + y] : -kInf;
+      const float hl = v ? A.hl[d.rev_off + y] : 0.f;
+      const float yh = D > 1 ? -qh[1] : 0.f, yl = D > 1 ? -ql[1] : 0.f;
+      sxh[tid] = make_float4(-qh[0], -qh[0], yh, yh);
+      sxl[tid] = make_float4(-ql[0], -ql[0], yl, yl);
+      if (D == 3) sz[tid] = make_float4(-qh[2], -qh[2], -ql[2], -ql[2]);
+      shl[tid] = make_float4(hh, hh, hl, hl);
+    }
+    __syncthreads();
+    const int cnt = min(kApplyThreads, t.rcount - ch);
+    const int jend = min(g * per + per, cnt);
+    for (int j = g * per; j < jend; j += kRecPts) {
+      float tv[4][kRecPts];
+      // all terms of the chunk relative to the current frames
+      auto terms = [&]() {
+        const float2 nR01 = make_float2(-R[0], -R[1]);
+        const float2 nR23 = make_float2(-R[2], -R[3]);
+#pragma unroll
+        for (int jj = 0; jj < kRecPts; ++jj) {
+          const float4 qh = sxh[j + jj], ql = sxl[j + jj], hv = shl[j + jj];
+          float2 ch01, ch23, cl01, cl23;
+          {
+            const float2 dh01 = add2(pxh01, make_float2(qh.x, qh.y)), dh23 = add2(pxh23, make_float2(qh.x, qh.y));
+            const float2 dl01 = add2(pxl01, make_float2(ql.x, ql.y)), dl23 = add2(pxl23, make_float2(ql.x, ql.y));
+            ch01 = mul2(dh01, dh01);
+            ch23 = mul2(dh23, dh23);
+            cl01 = mul2(dl01, fma2(two, dh01, dl01));
+            cl23 = mul2(dl23, fma2(two, dh23, dl23));
+          }
+          if (D > 1) {
+            const float2 dh01 = add2(pyh01, make_float2(qh.z, qh.w)), dh23 = add2(pyh23, make_float2(qh.z, qh.w));
+            const float2 dl01 = add2(pyl01, make_float2(ql.z, ql.w)), dl23 = add2(pyl23, make_float2(ql.z, ql.w));
+            ch01 = fma2(dh01, dh01, ch01);
+            ch23 = fma2(dh23, dh23, ch23);
+            cl01 = fma2(dl01, fma2(two, dh01, dl01), cl01);
+            cl23 = fma2(dl23, fma2(two, dh23, dl23), cl23);
+          }
+          if (D > 2) {
+            const float4 zz = sz[j + jj];
+            const float2 dh01 = add2(pzh01, make_float2(zz.x, zz.y)), dh23 = add2(pzh23, make_float2(zz.x, zz.y));
+            const float2 dl01 = add2(pzl01, make_float2(zz.z, zz.w)), dl23 = add2(pzl23, make_float2(zz.z, zz.w));
+            ch01 = fma2(dh01, dh01, ch01);
+            ch23 = fma2(dh23, dh23, ch23);
+            cl01 = fma2(dl01, fma2(two, dh01, dl01), cl01);
+            cl23 = fma2(dl23, fma2(two, dh23, dl23), cl23);
+          }
+          const float2 h2 = make_float2(hv.x, hv.y), l2 = make_float2(hv.z, hv.w);
+          float2 t01 = fma2(ch01, nhi, add2(h2, nR01));
+          float2 t23 = fma2(ch23, nhi, add2(h2, nR23));
+          t01 = fma2(cl01, nhi, fma2(ch01, nlo, t01));
+          t23 = fma2(cl23, nhi, fma2(ch23, nlo, t23));
+          t01 = add2(t01, l2);
+          t23 = add2(t23, l2);
+          tv[0][jj] = t01.x;
+          tv[1][jj] = t01.y;
+          tv[2][jj] = t23.x;
+          tv[3][jj] = t23.y;
+        }
+      };
+      terms();
+      float cmk[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        cmk[k] = fmaxf(tv[k][0], tv[k][1]);
+#pragma unroll
+        for (int jj = 2; jj < kRecPts; jj += 2) cmk[k] = max3f(cmk[k], tv[k][jj], tv[k][jj + 1]);
+      }
+      const bool fresh = (acc[0] == 0.f) | (acc[1] == 0.f) | (acc[2] == 0.f) | (acc[3] == 0.f);
+      if (fresh || fmaxf(max3f(cmk[0], cmk[1], cmk[2]), cmk[3]) > 0.5f) {
+        bool moved = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float cm = cmk[k];
+          if ((cm > 0.5f || (acc[k] == 0.f && cm < -kWindow)) && cm > -kInf) {
+            const float Rn = R[k] + quant(cm);
+            acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
+            R[k] = Rn;
+            moved = true;
+          }
+        }
+        if (moved) terms();  // rare: the chunk again from the moved frames
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k += 2) {
+        float2 s01 = make_float2(ex2(tv[k][0]), ex2(tv[k + 1][0]));
+#pragma unroll
+        for (int jj = 1; jj < kRecPts; ++jj) s01 = add2(s01, make_float2(ex2(tv[k][jj]), ex2(tv[k + 1][jj])));
+        acc[k] += s01.x;
+        acc[k + 1] += s01.y;
+      }
+    }
+  }
+  if (G == 1) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (tg + gs * i < t.ocount)
+        A.part32[d.part_off + (int64_t)t.split * n_owner + t.o0 + tg + gs * i] = make_float2(R[i], acc[i]);
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) comb[g * (4 * gs) + tg + gs * i] = make_float2(R[i], acc[i]);
+  __syncthreads();
+  for (int c = tid; c < t.ocount; c += kApplyThreads)
+    A.part32[d.part_off + (int64_t)t.split * n_owner + t.o0 + c] = merge_pieces(comb + c, G, 4 * gs);
+}
+
 // Tasks come from a work queue (an atomic counter; tasks are sorted by cost on
 // the host), so uneven edges of a batch of trees balance across the CTAs.  The
 // last CTA to leave resets the counter for the next launch.
-template <int D, int MINB>
+// EXACT: some problems run the exact-distance variant (A.exact); instantiated
+// separately so the plain kernel keeps its register budget.
+template <int D, int MINB, bool EXACT>
 __global__ void __launch_bounds__(kApplyThreads, MINB) apply_recomp_kernel(ApplyArgs A) {
-  __shared__ __align__(16) float sm[12 * kApplyThreads + 2 * 4 * kApplyThreads];  // 20 KB
+  __shared__ __align__(16) float sm[16 * kApplyThreads + 2 * 4 * kApplyThreads];  // 24 KB
   __shared__ int s_ti;
   for (;;) {
     if (threadIdx.x == 0) s_ti = atomicAdd(&A.queue[0], 1);
@@ -447,8 +623,12 @@ __global__ void __launch_bounds__(kApplyThreads, MINB) apply_recomp_kernel(Apply
     __syncthreads();
     if (ti >= A.ntasks) break;
     const Task t = A.tasks[ti];
-    if (A.done[A.dedges[t.dedge].prob]) continue;
-    recomp_task<D>(A, t, sm);
+    const int prob = A.dedges[t.dedge].prob;
+    if (A.done[prob]) continue;
+    if (EXACT && A.exact[prob])  // block-uniform: refined past the plain recomputation's floor
+      recomp_task_exact<D>(A, t, sm);
+    else
+      recomp_task<D>(A, t, sm);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -588,7 +768,7 @@ __global__ void noalloc_merge_kernel(const float2* part, int32_t n_rows, int32_t
 template <int D, int MINB>
 int occ_recomp() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<D, MINB>, kApplyThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_recomp_kernel<D, MINB, false>, kApplyThreads, 0);
   return n > 0 ? n : 1;
 }
 
@@ -606,14 +786,19 @@ cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int variant, int grid
   if (a.ntasks <= 0) return cudaSuccess;
   if (slot == 0) {
     apply_dense_kernel<<<grid, kApplyThreads, 0, s>>>(a);
+  } else if (a.any_exact) {
+    // rare (after certification): the 2-CTA register budget, whatever the tuned variant
+    if (slot == 1) apply_recomp_kernel<1, 2, true><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 2) apply_recomp_kernel<2, 2, true><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 3) apply_recomp_kernel<3, 2, true><<<grid, kApplyThreads, 0, s>>>(a);
   } else if (variant == 0) {
-    if (slot == 1) apply_recomp_kernel<1, 2><<<grid, kApplyThreads, 0, s>>>(a);
-    if (slot == 2) apply_recomp_kernel<2, 2><<<grid, kApplyThreads, 0, s>>>(a);
-    if (slot == 3) apply_recomp_kernel<3, 2><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 1) apply_recomp_kernel<1, 2, false><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 2) apply_recomp_kernel<2, 2, false><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 3) apply_recomp_kernel<3, 2, false><<<grid, kApplyThreads, 0, s>>>(a);
   } else {
-    if (slot == 1) apply_recomp_kernel<1, 3><<<grid, kApplyThreads, 0, s>>>(a);
-    if (slot == 2) apply_recomp_kernel<2, 3><<<grid, kApplyThreads, 0, s>>>(a);
-    if (slot == 3) apply_recomp_kernel<3, 3><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 1) apply_recomp_kernel<1, 3, false><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 2) apply_recomp_kernel<2, 3, false><<<grid, kApplyThreads, 0, s>>>(a);
+    if (slot == 3) apply_recomp_kernel<3, 3, false><<<grid, kApplyThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }

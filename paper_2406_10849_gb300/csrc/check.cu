@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) check_kernel(CheckArgs A) {
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
     const DEdgeD d = A.dedges[t.dedge];
+    if (A.mask && !A.mask[d.prob]) continue;  // block-uniform
     const EdgeD e = A.edges[d.edge];
     const ProbD P = A.probs[d.prob];
     const double kd = (P.cost_kind == 0 ? 1.0 : P.cost_scale) * P.inv_eps;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(256) check64_kernel(CheckArgs A) {
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
     const DEdgeD d = A.dedges[t.dedge];
+    if (A.mask && !A.mask[d.prob]) continue;  // block-uniform
     const EdgeD e = A.edges[d.edge];
     const ProbD P = A.probs[d.prob];
     const NodeD na = A.nodes[e.a], nb = A.nodes[e.b];
@@ -287,6 +289,40 @@ __global__ void get_potentials_kernel(const int32_t* dlist, int32_t i0, const DE
   for (int x = threadIdx.x; x < n; x += blockDim.x) values[(int64_t)i * ld + x] = (float)(f[d.off + x] - ez - mean);
 }
 
+// per problem: max |coordinate| (as the bits of a non-negative float)
+__global__ void coord_absmax_kernel(const float* coords, const NodeD* nodes, int32_t nnodes, const ProbD* probs,
+                                    uint32_t* cmax) {
+  for (int j = blockIdx.x; j < nnodes; j += gridDim.x) {
+    const NodeD nd = nodes[j];
+    if (nd.coord_off < 0) continue;
+    const int64_t cnt = (int64_t)nd.n * probs[nd.prob].dim;
+    float m = 0.f;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) m = fmaxf(m, fabsf(coords[nd.coord_off + i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(&cmax[nd.prob], __float_as_uint(m));
+  }
+}
+
+// coordinates split c = hi + lo, hi on the grid of unit = 2^-10 sigma, sigma the
+// power of two >= the problem's max |coordinate| (the scalings are exact)
+__global__ void split_coords_kernel(const float* coords, const NodeD* nodes, int32_t nnodes, const ProbD* probs,
+                                    const uint32_t* cmax, float* hi, float* lo) {
+  for (int j = blockIdx.x; j < nnodes; j += gridDim.x) {
+    const NodeD nd = nodes[j];
+    if (nd.coord_off < 0) continue;
+    const float m = __uint_as_float(cmax[nd.prob]);
+    int e = 0;
+    if (m > 0.f) (void)frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): sigma = 2^e >= m
+    const int64_t cnt = (int64_t)nd.n * probs[nd.prob].dim;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const float c = coords[nd.coord_off + i];
+      const float h = ldexpf(rintf(ldexpf(c, 10 - e)), e - 10);
+      hi[nd.coord_off + i] = h;
+      lo[nd.coord_off + i] = c - h;  // exact: c and h share the grid above unit / 2
+    }
+  }
+}
+
 // counts NaN and -inf entries of a padded dense cost (+inf is allowed)
 __global__ void scan_cost_kernel(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad) {
   int local = 0;
@@ -358,6 +394,17 @@ cudaError_t launch_get_potentials(const int32_t* dlist, int32_t count, const DEd
     const int32_t cnt = count - i0 < 65535 ? count - i0 : 65535;
     get_potentials_kernel<<<cnt, 256, 0, s>>>(dlist, i0, dedges, nodes, probs, Z, f, values, ld, centred ? 1 : 0);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_coords(const float* coords, const NodeD* nodes, int32_t nnodes, const ProbD* probs,
+                                uint32_t* cmax, int32_t nprob, float* hi, float* lo, cudaStream_t s) {
+  if (nnodes <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(uint32_t) * nprob, s);
+  if (e != cudaSuccess) return e;
+  const int grid = nnodes < 4096 ? nnodes : 4096;
+  coord_absmax_kernel<<<grid, 256, 0, s>>>(coords, nodes, nnodes, probs, cmax);
+  split_coords_kernel<<<grid, 256, 0, s>>>(coords, nodes, nnodes, probs, cmax, hi, lo);
   return cudaGetLastError();
 }
 

@@ -118,6 +118,10 @@ struct ApplyArgs {
   const double* f;           // potentials (FP64 path)
   const double* logg;        // node log gamma (FP64 path)
   const float* coords;
+  const float* coords_hi;    // coordinates split hi + lo (hi on the problem's 2^-10 sigma grid)
+  const float* coords_lo;
+  const int32_t* exact;      // per problem: 1 = recompute costs with exact squared distances
+  int32_t any_exact;         // host: some problem has exact set (selects the kernel instantiation)
   float2* part32;            // FP32 path partials: (frame R, sum) in base 2
   double2* part64;           // FP64 path partials: (max M, sum S) in base e
   int32_t* queue;            // work-queue counters of this launch (next task, CTAs finished)
@@ -186,6 +190,7 @@ struct NodeArgs {
   int32_t* err;              // device error flags (bit 0: non-finite potential)
   double tol;
   const double* ptol;        // per problem: the retirement threshold (tol, tightened by certification)
+  const int64_t* deadline;   // per problem: retire at this half-step at the latest (resumed problems)
   int32_t tol_kind;
   int32_t retire;            // 1: retire problems whose stopping quantity < tol
   // low-precision phase control (absorbed != 0 only for handles built for it)
@@ -221,6 +226,7 @@ struct CheckArgs {
   double* marg;        // per directed edge: B 1 on the owner's side (layout of f)
   double* edge_tc;     // per edge sum C B
   double* edge_mass;   // per edge sum B
+  const int32_t* mask; // per problem: 0 = skip its tasks (null: check every problem)
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
@@ -245,6 +251,9 @@ cudaError_t launch_operand(const double* f, const double* Z, const double* logg,
                            float* vh, float* vl, cudaStream_t s);
 cudaError_t launch_check64(const CheckArgs& a, cudaStream_t s);
 cudaError_t launch_scan_cost(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad, cudaStream_t s);
+// coordinates split hi + lo for the exact-distance recomputation (cmax: nprob scratch words)
+cudaError_t launch_split_coords(const float* coords, const NodeD* nodes, int32_t nnodes, const ProbD* probs,
+                                uint32_t* cmax, int32_t nprob, float* hi, float* lo, cudaStream_t s);
 cudaError_t launch_check(const CheckArgs& a, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
 cudaError_t launch_pad_copy(const float* src, int64_t src_ld, float* dst, int64_t dst_ld, int32_t rows,

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
           A.lowp[p] = 0;
           A.lowp_span[2 * p + 1] = t_now + 1;
         }
-      } else if (A.retire && crit < A.ptol[p]) {
+      } else if (A.retire && (crit < A.ptol[p] || t_now + 1 >= A.deadline[p])) {
         A.done[p] = 1;
         A.done_at[p] = t_now + 1;
       }

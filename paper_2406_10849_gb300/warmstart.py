@@ -53,12 +53,15 @@ def leaf_items(problems: Sequence):
 
 def inputs(problems: Sequence) -> np.ndarray:
     """Rows [mu_l (n), log(eps) + EPS_SHIFT], one per fixed leaf, FP32."""
-    rows = []
+    mus, eps = [], []
     for p in problems:
         for d in leaf_edges(p):
-            mu = np.asarray(p.marginals[leaf_of(p, d)], np.float32)
-            rows.append(np.concatenate([mu, [math.log(p.eps) + EPS_SHIFT]]).astype(np.float32))
-    return np.stack(rows)
+            mus.append(p.marginals[leaf_of(p, d)])
+            eps.append(math.log(p.eps) + EPS_SHIFT)
+    out = np.empty((len(mus), len(mus[0]) + 1), np.float32)
+    out[:, :-1] = np.asarray(mus, np.float32)
+    out[:, -1] = eps
+    return out
 
 
 def targets(solver: Solver, problems: Sequence, device="cuda"):
@@ -119,16 +122,20 @@ class WarmStart:
     def predict(self, X: np.ndarray, device="cuda") -> np.ndarray:
         return self.predict_device(X, device).cpu().numpy()
 
-    def warm_solve(self, problems: Sequence, tol: float = 1e-6, max_half_steps: int = 20000, **kw):
+    def warm_solve(self, problems: Sequence, tol: float = 1e-6, max_half_steps: int = 20000, timing=None, **kw):
         """Solve every problem from predicted leaf potentials (set on the device, no
         host round trip); problems that do not converge restart from u = 1.
-        Returns (results, fallbacks, seconds)."""
+        Returns (results, fallbacks, seconds); `timing` (a dict) receives the split:
+        create, predict (inputs + network + set), solve, fallback."""
         t0 = time.perf_counter()
-        pred = self.predict_device(inputs(problems))
         s = Solver(problems, options(tol=tol, tol_kind="max", max_half_steps=max_half_steps, **kw))
+        t1 = time.perf_counter()
+        pred = self.predict_device(inputs(problems))
         pr, de = leaf_items(problems)
         s.set_potentials_batch(pr, de, pred)
+        t2 = time.perf_counter()
         rc, res = s.solve()
+        t3 = time.perf_counter()
         s.close()
         # fall back when the warm start failed (cap reached far from tol, or not finite); a
         # problem whose FP32 accuracy floor sits just above tol would not gain from u = 1
@@ -142,12 +149,19 @@ class WarmStart:
             for i, x in zip(bad, res0):
                 x["half_steps"] += res[i]["half_steps"]
                 res[i] = x
-        return res, len(bad), time.perf_counter() - t0
+        t4 = time.perf_counter()
+        if timing is not None:
+            timing.update(create=t1 - t0, predict=t2 - t1, solve=t3 - t2, fallback=t4 - t3)
+        return res, len(bad), t4 - t0
 
 
-def zero_solve(problems: Sequence, tol: float = 1e-6, max_half_steps: int = 20000, **kw):
-    """Plain start u = 1; returns (results, solver, seconds) with the solver still open."""
+def zero_solve(problems: Sequence, tol: float = 1e-6, max_half_steps: int = 20000, timing=None, **kw):
+    """Plain start u = 1; returns (results, solver, seconds) with the solver still open;
+    `timing` (a dict) receives create and solve seconds."""
     t0 = time.perf_counter()
     s = Solver(problems, options(tol=tol, tol_kind="max", max_half_steps=max_half_steps, **kw))
+    t1 = time.perf_counter()
     rc, res = s.solve()
+    if timing is not None:
+        timing.update(create=t1 - t0, solve=time.perf_counter() - t1)
     return res, s, time.perf_counter() - t0

@@ -82,6 +82,31 @@ def test_iterate_parity_fp32(T, name, steps):
     assert marginal_gap(p, got, ref) <= 1e-6
 
 
+@pytest.mark.parametrize("name", ["star5_grid20_sqeuclid", "tree9_unequal_3d", "chain_1d_sqeuclid_n300"])
+@pytest.mark.parametrize("steps", [1, 9])
+def test_iterate_parity_exact_distances(T, name, steps):
+    """Recomputed costs with exactly formed squared distances (split coordinates)."""
+    p = ITERATE_CASES[name]()
+    ref = O.run_half_steps(p, steps)
+    with T.Solver([p], T.options(precision="fp32", exact_dist=True)) as s:
+        s.half_steps(steps)
+        got = s.potentials(0)
+    assert rel_err(got, ref, p.eps) <= 1e-4
+    assert marginal_gap(p, got, ref) <= 1e-6
+
+
+def test_exact_distances_lower_the_floor(T):
+    """16x16 stars at eps = 0.005: with exact squared distances every star is
+    certified at 2e-7 (max marginal L1) by the FP64-grade check."""
+    probs = gen.warmstart_stars(9_100_000, 16, side=16, eps=0.005)
+    with T.Solver(probs, T.options(tol=2e-7, tol_kind="max", max_half_steps=20000, exact_dist=True)) as s:
+        rc, res = s.solve()
+        fs = [s.potentials(i) for i in (0, 7)]
+    assert rc == 0, [r["max_marginal_l1"] for r in res]
+    for i, f in zip((0, 7), fs):
+        assert O.final_check(probs[i], f)["max_marginal_l1"] <= 2.5e-7
+
+
 @pytest.mark.parametrize("steps", [1, 2, 9])
 def test_iterate_parity_fp64(T, steps):
     p = gen.chain_problem(seed=1003, n=64, eps=0.01)
