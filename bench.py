@@ -418,6 +418,17 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_unit_rates():
+    """Build and run the unit-rate microbenchmark (csrc/unit_rates.cu): FP32 FMA
+    lanes, packed f32x2 lanes and MUFU ex2 per clock and SM, ex2.approx error."""
+    src = os.path.join(ROOT, "paper_2406_10849_gb300", "csrc", "unit_rates.cu")
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "unit_rates")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    print(out.strip(), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,10 +447,14 @@ def main():
     ap.add_argument("--test-trees", type=int, default=2000, help="warmstart: held-out stars")
     ap.add_argument("--side", type=int, default=32, help="warmstart: grid side (n = side^2)")
     ap.add_argument("--epochs", type=int, default=30, help="warmstart: training epochs")
+    ap.add_argument("--unit-rates", action="store_true",
+                    help="only build and run the FP32 / MUFU unit-rate microbenchmark")
     ap.add_argument("--trees", type=int, default=512, help="batched workload: number of trees")
     ap.add_argument("--dense-kernel", default="auto", choices=["auto", "tma", "ldg"],
                     help="stored-cost apply kernel (auto: the solver's autotuner picks)")
     args = ap.parse_args()
+    if args.unit_rates:
+        return run_unit_rates()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -440,7 +440,8 @@ int launch_absorb_step(tree_ot_handle* h, cudaStream_t s) {
   return TREE_OT_OK;
 }
 
-int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
+// only_stored: just the stored-cost (slot 0) kernel, for timing it
+int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored = false) {
   ApplyArgs a = apply_args(h, colour);
   if (h->fp64) {
     const int grid = std::max(1, std::min<int>(a.ntasks, h->apply_grid[0]));
@@ -448,7 +449,7 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
     return TREE_OT_OK;
   }
-  for (int slot = 0; slot < kApplySlots; ++slot) {
+  for (int slot = 0; slot < (only_stored ? 1 : kApplySlots); ++slot) {
     const int32_t cnt = h->slot_count[colour][slot];
     if (cnt == 0) continue;
     a.tasks = h->d_tasks[colour] + h->slot_begin[colour][slot];
@@ -466,7 +467,7 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s) {
     cudaError_t e = launch_apply_f32(a, slot, slot == 0 ? 0 : h->rec_variant, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
   }
-  if (h->lowp && !h->btasks[colour].empty()) {
+  if (h->lowp && !only_stored && !h->btasks[colour].empty()) {
     a.tasks = h->d_btasks[colour];
     a.ntasks = (int32_t)h->btasks[colour].size();
     const int grid = std::max(1, std::min<int>(a.ntasks, h->bf16_grid));
@@ -869,8 +870,8 @@ int autotune_dense(tree_ot_handle* h, cudaStream_t s) {
     h->dense_tma = tma;
     for (int rep = 0; rep < 4; ++rep) {
       if (rep == 1) CUDA_TRY(cudaEventRecord(e0, s));
-      RC_TRY(launch_apply(h, 0, s));
-      RC_TRY(launch_apply(h, 1, s));
+      RC_TRY(launch_apply(h, 0, s, true));
+      RC_TRY(launch_apply(h, 1, s, true));
     }
     CUDA_TRY(cudaEventRecord(e1, s));
     CUDA_TRY(cudaEventSynchronize(e1));
