@@ -111,6 +111,11 @@ typedef struct tree_ot_problem {
  * distances (coordinates split hi + lo, ~1.8x the FP32 work per element); this
  * bit uses the exact form from the first half-step for every such problem. */
 #define TREE_OT_OPT_EXACT_DIST   4u
+/* Stored costs: when the device has room (free memory above twice the matrices'
+ * size plus 1 GiB) every edge also keeps its cost transposed, so the column
+ * node's apply streams contiguous rows like the row node's (the same bytes per
+ * apply; twice the memory).  This bit keeps only the given layout. */
+#define TREE_OT_OPT_NO_TRANSPOSE 8u
 
 #define TREE_OT_TOL_SUM          0  /* the paper's stopping sum (Bipartite Iterative Scaling) */
 #define TREE_OT_TOL_MAX          1  /* the largest single term of that sum                 */

@@ -198,6 +198,7 @@ struct tree_ot_handle {
   int32_t grid_mult = 0;                   // 0: occupancy-derived grid; else CTAs per SM (autotuned)
   int32_t rec_variant = 0;                 // recomputed-cost kernel register budget (autotuned)
   int32_t dense_tma = 0;                   // stored-cost tasks on the bulk-copy staged kernel
+  bool use_ct = false;                     // stored costs also kept transposed (column owners stream rows)
   StreamTask* d_stasks[2] = {nullptr, nullptr};  // slot-0 tasks of each colour, resolved for that kernel
   void* d_setbuf = nullptr;                // batched potential set: directed-edge list + records
   int64_t setbuf_cap = 0;                  // items d_setbuf holds
@@ -288,11 +289,12 @@ void build_apply_tasks(tree_ot_handle* h, int32_t rec_ob) {
       for (int32_t o0 = 0; o0 < own.n; o0 += 64)
         tl.push_back(Task{(int32_t)di, dense ? (d.dir == 0 ? TASK_ROW : TASK_COL) : TASK_RECOMP, o0,
                           std::min(64, own.n - o0), 0, nbn.n, 0, 0});
-    } else if (dense && d.dir == 0) {
+    } else if (dense && (d.dir == 0 || h->use_ct)) {
+      // rows of C (owner = row node) or of its transpose (owner = column node; pad = 1)
       for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
         for (int32_t s = 0; s < d.nsplit; ++s)
           tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
-                            std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
+                            std::min(kRowCols, nbn.n - s * kRowCols), s, d.dir == 0 ? 0 : 1});
     } else if (dense) {
       for (int32_t s = 0; s < d.nsplit; ++s)
         for (int32_t o0 = 0; o0 < own.n; o0 += kColCols)
@@ -842,8 +844,13 @@ int upload_stream_tasks(tree_ot_handle* h, cudaStream_t s) {
       x.prob = d.prob;
       x.ocount = t.ocount;
       x.rcount = t.rcount;
-      x.ld = e.ld;
-      x.C = t.kind == TASK_ROW ? e.C + (int64_t)t.o0 * e.ld + t.r0 : e.C + (int64_t)t.r0 * e.ld + t.o0;
+      if (t.kind == TASK_ROW && t.pad == 1) {  // rows of the transpose
+        x.ld = e.ldt;
+        x.C = e.CT + (int64_t)t.o0 * e.ldt + t.r0;
+      } else {
+        x.ld = e.ld;
+        x.C = t.kind == TASK_ROW ? e.C + (int64_t)t.o0 * e.ld + t.r0 : e.C + (int64_t)t.r0 * e.ld + t.o0;
+      }
       x.m_off = d.off + t.o0;
       x.h_off = d.rev_off + t.r0;
       x.out_off = d.part_off + (int64_t)t.split * h->nodes[d.owner].n + t.o0;
@@ -981,6 +988,25 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   h->fp64 = o.precision == TREE_OT_PREC_FP64;
   h->nprob = num_probs;
   int rc = TREE_OT_OK;
+  // Stored costs: the column owner's apply reduces down columns, which streams
+  // short row pieces at a large stride.  When the device has the room, each edge
+  // also keeps its cost transposed so both directions stream contiguous rows.
+  if (!h->fp64 && !(o.flags & TREE_OT_OPT_NO_TRANSPOSE)) {
+    int64_t ct_bytes = 0;
+    for (int32_t p = 0; p < num_probs; ++p) {
+      if (probs[p].cost_kind != TREE_OT_COST_DENSE_F32) continue;
+      for (int32_t e = 0; e < probs[p].num_nodes - 1; ++e) {
+        const int64_t na = probs[p].support_size[probs[p].edges[2 * e]];
+        const int64_t nb = probs[p].support_size[probs[p].edges[2 * e + 1]];
+        ct_bytes += 4 * nb * align_up(na, 4) * 2;  // the transpose, and room for a padded copy of C
+      }
+    }
+    size_t free_b = 0, total_b = 0;
+    if (ct_bytes > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+        (int64_t)free_b > ct_bytes + (int64_t(1) << 30))
+      h->use_ct = true;
+    cudaGetLastError();
+  }
   auto bail = [&](int code) {
     tree_ot_destroy(h);
     return code;
@@ -1055,7 +1081,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
         if (h->fp64)
           d.nsplit = 1;
         else if (P.cost_kind == TREE_OT_COST_DENSE_F32)
-          d.nsplit = k == 0 ? (n_nbr + kRowCols - 1) / kRowCols : (n_nbr + kColRows - 1) / kColRows;
+          d.nsplit = (k == 0 || h->use_ct) ? (n_nbr + kRowCols - 1) / kRowCols : (n_nbr + kColRows - 1) / kColRows;
         else
           d.nsplit = (n_nbr + kRecRed - 1) / kRecRed;
         d.off = vec_off;
@@ -1104,10 +1130,11 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
         for (int32_t o0 = 0; o0 < own.n; o0 += 64)
           h->atasks.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(64, own.n - o0), 0, nbn.n, 0, 0});
       } else {
+        const int32_t rows = h->use_ct ? kRowCols : kColRows;  // reduction rows per split (see nsplit)
         for (int32_t s = 0; s < d.nsplit; ++s)
           for (int32_t o0 = 0; o0 < own.n; o0 += kBfCols)
-            tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kBfCols, own.n - o0), s * kColRows,
-                              std::min(kColRows, nbn.n - s * kColRows), s, 0});
+            tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kBfCols, own.n - o0), s * rows,
+                              std::min(rows, nbn.n - s * rows), s, 0});
       }
     }
     h->lowp = any;
@@ -1242,6 +1269,14 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       }
       cudaError_t ce = launch_scan_cost(ed.C, ed.ld, ed.na, ed.nb, h->d_scan, s);
       if (ce != cudaSuccess) return bail(cuda_fail(ce, "cost scan"));
+      if (h->use_ct) {
+        float* ct = nullptr;
+        ed.ldt = align_up(ed.na, 4);
+        if ((rc = h->alloc(&ct, (int64_t)ed.nb * ed.ldt))) return bail(rc);
+        ce = launch_transpose_pad(ed.C, ed.ld, ed.na, ed.nb, ct, ed.ldt, s);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cost transpose"));
+        ed.CT = ct;
+      }
     }
   }
   // plan tables

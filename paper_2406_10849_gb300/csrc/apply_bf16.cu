@@ -27,6 +27,8 @@ namespace treeot {
 namespace {
 
 #define kInf (__int_as_float(0x7f800000))
+constexpr int kBfRowsPerIter = 4;  // ROW: rows per warp iteration (16 loads of 16 B in flight per lane)
+constexpr int kBfColChunk = 16;    // COL: rows per chunk (16 loads of 16 B in flight per lane)
 
 __device__ __forceinline__ float quantf(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
 
@@ -115,52 +117,49 @@ __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nvec = (t.rcount + 7) >> 3;  // uint4 = 8 BF16 entries
-  // two rows per warp iteration: eight 16-byte loads in flight per lane
-  for (int r = warp; r < t.ocount; r += 2 * (kApplyThreads / 32)) {
-    const int r2 = r + kApplyThreads / 32;
-    const bool has2 = r2 < t.ocount;
-    const uint4* row0 = reinterpret_cast<const uint4*>(e.K + (int64_t)(t.o0 + r) * e.ldk + t.r0);
-    const uint4* row1 = reinterpret_cast<const uint4*>(e.K + (int64_t)(t.o0 + (has2 ? r2 : r)) * e.ldk + t.r0);
-    uint4 k[8];
+  constexpr int W = kApplyThreads / 32;
+  // kBfRowsPerIter rows per warp iteration: 4 x kBfRowsPerIter 16-byte loads in flight per lane
+  for (int r = warp; r < t.ocount; r += kBfRowsPerIter * W) {
+    uint4 k[kBfRowsPerIter][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = lane + 32 * i;
-      k[i] = v < nvec ? __ldg(row0 + v) : make_uint4(0u, 0u, 0u, 0u);
-      k[4 + i] = (v < nvec && has2) ? __ldg(row1 + v) : make_uint4(0u, 0u, 0u, 0u);
+    for (int q = 0; q < kBfRowsPerIter; ++q) {
+      const int rq = r + q * W;
+      const bool has = rq < t.ocount;
+      const uint4* row = reinterpret_cast<const uint4*>(e.K + (int64_t)(t.o0 + (has ? rq : r)) * e.ldk + t.r0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int v = lane + 32 * i;
+        k[q][i] = (v < nvec && has) ? __ldg(row + v) : make_uint4(0u, 0u, 0u, 0u);
+      }
     }
-    float acc0 = 0.f, acc1 = 0.f;
+    float acc[kBfRowsPerIter];
+#pragma unroll
+    for (int q = 0; q < kBfRowsPerIter; ++q) acc[q] = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int y0 = 8 * (lane + 32 * i);
       const float4 w0 = *reinterpret_cast<const float4*>(wv + y0);
       const float4 w1 = *reinterpret_cast<const float4*>(wv + y0 + 4);
-      acc0 = fmaf(bf_lo(k[i].x), w0.x, acc0);
-      acc0 = fmaf(bf_hi(k[i].x), w0.y, acc0);
-      acc0 = fmaf(bf_lo(k[i].y), w0.z, acc0);
-      acc0 = fmaf(bf_hi(k[i].y), w0.w, acc0);
-      acc0 = fmaf(bf_lo(k[i].z), w1.x, acc0);
-      acc0 = fmaf(bf_hi(k[i].z), w1.y, acc0);
-      acc0 = fmaf(bf_lo(k[i].w), w1.z, acc0);
-      acc0 = fmaf(bf_hi(k[i].w), w1.w, acc0);
-      acc1 = fmaf(bf_lo(k[4 + i].x), w0.x, acc1);
-      acc1 = fmaf(bf_hi(k[4 + i].x), w0.y, acc1);
-      acc1 = fmaf(bf_lo(k[4 + i].y), w0.z, acc1);
-      acc1 = fmaf(bf_hi(k[4 + i].y), w0.w, acc1);
-      acc1 = fmaf(bf_lo(k[4 + i].z), w1.x, acc1);
-      acc1 = fmaf(bf_hi(k[4 + i].z), w1.y, acc1);
-      acc1 = fmaf(bf_lo(k[4 + i].w), w1.z, acc1);
-      acc1 = fmaf(bf_hi(k[4 + i].w), w1.w, acc1);
+#pragma unroll
+      for (int q = 0; q < kBfRowsPerIter; ++q) {
+        acc[q] = fmaf(bf_lo(k[q][i].x), w0.x, acc[q]);
+        acc[q] = fmaf(bf_hi(k[q][i].x), w0.y, acc[q]);
+        acc[q] = fmaf(bf_lo(k[q][i].y), w0.z, acc[q]);
+        acc[q] = fmaf(bf_hi(k[q][i].y), w0.w, acc[q]);
+        acc[q] = fmaf(bf_lo(k[q][i].z), w1.x, acc[q]);
+        acc[q] = fmaf(bf_hi(k[q][i].z), w1.y, acc[q]);
+        acc[q] = fmaf(bf_lo(k[q][i].w), w1.z, acc[q]);
+        acc[q] = fmaf(bf_hi(k[q][i].w), w1.w, acc[q]);
+      }
     }
-    acc0 = warp_sum(acc0);
-    acc1 = warp_sum(acc1);
-    if (lane == 0) {
-      const int x0 = t.o0 + r;
-      A.part32[d.part_off + (int64_t)t.split * e.na + x0] =
-          make_float2(A.arho[d.off + x0] - A.bh[d.off + x0], acc0 * ex2(-A.bl[d.off + x0]));
-      if (has2) {
-        const int x1 = t.o0 + r2;
-        A.part32[d.part_off + (int64_t)t.split * e.na + x1] =
-            make_float2(A.arho[d.off + x1] - A.bh[d.off + x1], acc1 * ex2(-A.bl[d.off + x1]));
+#pragma unroll
+    for (int q = 0; q < kBfRowsPerIter; ++q) {
+      const float sq = warp_sum(acc[q]);
+      const int rq = r + q * W;
+      if (lane == 0 && rq < t.ocount) {
+        const int x = t.o0 + rq;
+        A.part32[d.part_off + (int64_t)t.split * e.na + x] =
+            make_float2(A.arho[d.off + x] - A.bh[d.off + x], sq * ex2(-A.bl[d.off + x]));
       }
     }
   }
@@ -170,9 +169,9 @@ __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
 __device__ void bf_col_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];  // owner = column node b
   const EdgeD e = A.edges[d.edge];
-  float* wv = sm;                    // [kColRows] weights of the reduction rows
-  float* comb = sm + kColRows;       // [8][kBfCols] per-warp column sums
-  for (int i = threadIdx.x; i < kColRows; i += kApplyThreads) {
+  float* wv = sm;                    // [kRowCols] weights of the reduction rows (<= kRowCols per split)
+  float* comb = sm + kRowCols;       // [8][kBfCols] per-warp column sums
+  for (int i = threadIdx.x; i < t.rcount; i += kApplyThreads) {
     float w = 0.f;
     if (i < t.rcount) {
       const int64_t o = d.rev_off + t.r0 + i;  // row-side vectors (owner a)
@@ -190,16 +189,16 @@ __device__ void bf_col_task(const ApplyArgs& A, const Task& t, float* sm) {
   const bool on = c0 < t.ocount;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const uint16_t* base = e.K + t.o0 + c0;
-  for (int rr = rr0; rr < rr1; rr += 8) {
-    uint4 k[8];
+  for (int rr = rr0; rr < rr1; rr += kBfColChunk) {
+    uint4 k[kBfColChunk];  // kBfColChunk 16-byte loads in flight per lane
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < kBfColChunk; ++i) {
       const int xr = rr + i;
       k[i] = (on && xr < rr1) ? __ldg(reinterpret_cast<const uint4*>(base + (int64_t)(t.r0 + xr) * e.ldk))
                               : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < kBfColChunk; ++i) {
       const float w = (rr + i < rr1) ? wv[rr + i] : 0.f;
       acc[0] = fmaf(bf_lo(k[i].x), w, acc[0]);
       acc[1] = fmaf(bf_hi(k[i].x), w, acc[1]);
@@ -226,7 +225,7 @@ __device__ void bf_col_task(const ApplyArgs& A, const Task& t, float* sm) {
 }
 
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_bf16_kernel(ApplyArgs A) {
-  __shared__ __align__(16) float sm[kColRows + 8 * kBfCols];  // 10 KB
+  __shared__ __align__(16) float sm[kRowCols + 8 * kBfCols];  // 12 KB
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
     const int prob = A.dedges[t.dedge].prob;

@@ -70,7 +70,10 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
   const EdgeD e = A.edges[d.edge];
   const ProbD P = A.probs[d.prob];
-  const int n_owner = e.na;
+  // owner = row node: rows of C; owner = column node (pad = 1): rows of the transpose
+  const float* Cm = t.pad ? e.CT : e.C;
+  const int64_t ldm = t.pad ? e.ldt : e.ld;
+  const int n_owner = t.pad ? e.nb : e.na;
   float* sh = sm;
   float* sl = sm + kRowCols;
   const int tid = threadIdx.x;
@@ -88,10 +91,10 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const uint32_t row_bytes = 16u * (uint32_t)nvec;  // within the row: the stride is padded to 4 floats
   for (int r = warp; r < t.ocount; r += kApplyThreads / 32) {
     const int x = t.o0 + r;
-    const float4* row = reinterpret_cast<const float4*>(e.C + (int64_t)x * e.ld + t.r0);
-    // the warp's next row heads for L2 while this one is in flight: twice the bytes in flight per warp
+    const float4* row = reinterpret_cast<const float4*>(Cm + (int64_t)x * ldm + t.r0);
+    // the warp's next row heads for L2 while this one is in flight
     if (lane == 0 && r + kApplyThreads / 32 < t.ocount)
-      prefetch_l2(e.C + (int64_t)(x + kApplyThreads / 32) * e.ld + t.r0, row_bytes);
+      prefetch_l2(Cm + (int64_t)(x + kApplyThreads / 32) * ldm + t.r0, row_bytes);
     float4 c[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {

@@ -346,7 +346,41 @@ __global__ void pad_copy_kernel(const float* src, int64_t src_ld, float* dst, in
     dst[(int64_t)r * dst_ld + c] = c < cols ? src[(int64_t)r * src_ld + c] : INFINITY;
 }
 
+// 32 x 32 tiles through shared memory: reads and writes both coalesced
+// src rows r < rows (of this launch's slice), columns c < cols; dst row c, columns
+// r < dst_cols of the slice (rows <= r < dst_cols are the +inf pads)
+__global__ void transpose_pad_kernel(const float* src, int64_t src_ld, int64_t rows, int32_t cols, float* dst,
+                                     int64_t dst_ld, int64_t dst_cols) {
+  __shared__ float tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[r * src_ld + c] : INFINITY;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < dst_cols) dst[c * dst_ld + r] = tile[threadIdx.x][i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_transpose_pad(const float* src, int64_t src_ld, int32_t rows, int32_t cols, float* dst,
+                                 int64_t dst_ld, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  // dst columns run to dst_ld (>= rows): the tiles past rows write the +inf pads
+  const int64_t gy = (dst_ld + 31) / 32, gx = ((int64_t)cols + 31) / 32;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    const int64_t ny = gy - y0 < 65535 ? gy - y0 : 65535;
+    const int64_t first = y0 * 32;  // first source row / destination column of this slice
+    dim3 grid((unsigned)gx, (unsigned)ny);
+    transpose_pad_kernel<<<grid, dim3(32, 8), 0, s>>>(src + (first < rows ? first : 0) * src_ld, src_ld,
+                                                       (int64_t)rows - first, cols, dst + first, dst_ld,
+                                                       dst_ld - first);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_check64(const CheckArgs& a, cudaStream_t s) {
   if (a.ntasks <= 0) return cudaSuccess;

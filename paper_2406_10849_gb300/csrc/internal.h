@@ -50,6 +50,8 @@ struct DEdgeD {
 struct EdgeD {
   const float* C;   // dense cost, rows = node a, row stride ld (multiple of 4); pad columns +inf
   int64_t ld;
+  const float* CT;  // its transpose (rows = node b, stride ldt, +inf pads) or null
+  int64_t ldt;
   uint16_t* K;      // absorbed BF16 Gibbs kernel (low-precision mode), row stride ldk (multiple of 8)
   int64_t ldk;
   int32_t a, b;     // global node ids (rows a, columns b)
@@ -86,7 +88,7 @@ struct Task {
   int32_t o0, ocount;   // output range (owner support)
   int32_t r0, rcount;   // reduction range (neighbour support)
   int32_t split;
-  int32_t pad;          // RECOMP: warp groups sharing the task (1, 2, 4, 8); else 0
+  int32_t pad;          // RECOMP: warp groups sharing the task (1, 2, 4, 8); ROW: 1 = rows of CT
 };
 
 // A stored-cost (ROW / COL) task with every address resolved on the host, for
@@ -251,6 +253,9 @@ cudaError_t launch_operand(const double* f, const double* Z, const double* logg,
                            float* vh, float* vl, cudaStream_t s);
 cudaError_t launch_check64(const CheckArgs& a, cudaStream_t s);
 cudaError_t launch_scan_cost(const float* C, int64_t ld, int32_t rows, int32_t cols, int32_t* bad, cudaStream_t s);
+// dst (cols x dst_ld) = transpose of src (rows x src_ld, first cols columns), +inf pads
+cudaError_t launch_transpose_pad(const float* src, int64_t src_ld, int32_t rows, int32_t cols, float* dst,
+                                 int64_t dst_ld, cudaStream_t s);
 // coordinates split hi + lo for the exact-distance recomputation (cmax: nprob scratch words)
 cudaError_t launch_split_coords(const float* coords, const NodeD* nodes, int32_t nnodes, const ProbD* probs,
                                 uint32_t* cmax, int32_t nprob, float* hi, float* lo, cudaStream_t s);

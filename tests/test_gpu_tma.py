@@ -48,13 +48,16 @@ DENSE_CASES = {
 }
 
 
+@pytest.mark.parametrize("transpose", [True, False])
 @pytest.mark.parametrize("kernel", ["tma", "ldg"])
 @pytest.mark.parametrize("name", sorted(DENSE_CASES))
 @pytest.mark.parametrize("steps", [1, 9])
-def test_dense_kernel_iterate_parity(T, kernel, name, steps):
+def test_dense_kernel_iterate_parity(T, kernel, name, steps, transpose):
+    """Both stored-cost kernels, with the column owner's apply on the transposed
+    copy (rows) or on the given layout (columns)."""
     p = DENSE_CASES[name]()
     ref = O.run_half_steps(p, steps)
-    with T.Solver([p], T.options(precision="fp32", dense_kernel=kernel)) as s:
+    with T.Solver([p], T.options(precision="fp32", dense_kernel=kernel, transpose=transpose)) as s:
         assert s.plan_stats()["dense_tma"] == (1 if kernel == "tma" else 0)
         s.half_steps(steps)
         got = s.potentials(0)
