@@ -357,12 +357,14 @@ def test_warm_start_from_converged_potentials(T):
 # absorbed BF16 phase + FP32 refinement (stored costs)
 # ---------------------------------------------------------------------------
 
-def test_bf16_phase_then_fp32_refinement_reaches_tolerance(T):
+@pytest.mark.parametrize("transpose", [True, False])
+def test_bf16_phase_then_fp32_refinement_reaches_tolerance(T, transpose):
     """BF16 absorbed kernel until the stopping quantity is below refine_tol, then
-    the FP32 kernel: the result meets the FP32 parity bar."""
+    the FP32 kernel: the result meets the FP32 parity bar (column node's apply on
+    the transposed kernel, or down the columns)."""
     p = gen.prufer_problem(seed=3004, J=12, n=700, num_leaves=6, eps=0.01)
     opts = T.options(precision="fp32", tol=2e-7, tol_kind="max", apply_mode="bf16", refine_tol=1e-3,
-                     absorb_tau=24, lowp_start=4, max_half_steps=40000)
+                     absorb_tau=24, lowp_start=4, max_half_steps=40000, transpose=transpose)
     with T.Solver([p], opts) as s:
         rc, res = s.solve()
         got = s.potentials(0)
@@ -399,3 +401,20 @@ def test_bf16_iterate_close_to_oracle(T):
     ref = O.run_half_steps(p, 8)
     assert marginal_gap(p, got, ref) <= 3e-2
     assert rel_err(got, ref, p.eps) <= 5e-2
+
+
+def test_bf16_transposed_kernel_matches_column_sums(T):
+    """The transposed BF16 copy holds the same values: the column node's apply on
+    it agrees with the column-sum apply far inside the BF16 phase's own error
+    (FP32 summation order differs, and with it the half-step at which an edge's
+    drift crosses absorb_tau and it is re-absorbed)."""
+    p = gen.prufer_problem(seed=3006, J=10, n=1100, num_leaves=5, eps=0.01)
+    out = {}
+    for tr in (True, False):
+        opts = T.options(precision="fp32", apply_mode="bf16", lowp_start=2, absorb_tau=24, transpose=tr)
+        with T.Solver([p], opts) as s:
+            s.half_steps(9)
+            out[tr] = s.potentials(0)
+    ref = O.run_half_steps(p, 9)
+    assert rel_err(out[True], out[False], p.eps) <= 5e-4
+    assert rel_err(out[True], ref, p.eps) <= 5e-2 and rel_err(out[False], ref, p.eps) <= 5e-2
