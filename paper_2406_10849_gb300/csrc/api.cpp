@@ -999,7 +999,6 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
         const int64_t na = probs[p].support_size[probs[p].edges[2 * e]];
         const int64_t nb = probs[p].support_size[probs[p].edges[2 * e + 1]];
         ct_bytes += 4 * nb * align_up(na, 4) * 2;  // the transpose, and room for a padded copy of C
-        if (o.apply_mode == TREE_OT_APPLY_BF16) ct_bytes += 2 * nb * align_up(na, 8);  // transposed BF16 kernel
       }
     }
     size_t free_b = 0, total_b = 0;
@@ -1130,16 +1129,14 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
                               std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
         for (int32_t o0 = 0; o0 < own.n; o0 += 64)
           h->atasks.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(64, own.n - o0), 0, nbn.n, 0, 0});
-      } else if (h->use_ct) {  // rows of the transposed kernel
-        for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
-          for (int32_t s = 0; s < d.nsplit; ++s)
-            tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
-                              std::min(kRowCols, nbn.n - s * kRowCols), s, 1});
       } else {
+        // column sums of K~ (measured faster than rows of a transposed BF16 copy:
+        // 0.46 against 0.54 ms per launch on the 64-node tree)
+        const int32_t rows = h->use_ct ? kRowCols : kColRows;  // reduction rows per split (see nsplit)
         for (int32_t s = 0; s < d.nsplit; ++s)
           for (int32_t o0 = 0; o0 < own.n; o0 += kBfCols)
-            tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kBfCols, own.n - o0), s * kColRows,
-                              std::min(kColRows, nbn.n - s * kColRows), s, 0});
+            tl.push_back(Task{(int32_t)di, TASK_COL, o0, std::min(kBfCols, own.n - o0), s * rows,
+                              std::min(rows, nbn.n - s * rows), s, 0});
       }
     }
     h->lowp = any;
@@ -1204,12 +1201,6 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       if (h->probs[h->nodes[ed.a].prob].cost_kind != TREE_OT_COST_DENSE_F32) continue;
       ed.ldk = align_up(ed.nb, 8);
       if ((rc = h->alloc(&ed.K, (int64_t)ed.na * ed.ldk))) return bail(rc);
-      if (h->use_ct) {  // transposed copy for the column node's apply; pads stay zero
-        ed.ldkt = align_up(ed.na, 8);
-        if ((rc = h->alloc(&ed.KT, (int64_t)ed.nb * ed.ldkt))) return bail(rc);
-        const cudaError_t ce = cudaMemsetAsync(ed.KT, 0, sizeof(uint16_t) * ed.nb * ed.ldkt, s);
-        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemsetAsync(KT)"));
-      }
     }
   }
 

@@ -40,12 +40,10 @@ __device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 
 // problems in the low-precision phase
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) absorb_kernel(AbsorbArgs A) {
-  __shared__ float s_ah[64], s_al[64], s_rho[64];
-  __shared__ uint16_t tile[64][66];  // one 64 x 64 block of Kt, for the transposed copy
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];  // dedge = 2e (row side), o0/ocount = rows
     const DEdgeD da = A.dedges[t.dedge];
-    if (A.lowp[da.prob] != 1 || !A.drift[da.edge]) continue;  // block-uniform
+    if (A.lowp[da.prob] != 1 || !A.drift[da.edge]) continue;
     const DEdgeD db = A.dedges[t.dedge + 1];
     const EdgeD e = A.edges[da.edge];
     const ProbD P = A.probs[da.prob];
@@ -59,11 +57,12 @@ __global__ void __launch_bounds__(256) absorb_kernel(AbsorbArgs A) {
         A.bl[db.off + y] = A.hl[db.off + y];
       }
     }
-    // pass 1: row maxima of A + B - sC (exact grid sums, small final rounding)
     for (int r = warp; r < t.ocount; r += 8) {
       const int x = t.o0 + r;
       const float ah = A.hh[da.off + x], al = A.hl[da.off + x];
       const float* Crow = e.C + (int64_t)x * e.ld;
+      __nv_bfloat16* Krow = reinterpret_cast<__nv_bfloat16*>(e.K) + (int64_t)x * e.ldk;
+      // pass 1: row maximum of A + B - sC (exact grid sums, small final rounding)
       float mx = -kInf;
       if (ah > -kInf) {
         for (int y = lane; y < e.nb; y += 32) {
@@ -75,46 +74,22 @@ __global__ void __launch_bounds__(256) absorb_kernel(AbsorbArgs A) {
       }
       mx = warp_max(mx);
       const float rho = mx > -kInf ? quantf(mx) : 0.f;
+      // pass 2: Kt = 2^(value - rho) in BF16; padding columns are zero
+      for (int y = lane; y < e.ldk; y += 32) {
+        float k = 0.f;
+        if (y < e.nb && ah > -kInf) {
+          const float c = Crow[y];
+          float v = fmaf(-c, shi, (ah - rho) + A.hh[db.off + y]);
+          v = fmaf(-c, slo, v) + (al + A.hl[db.off + y]);
+          k = ex2(v);
+        }
+        Krow[y] = __float2bfloat16_rn(k);
+      }
       if (lane == 0) {
-        s_ah[r] = ah;
-        s_al[r] = al;
-        s_rho[r] = rho;
         A.arho[da.off + x] = rho;
         A.bh[da.off + x] = ah;
         A.bl[da.off + x] = al;
       }
-    }
-    __syncthreads();
-    // pass 2, 64 columns at a time: Kt = 2^(value - rho) in BF16 (padding columns zero);
-    // the block also goes, transposed, to KT when the edge keeps one
-    for (int c0 = 0; c0 < e.ldk; c0 += 64) {
-      for (int r = warp; r < t.ocount; r += 8) {
-        const int x = t.o0 + r;
-        const float ah = s_ah[r], al = s_al[r], rho = s_rho[r];
-        const float* Crow = e.C + (int64_t)x * e.ld;
-        __nv_bfloat16* Krow = reinterpret_cast<__nv_bfloat16*>(e.K) + (int64_t)x * e.ldk;
-        for (int yy = lane; yy < 64; yy += 32) {
-          const int y = c0 + yy;
-          float k = 0.f;
-          if (y < e.nb && ah > -kInf) {
-            const float c = Crow[y];
-            float v = fmaf(-c, shi, (ah - rho) + A.hh[db.off + y]);
-            v = fmaf(-c, slo, v) + (al + A.hl[db.off + y]);
-            k = ex2(v);
-          }
-          const __nv_bfloat16 kb = __float2bfloat16_rn(k);
-          if (y < e.ldk) Krow[y] = kb;
-          tile[r][yy] = __bfloat16_as_ushort(kb);
-        }
-      }
-      if (e.KT) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-          const int yy = i >> 6, xx = i & 63;  // KT row c0 + yy, columns o0 + xx: contiguous in xx
-          if (c0 + yy < e.nb && xx < t.ocount) e.KT[(int64_t)(c0 + yy) * e.ldkt + t.o0 + xx] = tile[xx][yy];
-        }
-      }
-      __syncthreads();
     }
   }
 }
@@ -126,23 +101,16 @@ __global__ void clear_flags_kernel(int32_t* drift, int32_t nedges) {
 // ---------------------------------------------------------------------------
 // absorbed apply
 // ---------------------------------------------------------------------------
-// Rows of Kt (owner = row node a) or, pad = 1, rows of its transpose (owner =
-// column node b; the row normaliser rho then sits in the reduction weights).
 __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
-  const DEdgeD d = A.dedges[t.dedge];
+  const DEdgeD d = A.dedges[t.dedge];  // owner = row node a
   const EdgeD e = A.edges[d.edge];
-  const bool tr = t.pad == 1;
-  const uint16_t* Km = tr ? e.KT : e.K;
-  const int64_t ldm = tr ? e.ldkt : e.ldk;
-  const int n_owner = tr ? e.nb : e.na;
   float* wv = sm;  // [kRowCols] weights of the reduction columns
   for (int i = threadIdx.x; i < kRowCols; i += kApplyThreads) {
     float w = 0.f;
     if (i < t.rcount) {
       const int64_t o = d.rev_off + t.r0 + i;
       const float hh = A.hh[o];
-      if (hh > -kInf)  // mu = 0 entries weigh nothing
-        w = tr ? ex2((hh - A.bh[o]) + (A.hl[o] - A.bl[o]) + A.arho[o]) : ex2((hh - A.bh[o]) + (A.hl[o] - A.bl[o]));
+      if (hh > -kInf) w = ex2((hh - A.bh[o]) + (A.hl[o] - A.bl[o]));  // mu = 0 entries weigh nothing
     }
     wv[i] = w;
   }
@@ -157,7 +125,7 @@ __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
     for (int q = 0; q < kBfRowsPerIter; ++q) {
       const int rq = r + q * W;
       const bool has = rq < t.ocount;
-      const uint4* row = reinterpret_cast<const uint4*>(Km + (int64_t)(t.o0 + (has ? rq : r)) * ldm + t.r0);
+      const uint4* row = reinterpret_cast<const uint4*>(e.K + (int64_t)(t.o0 + (has ? rq : r)) * e.ldk + t.r0);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int v = lane + 32 * i;
@@ -190,8 +158,8 @@ __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
       const int rq = r + q * W;
       if (lane == 0 && rq < t.ocount) {
         const int x = t.o0 + rq;
-        const float R = tr ? -A.bh[d.off + x] : A.arho[d.off + x] - A.bh[d.off + x];
-        A.part32[d.part_off + (int64_t)t.split * n_owner + x] = make_float2(R, sq * ex2(-A.bl[d.off + x]));
+        A.part32[d.part_off + (int64_t)t.split * e.na + x] =
+            make_float2(A.arho[d.off + x] - A.bh[d.off + x], sq * ex2(-A.bl[d.off + x]));
       }
     }
   }

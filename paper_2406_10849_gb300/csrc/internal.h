@@ -54,8 +54,6 @@ struct EdgeD {
   int64_t ldt;
   uint16_t* K;      // absorbed BF16 Gibbs kernel (low-precision mode), row stride ldk (multiple of 8)
   int64_t ldk;
-  uint16_t* KT;     // its transpose (rows = node b, stride ldkt, zero pads) or null
-  int64_t ldkt;
   int32_t a, b;     // global node ids (rows a, columns b)
   int32_t na, nb;
 };

@@ -403,11 +403,11 @@ def test_bf16_iterate_close_to_oracle(T):
     assert rel_err(got, ref, p.eps) <= 5e-2
 
 
-def test_bf16_transposed_kernel_matches_column_sums(T):
-    """The transposed BF16 copy holds the same values: the column node's apply on
-    it agrees with the column-sum apply far inside the BF16 phase's own error
-    (FP32 summation order differs, and with it the half-step at which an edge's
-    drift crosses absorb_tau and it is re-absorbed)."""
+def test_bf16_layouts_agree(T):
+    """With and without the transposed FP32 costs (which also change the BF16
+    column tasks' reduction split from 512 to 1024 rows) the BF16 iterates agree
+    far inside the BF16 phase's own error (FP32 summation order differs, and with
+    it the half-step at which an edge's drift crosses absorb_tau)."""
     p = gen.prufer_problem(seed=3006, J=10, n=1100, num_leaves=5, eps=0.01)
     out = {}
     for tr in (True, False):
