@@ -1123,9 +1123,11 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       const NodeD& nbn = h->nodes[d.nbr];
       std::vector<Task>& tl = h->btasks[own.colour];
       if (d.dir == 0) {
-        for (int32_t o0 = 0; o0 < own.n; o0 += 8 * kRowRowsPerWarp)
+        // taller than the FP32 row tasks: a BF16 row is half the bytes, and every task
+        // first forms its columns' weights
+        for (int32_t o0 = 0; o0 < own.n; o0 += kBfRowTask)
           for (int32_t s = 0; s < d.nsplit; ++s)
-            tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(8 * kRowRowsPerWarp, own.n - o0), s * kRowCols,
+            tl.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(kBfRowTask, own.n - o0), s * kRowCols,
                               std::min(kRowCols, nbn.n - s * kRowCols), s, 0});
         for (int32_t o0 = 0; o0 < own.n; o0 += 64)
           h->atasks.push_back(Task{(int32_t)di, TASK_ROW, o0, std::min(64, own.n - o0), 0, nbn.n, 0, 0});

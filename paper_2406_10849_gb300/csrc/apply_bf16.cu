@@ -28,7 +28,7 @@ namespace {
 
 #define kInf (__int_as_float(0x7f800000))
 constexpr int kBfRowsPerIter = 4;  // ROW: rows per warp iteration (16 loads of 16 B in flight per lane)
-constexpr int kBfColChunk = 16;    // COL: rows per chunk (16 loads of 16 B in flight per lane)
+constexpr int kBfColChunk = 8;     // COL: rows per chunk (8 loads of 16 B in flight per lane)
 
 __device__ __forceinline__ float quantf(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
 
@@ -104,6 +104,26 @@ __global__ void clear_flags_kernel(int32_t* drift, int32_t nedges) {
 __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];  // owner = row node a
   const EdgeD e = A.edges[d.edge];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nvec = (t.rcount + 7) >> 3;  // uint4 = 8 BF16 entries
+  constexpr int W = kApplyThreads / 32;
+  // kBfRowsPerIter rows per warp iteration: 4 x kBfRowsPerIter 16-byte loads in flight per lane
+  uint4 k[kBfRowsPerIter][4];
+  auto load = [&](int r) {
+#pragma unroll
+    for (int q = 0; q < kBfRowsPerIter; ++q) {
+      const int rq = r + q * W;
+      const bool has = rq < t.ocount;
+      const uint4* row = reinterpret_cast<const uint4*>(e.K + (int64_t)(t.o0 + (has ? rq : r)) * e.ldk + t.r0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int v = lane + 32 * i;
+        k[q][i] = (v < nvec && has) ? ldg_stream_u4(row + v) : make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+  };
+  // the first rows are in flight while the task's weights are formed
+  if (warp < t.ocount) load(warp);
   float* wv = sm;  // [kRowCols] weights of the reduction columns
   for (int i = threadIdx.x; i < kRowCols; i += kApplyThreads) {
     float w = 0.f;
@@ -115,23 +135,8 @@ __device__ void bf_row_task(const ApplyArgs& A, const Task& t, float* sm) {
     wv[i] = w;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nvec = (t.rcount + 7) >> 3;  // uint4 = 8 BF16 entries
-  constexpr int W = kApplyThreads / 32;
-  // kBfRowsPerIter rows per warp iteration: 4 x kBfRowsPerIter 16-byte loads in flight per lane
   for (int r = warp; r < t.ocount; r += kBfRowsPerIter * W) {
-    uint4 k[kBfRowsPerIter][4];
-#pragma unroll
-    for (int q = 0; q < kBfRowsPerIter; ++q) {
-      const int rq = r + q * W;
-      const bool has = rq < t.ocount;
-      const uint4* row = reinterpret_cast<const uint4*>(e.K + (int64_t)(t.o0 + (has ? rq : r)) * e.ldk + t.r0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int v = lane + 32 * i;
-        k[q][i] = (v < nvec && has) ? __ldg(row + v) : make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
+    if (r != warp) load(r);
     float acc[kBfRowsPerIter];
 #pragma unroll
     for (int q = 0; q < kBfRowsPerIter; ++q) acc[q] = 0.f;
@@ -171,6 +176,23 @@ __device__ void bf_col_task(const ApplyArgs& A, const Task& t, float* sm) {
   const EdgeD e = A.edges[d.edge];
   float* wv = sm;                    // [kRowCols] weights of the reduction rows (<= kRowCols per split)
   float* comb = sm + kRowCols;       // [8][kBfCols] per-warp column sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpw = (t.rcount + 7) / 8;
+  const int rr0 = warp * rpw;
+  const int rr1 = min(rr0 + rpw, t.rcount);
+  const int c0 = 8 * lane;
+  const bool on = c0 < t.ocount;
+  const uint16_t* base = e.K + t.o0 + c0;
+  uint4 k[kBfColChunk];  // kBfColChunk 16-byte loads in flight per lane
+  auto load = [&](int rr) {
+#pragma unroll
+    for (int i = 0; i < kBfColChunk; ++i) {
+      const int xr = rr + i;
+      k[i] = (on && xr < rr1) ? ldg_stream_u4(reinterpret_cast<const uint4*>(base + (int64_t)(t.r0 + xr) * e.ldk))
+                              : make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  load(rr0);  // the first rows are in flight while the task's weights are formed
   for (int i = threadIdx.x; i < t.rcount; i += kApplyThreads) {
     float w = 0.f;
     if (i < t.rcount) {
@@ -181,22 +203,9 @@ __device__ void bf_col_task(const ApplyArgs& A, const Task& t, float* sm) {
     wv[i] = w;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rpw = (t.rcount + 7) / 8;
-  const int rr0 = warp * rpw;
-  const int rr1 = min(rr0 + rpw, t.rcount);
-  const int c0 = 8 * lane;
-  const bool on = c0 < t.ocount;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const uint16_t* base = e.K + t.o0 + c0;
   for (int rr = rr0; rr < rr1; rr += kBfColChunk) {
-    uint4 k[kBfColChunk];  // kBfColChunk 16-byte loads in flight per lane
-#pragma unroll
-    for (int i = 0; i < kBfColChunk; ++i) {
-      const int xr = rr + i;
-      k[i] = (on && xr < rr1) ? __ldg(reinterpret_cast<const uint4*>(base + (int64_t)(t.r0 + xr) * e.ldk))
-                              : make_uint4(0u, 0u, 0u, 0u);
-    }
+    if (rr != rr0) load(rr);
 #pragma unroll
     for (int i = 0; i < kBfColChunk; ++i) {
       const float w = (rr + i < rr1) ? wv[rr + i] : 0.f;

@@ -74,33 +74,38 @@ __device__ void row_task(const ApplyArgs& A, const Task& t, float* sm) {
   const float* Cm = t.pad ? e.CT : e.C;
   const int64_t ldm = t.pad ? e.ldt : e.ld;
   const int n_owner = t.pad ? e.nb : e.na;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nvec = (t.rcount + 3) >> 2;
+  const uint32_t row_bytes = 16u * (uint32_t)nvec;  // within the row: the stride is padded to 4 floats
+  float4 c[8];
+  auto load = [&](int r) {
+    const int x = t.o0 + r;
+    const float4* row = reinterpret_cast<const float4*>(Cm + (int64_t)x * ldm + t.r0);
+    // the warp's next row heads for L2 while this one is in flight
+    if (lane == 0 && r + kApplyThreads / 32 < t.ocount)
+      prefetch_l2(Cm + (int64_t)(x + kApplyThreads / 32) * ldm + t.r0, row_bytes);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int v = lane + 32 * i;
+      c[i] = v < nvec ? ldg_stream(row + v) : make_float4(kInf, kInf, kInf, kInf);
+    }
+  };
+  if (warp < t.ocount) load(warp);  // the first row is in flight while the operand is staged
   float* sh = sm;
   float* sl = sm + kRowCols;
-  const int tid = threadIdx.x;
   for (int i = tid; i < kRowCols; i += kApplyThreads) {
     const bool v = i < t.rcount;
     sh[i] = v ? A.hh[d.rev_off + t.r0 + i] : 0.f;
     sl[i] = v ? A.hl[d.rev_off + t.r0 + i] : 0.f;
   }
   __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  const int nvec = (t.rcount + 3) >> 2;
   const float4* sh4 = reinterpret_cast<const float4*>(sh);
   const float4* sl4 = reinterpret_cast<const float4*>(sl);
   const float2 nhi = make_float2(-P.s2, -P.s2), nlo = make_float2(-P.s2_lo, -P.s2_lo);
-  const uint32_t row_bytes = 16u * (uint32_t)nvec;  // within the row: the stride is padded to 4 floats
   for (int r = warp; r < t.ocount; r += kApplyThreads / 32) {
     const int x = t.o0 + r;
-    const float4* row = reinterpret_cast<const float4*>(Cm + (int64_t)x * ldm + t.r0);
-    // the warp's next row heads for L2 while this one is in flight
-    if (lane == 0 && r + kApplyThreads / 32 < t.ocount)
-      prefetch_l2(Cm + (int64_t)(x + kApplyThreads / 32) * ldm + t.r0, row_bytes);
-    float4 c[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int v = lane + 32 * i;
-      c[i] = v < nvec ? ldg_stream(row + v) : make_float4(kInf, kInf, kInf, kInf);
-    }
+    if (r != warp) load(r);
     float R = A.fr[d.off + x];  // warp-uniform, on the grid
     float cm = -kInf, acc = 0.f;
     {

@@ -28,6 +28,7 @@ constexpr int kRecRed = 512;           // RECOMP task: reduction points per task
 constexpr int kNodeThreads = 256;
 constexpr int kNodeChunk = 512;        // node update: support points per CTA
 constexpr int kBfCols = 256;           // BF16 COL task: columns per task (32 lanes x 8)
+constexpr int kBfRowTask = 256;        // BF16 ROW task: rows per task
 constexpr double kGrid = 1024.0;       // apply operands and frames live on a 2^-10 grid
 
 enum TaskKind : int32_t {
