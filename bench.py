@@ -602,7 +602,7 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    cpu = None if args.no_cpu else cpu_baseline(p)
+    cpu = None if (args.no_cpu or world > 1) else cpu_baseline(p)  # the host baseline: N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
