@@ -71,10 +71,16 @@ KERNEL_SOURCES = {"apply_dense_kernel": "apply_f32.cu", "apply_dense_tma_kernel"
 
 
 def kernel_hash(kernel: str = "apply_dense_kernel") -> str:
+    """Hash of the code a kernel is built from (its source, ptx.cuh and internal.h),
+    with line comments and blank lines dropped: editing a comment keeps a profile
+    valid, editing code does not."""
     h = hashlib.sha256()
     for f in (KERNEL_SOURCES[kernel], "ptx.cuh", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2406_10849_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2406_10849_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -116,6 +116,11 @@ typedef struct tree_ot_problem {
  * node's apply streams contiguous rows like the row node's (the same bytes per
  * apply; twice the memory).  This bit keeps only the given layout. */
 #define TREE_OT_OPT_NO_TRANSPOSE 8u
+/* Test hook for the staged kernel's failure path: its producer issues no
+ * copies, so every consumer's bounded wait runs out (about a second); the
+ * kernel returns normally and tree_ot_solve reports TREE_OT_ERR_TIMEOUT.
+ * Implies TREE_OT_OPT_DENSE_TMA.  No GPU fault is involved. */
+#define TREE_OT_OPT_TEST_STALL   16u
 
 #define TREE_OT_TOL_SUM          0  /* the paper's stopping sum (Bipartite Iterative Scaling) */
 #define TREE_OT_TOL_MAX          1  /* the largest single term of that sum                 */

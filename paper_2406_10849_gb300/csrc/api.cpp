@@ -361,6 +361,7 @@ ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   a.bl = h->d_bl;
   a.arho = h->d_arho;
   a.err = h->d_err;
+  a.test_stall = (h->opt.flags & TREE_OT_OPT_TEST_STALL) ? 1 : 0;
   return a;
 }
 
@@ -1336,7 +1337,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   if (o.autotune && !h->fp64 && (rc = autotune_recompute(h, s))) return bail(rc);
   if (!h->fp64) {
     if ((rc = upload_stream_tasks(h, s))) return bail(rc);
-    if (o.flags & TREE_OT_OPT_DENSE_TMA) {
+    if (o.flags & (TREE_OT_OPT_DENSE_TMA | TREE_OT_OPT_TEST_STALL)) {
       if (!apply_tma_available()) return bail(fail(TREE_OT_ERR_CUDA, "staged edge apply unavailable"));
       h->dense_tma = 1;
     } else if (!(o.flags & TREE_OT_OPT_DENSE_LDG) && o.autotune && (rc = autotune_dense(h, s))) {

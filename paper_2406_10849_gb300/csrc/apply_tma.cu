@@ -8,9 +8,13 @@
 //   * the reduction-side operand (hh, hl) and the outputs' frame sources (m)
 //     into one of two per-task buffers.
 // The consumer warps (kGroups groups of eight) compute from shared memory only,
-// so no consumer ever stalls on a global load; group g takes the task's stages
-// s = g (mod kGroups).  The producer keeps up to kStages stages plus the next task's
-// vectors in flight (about 170 KB per SM).  Task records are resolved on the
+// so no consumer ever stalls on a global load; group g takes the stages whose
+// running index (over all of the CTA's tasks) is g (mod kGroups).  kStages is a
+// multiple of kGroups, so every ring slot is always read by the same group and a
+// group waits on each of its slots' phases in order: a parity wait is never more
+// than one phase ahead of its barrier (one phase ahead would read as already
+// complete).  The producer keeps up to kStages stages plus the next task's
+// vectors in flight (about 200 KB per SM).  Task records are resolved on the
 // host (StreamTask): one load per task, no pointer chasing.
 //
 //   ROW task (<= 64 rows x 1024 columns): one stage = 8 rows; consumer warp w
@@ -19,8 +23,8 @@
 //     warp w of the group takes rows 8w..8w+7 of its stages for its lane's 4
 //     columns and keeps running frames; the warps merge at the task's end.
 //
-// Every mbarrier wait is bounded (kSpinLimit polls with back-off).  A wait that
-// runs out sets bit 1 of the error word (reported as TREE_OT_ERR_TIMEOUT) and
+// Every mbarrier wait is bounded (kWaitLimitNs of wall time, with back-off).  A
+// wait that runs out sets bit 1 of the error word (TREE_OT_ERR_TIMEOUT) and
 // the ring's abort flag; from then on the producer issues no copies and every
 // consumer warp skips its work but still arrives on every barrier and reaches
 // every named barrier of the CTA, so nothing waits forever.  Before exiting,
@@ -36,7 +40,7 @@ namespace treeot {
 namespace {
 
 #define kInf (__int_as_float(0x7f800000))
-constexpr int kStages = 5;
+constexpr int kStages = 6;
 constexpr int kStageBytes = 32 * 1024;
 constexpr int kGroupWarps = 8;  // consumer warps per group (one per stage row block)
 // Consumer groups take turns on stages.  The register file is split between the
@@ -45,9 +49,11 @@ constexpr int kGroupWarps = 8;  // consumer warps per group (one per stage row b
 // most 102 registers per thread, which the shared-memory-resident rows allow.
 constexpr int kGroups = 2;
 constexpr int kConsumers = kGroupWarps * kGroups;  // consumer warps
+static_assert(kStages % kGroups == 0, "each ring slot must belong to one consumer group");
 constexpr int kTmaThreads = (kConsumers + 1) * 32;
 constexpr float kWindowT = 12.f;
-constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr uint64_t kWaitLimitNs = 250ull * 1000 * 1000;  // a wait gives up after 250 ms
+constexpr uint32_t kWaitPolls = 1u << 24;                 // or after this many polls
 // per-task buffer: hh[1024], hl[1024], frames[128] (floats)
 constexpr int kVecFloats = kRowCols;
 constexpr int kFrameMax = kColCols;  // >= 8 * kRowRowsPerWarp
@@ -83,11 +89,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false when the limit ran out
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait: kWaitLimitNs of wall time (checked every 64 polls) and, as a
+// backstop, kWaitPolls polls; false when either ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+  uint64_t start = 0;
+  for (uint32_t i = 0; i < kWaitPolls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (i > 64) __nanosleep(64);
+    if ((i & 63) == 63) {
+      const uint64_t now = global_ns();
+      if (start == 0) start = now;
+      else if (now - start > kWaitLimitNs) return false;
+      __nanosleep(256);
+    }
   }
   return false;
 }
@@ -140,6 +159,7 @@ __device__ void producer(const ApplyArgs& A, char* stages, char* tbufs, Ring* ri
   const int lane = threadIdx.x & 31;
   uint32_t it = 0;  // stages issued
   uint32_t tc = 0;  // task buffers issued
+  if (A.test_stall) return;  // test hook: nothing arrives, every consumer wait runs out
   bool alive = true;
   for (int ti = blockIdx.x; ti < A.ntasks && alive; ti += gridDim.x) {
     const StreamTask t = A.stasks[ti];
@@ -297,7 +317,7 @@ __device__ void consumers(const ApplyArgs& A, char* stages, char* tbufs, Ring* r
     const int ns = task_stages(t);
     if (t.kind == TASK_ROW) {
       for (int s = 0; s < ns; ++s, ++it) {
-        if ((s % kGroups) != grp) continue;  // the other group's stage
+        if ((it % kGroups) != grp) continue;  // the other group's stage (and slot)
         const int slot = it % kStages;
         const bool ok = ready(&ring->full[slot], (it / kStages) & 1) && vec_ok;
         const int r = 8 * s + gw;
@@ -322,7 +342,7 @@ __device__ void consumers(const ApplyArgs& A, char* stages, char* tbufs, Ring* r
         acc[k] = 0.f;
       }
       for (int s = 0; s < ns; ++s, ++it) {
-        if ((s % kGroups) != grp) continue;
+        if ((it % kGroups) != grp) continue;
         const int slot = it % kStages;
         if (!(ready(&ring->full[slot], (it / kStages) & 1) && vec_ok)) {
           __syncwarp();

@@ -135,6 +135,7 @@ struct ApplyArgs {
   const float* arho;         // row normalisers of the absorbed kernels (row side of each edge)
   int32_t* err;              // error word: bit 1 = a bounded wait of a staged kernel ran out
   const StreamTask* stasks;  // staged kernel: resolved stored-cost tasks (ntasks of them)
+  int32_t test_stall;        // staged kernel: the producer issues nothing (tests the timeout path)
 };
 
 struct AbsorbArgs {

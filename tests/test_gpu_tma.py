@@ -91,3 +91,24 @@ def test_kernels_agree_on_a_batch(T):
         assert rel_err(out["tma"][i], out["ldg"][i], p.eps) <= 2e-5
         ref = O.run_half_steps(p, 6)
         assert marginal_gap(p, out["tma"][i], ref) <= 1e-6
+
+
+def test_staged_kernel_timeout_is_reported(T):
+    """Failure path of the staged kernel, without a GPU fault: with the test hook
+    its producer issues nothing, every consumer's bounded wait runs out (250 ms),
+    the kernel returns, and the solve reports TREE_OT_ERR_TIMEOUT; the device
+    stays usable for the next handle."""
+    import time
+    p = DENSE_CASES["chain_dense_n70"]()
+    opts = T.options(precision="fp32", test_stall=True, use_graph=False, check_every=2, max_half_steps=2)
+    with T.Solver([p], opts) as s:
+        t0 = time.perf_counter()
+        with pytest.raises(T.TreeOTError) as ei:
+            s.solve()
+        dt = time.perf_counter() - t0
+    assert ei.value.code == -10, ei.value     # TREE_OT_ERR_TIMEOUT
+    assert dt < 30.0
+    with T.Solver([p], T.options(precision="fp32", dense_kernel="tma")) as s:
+        s.half_steps(1)
+        ref = O.run_half_steps(p, 1)
+        assert rel_err(s.potentials(0), ref, p.eps) <= 1e-4
