@@ -172,7 +172,7 @@ struct NodeArgs {
   int32_t* done;
   int64_t* done_at;
   double* f;
-  double* m;                 // raw merged message (before subtracting Z of the neighbour)
+  double* m;                 // merged message minus the neighbour's normaliser (node update scratch)
   float* fr;                 // frame of m for the next apply (log2, 2^-10 grid)
   float* hh;
   float* hl;

@@ -25,23 +25,75 @@
 namespace treeot {
 namespace {
 
-// merge the apply's (frame, sum) pieces of one output; empty pieces (sum 0) carry no frame
-__device__ __forceinline__ double merge32(const float2* part, int nsplit, int64_t stride) {
+// Two paths.  FP64 handles merge FP64 partials and work in double throughout.
+// FP32 handles keep the potentials and messages in double (their magnitudes
+// reach hundreds, their accuracy must not) but do everything that needs only
+// FP32 accuracy in FP32: the merge, the frames, the operand split and the
+// stopping terms.  GB300 executes FP64 arithmetic and float <-> double
+// conversions at a small fraction of its FP32 rate, so the FP32 path counts
+// every FP64-pipe instruction (about 15 per output and edge).
+
+constexpr float kLn2f = 0.693147180559945309f;
+constexpr float kLog2ef = 1.442695040888963407f;
+
+__device__ __forceinline__ float quant(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
+
+// merge the apply's (frame, sum) pieces of one output (FP32 partials); empty
+// pieces (sum 0) carry no frame.  The message is returned as a pair:
+//   m = t ln2 + l,   t = R + e (largest frame plus the sum's binary exponent),
+//   l = ln of the sum's mantissa plus the rounding error of t, |l| < 1.
+// t is exact when the frames lie on the 2^-10 grid (every FP32 kernel's do).
+struct Msg32 {
+  float t, l;
+};
+
+__device__ __forceinline__ Msg32 merge32(const float2* part, int nsplit, int64_t stride) {
   float Rm = -INFINITY;
   for (int p = 0; p < nsplit; ++p) {
     const float2 v = part[p * stride];
     if (v.y > 0.f) Rm = fmaxf(Rm, v.x);
   }
-  if (Rm == -INFINITY) return -INFINITY;
+  if (Rm == -INFINITY) return Msg32{-INFINITY, 0.f};
   float S = 0.f;
   for (int p = 0; p < nsplit; ++p) {
     const float2 v = part[p * stride];
     if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
   }
-  if (!isfinite(S) || !(S > 0.f)) return (S > 0.f) ? INFINITY : -INFINITY;
+  if (!isfinite(S) || !(S > 0.f)) return Msg32{(S > 0.f) ? INFINITY : -INFINITY, 0.f};
   int e;
   const float mant = frexpf(S, &e);  // S = mant * 2^e, mant in [0.5, 1)
-  return ((double)Rm + (double)e) * kLn2 + (double)logf(mant);
+  const float ef = (float)e;
+  const float t = Rm + ef;  // TwoSum: err is what t lost
+  const float bb = t - Rm;
+  const float err = (Rm - (t - bb)) + (ef - bb);
+  return Msg32{t, fmaf(err, kLn2f, logf(mant))};
+}
+
+// the message minus the neighbour's normaliser, in double
+__device__ __forceinline__ double msg_minus(const Msg32& mm, double Z) {
+  return fma((double)mm.t, kLn2, (double)mm.l - Z);
+}
+
+// frame of a message for the next apply: log2 of it on the 2^-10 grid (0 when not finite)
+__device__ __forceinline__ float frame32(const Msg32& mm) {
+  return isfinite(mm.t) ? quant(fmaf(mm.l, kLog2ef, mm.t)) : 0.f;
+}
+
+__device__ __forceinline__ float frame64(double m) {
+  return isfinite(m) ? (float)(rint(m * (kLog2e * kGrid)) * (1.0 / kGrid)) : 0.f;
+}
+
+// two-float split of an apply operand v (log2 units): hi on the 2^-10 grid, lo
+// the (small) rest.  hi comes from v rounded to FP32: any grid point within
+// 2^-10 of v will do.
+__device__ __forceinline__ void split2(double v, float& hi, float& lo) {
+  if (!isfinite(v)) {
+    hi = (float)v;
+    lo = 0.f;
+    return;
+  }
+  hi = quant((float)v);
+  lo = (float)(v - (double)hi);
 }
 
 __device__ __forceinline__ double merge64(const double2* part, int nsplit, int64_t stride) {
@@ -56,23 +108,8 @@ __device__ __forceinline__ double merge64(const double2* part, int nsplit, int64
   return M + log(S);
 }
 
-// exp of a double argument, evaluated at the precision of the path
-template <bool F64>
-__device__ __forceinline__ double expx(double a) {
-  if (F64) return exp(a);
-  return (double)ex2((float)(a * kLog2e));
-}
-
-// two-float split of an apply operand: hi on the 2^-10 grid, lo the (small) rest
-__device__ __forceinline__ void split2(double v, float& hi, float& lo) {
-  if (!isfinite(v)) {
-    hi = (float)v;
-    lo = 0.f;
-    return;
-  }
-  hi = (float)(rint(v * kGrid) / kGrid);
-  lo = (float)(v - (double)hi);
-}
+// exp at FP32 accuracy (the argument scaled to log2 units in double, then rounded once)
+__device__ __forceinline__ float exp32(double a) { return ex2((float)(a * kLog2e)); }
 
 // block-wide sum / max of a double (kNodeThreads threads); result valid in all threads
 __device__ double block_sum(double v, double* red) {
@@ -99,15 +136,23 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-// frame of a message for the next apply: log2 of it on the 2^-10 grid (0 when not finite)
-__device__ __forceinline__ float frame_grid(double m) {
-  return isfinite(m) ? (float)(rint(m * (kLog2e * kGrid)) * (1.0 / kGrid)) : 0.f;
-}
-
+// The merged message minus the neighbour's normaliser, m_(j,k)(x) - Z_k, is
+// stored in A.m (only this kernel reads it back, in the same thread); its
+// frame goes to A.fr.
 template <bool F64>
-__device__ __forceinline__ double merged(const NodeArgs& A, const DEdgeD& d, int n_owner, int x) {
-  if (F64) return merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
-  return merge32(A.part32 + d.part_off + x, d.nsplit, n_owner);
+__device__ __forceinline__ double merge_store(const NodeArgs& A, const DEdgeD& d, int n_owner, int x, double Zk) {
+  double mi;
+  if constexpr (F64) {
+    const double mr = merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
+    A.fr[d.off + x] = frame64(mr);
+    mi = mr - Zk;
+  } else {
+    const Msg32 mm = merge32(A.part32 + d.part_off + x, d.nsplit, n_owner);
+    A.fr[d.off + x] = frame32(mm);
+    mi = msg_minus(mm, Zk);
+  }
+  A.m[d.off + x] = mi;
+  return mi;
 }
 
 template <bool F64>
@@ -115,23 +160,25 @@ __device__ void fixed_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk&
   const DEdgeD d = A.dedges[A.node_dedges[nd.dedge_begin]];
   const double Zn = A.Z[d.nbr];
   double r = 0.0;
+  float r32 = 0.f;
   bool bad = false;
   // low-precision phase: flag the edge when the operand leaves its absorbed base
   const bool track = A.absorbed && A.lowp[nd.prob] == 1;
   bool drift = false;
   for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
     const int x = c.x0 + xi;
-    const double mr = merged<F64>(A, d, nd.n, x);
-    A.m[d.off + x] = mr;
-    A.fr[d.off + x] = frame_grid(mr);
-    const double mi = mr - Zn;
+    const double mi = merge_store<F64>(A, d, nd.n, x, Zn);
     const double fo = A.f[d.off + x];
     const double lg = A.logg[nd.node_off + x];
     const double mu = A.mu[nd.node_off + x];
-    const double q = (mu > 0.0) ? mu * expx<F64>(fo * P.inv_eps + mi) : 0.0;
-    r += fabs(q - mu);
-    const double fn = -P.eps * mi;
-    A.f[d.off + x] = fn;
+    // stopping term mu |exp(f/eps + m) - 1| of the previous iterate
+    if (mu > 0.0) {
+      if constexpr (F64)
+        r += fabs(mu * exp(fo * P.inv_eps + mi) - mu);
+      else
+        r32 += (float)mu * fabsf(exp32(fma(fo, P.inv_eps, mi)) - 1.f);
+    }
+    A.f[d.off + x] = -P.eps * mi;
     float hi, lo;
     if (lg == -INFINITY) {
       hi = -INFINITY;
@@ -146,10 +193,14 @@ __device__ void fixed_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk&
   }
   if (bad) atomicOr(A.err, 1);
   if (__syncthreads_or(drift) && threadIdx.x == 0) atomicOr(&A.drift[d.edge], 1);
-  r = block_sum(r, red);
+  r = block_sum(r + (double)r32, red);
   if (threadIdx.x == 0) atomicAdd(&A.resid_acc[A.node_dedges[nd.dedge_begin]], r);
 }
 
+// q_k(x) = exp(f_(j,k)/eps + m_(j,k) - Z_j) of the previous iterate.  The FP32
+// path forms it once, in the first pass over the edges, and parks it in the
+// edge's hh slot (overwritten by the new operand in the second pass, by the
+// same thread).
 template <bool F64>
 __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
                            double* s_s, double* s_q, int node_id) {
@@ -157,44 +208,62 @@ __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& 
   const double Zold = A.Z[node_id];
   const bool track = A.absorbed && A.lowp[nd.prob] == 1;
   const double inv_deg = 1.0 / (double)deg;
+  const float inv_deg32 = 1.f / (float)deg;
+  float* s_q32 = reinterpret_cast<float*>(s_q);
   bool bad = false;
   double smax = -INFINITY;
   for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
     const int x = c.x0 + xi;
     double ssum = 0.0, qsum = 0.0;
+    float qsum32 = 0.f;
     for (int i = 0; i < deg; ++i) {
       const DEdgeD d = A.dedges[A.node_dedges[nd.dedge_begin + i]];
-      const double mr = merged<F64>(A, d, nd.n, x);
-      A.m[d.off + x] = mr;
-      A.fr[d.off + x] = frame_grid(mr);
-      const double mi = mr - A.Z[d.nbr];
+      const double mi = merge_store<F64>(A, d, nd.n, x, A.Z[d.nbr]);
       const double fo = A.f[d.off + x];
-      qsum += expx<F64>((fo * P.inv_eps - Zold) + mi);
+      if constexpr (F64) {
+        qsum += exp((fo * P.inv_eps - Zold) + mi);
+      } else {
+        const float q = exp32(fma(fo, P.inv_eps, mi - Zold));
+        A.hh[d.off + x] = q;
+        qsum32 += q;
+      }
       ssum += mi;
     }
     const double s = ssum * inv_deg;
     if (!isfinite(s)) bad = true;
     s_s[xi] = s;
-    s_q[xi] = qsum * inv_deg;
+    if constexpr (F64)
+      s_q[xi] = qsum * inv_deg;
+    else
+      s_q32[xi] = qsum32 * inv_deg32;
     smax = fmax(smax, s);
   }
   smax = block_max(smax, red);
   double se = 0.0;
-  for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) se += expx<F64>(s_s[xi] - smax);
-  se = block_sum(se, red);
+  float se32 = 0.f;
+  for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
+    if constexpr (F64)
+      se += exp(s_s[xi] - smax);
+    else
+      se32 += exp32(s_s[xi] - smax);
+  }
+  se = block_sum(se + (double)se32, red);
   if (threadIdx.x == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2(smax, se);
   for (int i = 0; i < deg; ++i) {
     const int di = A.node_dedges[nd.dedge_begin + i];
     const DEdgeD d = A.dedges[di];
-    const double Zk = A.Z[d.nbr];
     double r = 0.0;
+    float r32 = 0.f;
     bool drift = false;
     for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
       const int x = c.x0 + xi;
-      const double mi = A.m[d.off + x] - Zk;
-      const double fo = A.f[d.off + x];
-      const double q = expx<F64>((fo * P.inv_eps - Zold) + mi);
-      r += fabs(q - s_q[xi]);
+      const double mi = A.m[d.off + x];
+      if constexpr (F64) {
+        const double fo = A.f[d.off + x];
+        r += fabs(exp((fo * P.inv_eps - Zold) + mi) - s_q[xi]);
+      } else {
+        r32 += fabsf(A.hh[d.off + x] - s_q32[xi]);
+      }
       const double g = s_s[xi] - mi;  // f'/eps
       A.f[d.off + x] = P.eps * g;
       float hi, lo;
@@ -204,7 +273,7 @@ __device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& 
       if (track && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) drift = true;
     }
     if (__syncthreads_or(drift) && threadIdx.x == 0) atomicOr(&A.drift[d.edge], 1);
-    r = block_sum(r, red);
+    r = block_sum(r + (double)r32, red);
     if (threadIdx.x == 0) atomicAdd(&A.resid_acc[di], r);
   }
   if (bad) atomicOr(A.err, 1);

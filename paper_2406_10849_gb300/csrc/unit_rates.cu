@@ -1,6 +1,8 @@
 // Unit-rate microbenchmark for the roofline denominators of the recomputed-cost
 // apply: FP32 FMA lanes per clock and SM (scalar and packed f32x2), MUFU ex2 per
-// clock and SM, and the relative error of ex2.approx.ftz.f32 against FP64 exp2.
+// clock and SM, and the relative error of ex2.approx.ftz.f32 against FP64 exp2;
+// for the node update, FP64 FMA lanes and float <-> double conversion pairs per
+// clock and SM.
 // A standalone program (not part of the library); bench.py --unit-rates builds
 // and runs it.  Prints one JSON object.
 #include <cmath>
@@ -63,6 +65,37 @@ __global__ void k_ex2(float* out, int iters, float b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// 8 independent FP64 FMA chains per thread
+__global__ void k_dfma(float* out, int iters, float b) {
+  double a[8];
+  const double bd = b;
+  for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], bd, 0.5);
+  }
+  double s = 0.0;
+  for (int i = 0; i < 8; ++i) s += a[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+}
+
+// 8 independent chains per thread of a float -> double -> float conversion pair
+__global__ void k_cvt(float* out, int iters, float b) {
+  float a[8];
+  for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3f + i + b;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      double d;
+      asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(a[i]));
+      asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(a[i]) : "d"(d));
+    }
+  }
+  float s = 0.f;
+  for (int i = 0; i < 8; ++i) s += a[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // relative error of ex2.approx over t in [-24, 1): sum, sum of squares, max |.|
 __global__ void k_ex2_err(double* stats, long n) {
   double s = 0.0, s2 = 0.0, mx = 0.0;
@@ -92,19 +125,22 @@ int main() {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  double rate[3] = {0, 0, 0};
-  for (int k = 0; k < 3; ++k) {
+  double rate[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 5; ++k) {
+    const int kiters = k >= 3 ? iters / 16 : iters;  // FP64 work is much slower
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
       cudaEventRecord(e0);
       if (k == 0) k_ffma<<<blocks, threads>>>(out, iters, 0.999f);
       if (k == 1) k_ffma2<<<blocks, threads>>>(out, iters, 0.999f);
       if (k == 2) k_ex2<<<blocks, threads>>>(out, iters, 0.999f);
+      if (k == 3) k_dfma<<<blocks, threads>>>(out, kiters, 0.999f);
+      if (k == 4) k_cvt<<<blocks, threads>>>(out, kiters, 0.999f);
       cudaEventRecord(e1);
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&ms, e0, e1);
     }
-    const double lanes = (double)blocks * threads * iters * 8 * (k == 1 ? 2 : 1);
+    const double lanes = (double)blocks * threads * kiters * 8 * (k == 1 ? 2 : 1);
     rate[k] = lanes / (ms * 1e-3);  // lane operations per second
   }
   const long n = 1L << 26;
@@ -117,9 +153,11 @@ int main() {
   const cudaError_t err = cudaGetLastError();
   const double ghz = clk_khz * 1e-6;
   printf("{\"sms\": %d, \"max_clock_ghz\": %.3f, \"ffma_lanes_per_clk_sm\": %.2f, \"ffma2_lanes_per_clk_sm\": %.2f, "
-         "\"ex2_per_clk_sm\": %.2f, \"ex2_rel_err\": {\"mean\": %.3e, \"rms\": %.3e, \"max\": %.3e}, "
+         "\"ex2_per_clk_sm\": %.2f, \"dfma_lanes_per_clk_sm\": %.3f, \"cvt_f32_f64_pairs_per_clk_sm\": %.3f, "
+         "\"ex2_rel_err\": {\"mean\": %.3e, \"rms\": %.3e, \"max\": %.3e}, "
          "\"note\": \"per clock at the device's maximum SM clock\", \"status\": \"%s\"}\n",
          sms, ghz, rate[0] / (ghz * 1e9) / sms, rate[1] / (ghz * 1e9) / sms, rate[2] / (ghz * 1e9) / sms,
+         rate[3] / (ghz * 1e9) / sms, rate[4] / (ghz * 1e9) / sms,
          h[0] / n, sqrt(h[1] / n), h[2], cudaGetErrorString(err));
   cudaFree(st);
   cudaFree(out);
