@@ -22,6 +22,10 @@ using namespace treeot;
 
 namespace {
 
+// node update: the largest dynamic shared memory a CTA may take (a chunk needs
+// about 12 KB plus 70-90 bytes per edge of its node)
+constexpr uint32_t kNodeSmemMax = 200u * 1024;
+
 thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
@@ -174,6 +178,7 @@ struct tree_ot_handle {
   int32_t slot_begin[2][kApplySlots] = {};
   int32_t slot_count[2][kApplySlots] = {};
   std::vector<NodeChunk> chunks[2];
+  uint32_t node_smem[2] = {0, 0};  // node update: dynamic shared memory per CTA, per colour
   std::vector<Task> check_tasks;
   std::vector<Task> btasks[2];             // absorbed BF16 apply tasks per colour
   std::vector<Task> atasks;                // absorption blocks (dedge 2e, 64 rows)
@@ -212,8 +217,8 @@ struct tree_ot_handle {
   unsigned long long h_absorb_count = 0;
   float *d_bh = nullptr, *d_bl = nullptr, *d_arho = nullptr;
   int bf16_grid = 1;
-  float* d_fr = nullptr;                   // frames of d_m (FP32, log2 on the 2^-10 grid)
-  double *d_f = nullptr, *d_m = nullptr, *d_Z = nullptr, *d_rho = nullptr, *d_logg = nullptr, *d_mu = nullptr;
+  float* d_fr = nullptr;                   // frames of the messages (FP32, log2 on the 2^-10 grid)
+  double *d_f = nullptr, *d_Z = nullptr, *d_rho = nullptr, *d_logg = nullptr, *d_mu = nullptr;
   double *d_resid_acc = nullptr, *d_resid_dedge = nullptr, *d_res_sum = nullptr, *d_marg = nullptr;
   double *d_edge_tc = nullptr, *d_edge_mass = nullptr;
   float *d_hh = nullptr, *d_hl = nullptr, *d_ah = nullptr, *d_al = nullptr, *d_coords = nullptr;
@@ -343,7 +348,6 @@ ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   a.nodes = h->d_nodes;
   a.probs = h->d_probs;
   a.done = h->d_done;
-  a.m = h->d_m;
   a.fr = h->d_fr;
   a.hh = h->d_hh;
   a.hl = h->d_hl;
@@ -369,6 +373,7 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   NodeArgs a{};
   a.chunks = h->d_chunks[colour];
   a.nchunks = (int32_t)h->chunks[colour].size();
+  a.smem = h->node_smem[colour];
   a.colour = colour;
   a.nodes = h->d_nodes;
   a.dedges = h->d_dedges;
@@ -378,7 +383,6 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.done = h->d_done;
   a.done_at = h->d_done_at;
   a.f = h->d_f;
-  a.m = h->d_m;
   a.fr = h->d_fr;
   a.hh = h->d_hh;
   a.hl = h->d_hl;
@@ -499,7 +503,6 @@ int queue_half_steps(tree_ot_handle* h, int64_t T, bool retire, cudaStream_t s) 
 
 int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(h->d_f, 0, sizeof(double) * h->vec_len, s));
-  CUDA_TRY(cudaMemsetAsync(h->d_m, 0, sizeof(double) * h->vec_len, s));
   CUDA_TRY(cudaMemsetAsync(h->d_fr, 0, sizeof(float) * h->vec_len, s));
   CUDA_TRY(cudaMemsetAsync(h->d_Z, 0, sizeof(double) * h->nodes.size(), s));
   CUDA_TRY(cudaMemsetAsync(h->d_rho, 0, sizeof(double) * h->nodes.size(), s));
@@ -1047,7 +1050,10 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       node_off += align_up(nd.n, 32);
       nd.coord_off = have_coords ? coord_off : -1;
       if (have_coords) coord_off += align_up((int64_t)nd.n * pd.dim, 4);
-      nd.nchunks = (nd.n + kNodeChunk - 1) / kNodeChunk;
+      {
+        const int32_t cp = node_chunk_points(nd.n, nd.deg);
+        nd.nchunks = (nd.n + cp - 1) / cp;
+      }
       nd.chunk_base = chunk_base;
       chunk_base += nd.nchunks;
       pd.nodes_in_colour[nd.colour] += 1;
@@ -1144,12 +1150,17 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     }
     h->lowp = any;
   }
+  h->node_smem[0] = h->node_smem[1] = 0;
   for (size_t j = 0; j < h->nodes.size(); ++j) {
     const NodeD& nd = h->nodes[j];
+    const int32_t cp = node_chunk_points(nd.n, nd.deg);
     for (int32_t c = 0; c < nd.nchunks; ++c)
-      h->chunks[nd.colour].push_back(
-          NodeChunk{(int32_t)j, c, c * kNodeChunk, std::min(kNodeChunk, nd.n - c * kNodeChunk)});
+      h->chunks[nd.colour].push_back(NodeChunk{(int32_t)j, c, c * cp, std::min(cp, nd.n - c * cp)});
+    const uint32_t b = node_smem_layout(nd.deg, std::min(cp, nd.n), h->fp64).bytes;
+    h->node_smem[nd.colour] = std::max(h->node_smem[nd.colour], b);
   }
+  if (std::max(h->node_smem[0], h->node_smem[1]) > kNodeSmemMax)
+    return bail(fail(TREE_OT_ERR_ARG, "a node's degree is too high for the node update"));
   for (size_t e = 0; e < h->edges.size(); ++e) {
     const EdgeD& ed = h->edges[e];
     for (int32_t o0 = 0; o0 < ed.na; o0 += 64)
@@ -1168,7 +1179,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = h->alloc(&h->d_chunks[0], (int64_t)h->chunks[0].size())) ||
       (rc = h->alloc(&h->d_chunks[1], (int64_t)h->chunks[1].size())) ||
       (rc = h->alloc(&h->d_check_tasks, (int64_t)h->check_tasks.size())) || (rc = h->alloc(&h->d_f, h->vec_len)) ||
-      (rc = h->alloc(&h->d_m, h->vec_len)) || (rc = h->alloc(&h->d_fr, h->vec_len)) || (rc = h->alloc(&h->d_hh, h->vec_len)) ||
+      (rc = h->alloc(&h->d_fr, h->vec_len)) || (rc = h->alloc(&h->d_hh, h->vec_len)) ||
       (rc = h->alloc(&h->d_hl, h->vec_len)) || (rc = h->alloc(&h->d_ah, h->vec_len)) ||
       (rc = h->alloc(&h->d_al, h->vec_len)) || (rc = h->alloc(&h->d_marg, h->vec_len)) ||
       (rc = h->alloc(&h->d_Z, NN)) || (rc = h->alloc(&h->d_rho, NN)) || (rc = h->alloc(&h->d_logg, h->node_len)) ||

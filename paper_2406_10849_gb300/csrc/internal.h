@@ -26,7 +26,7 @@ constexpr int kColRows = 512;          // COL task: rows per task (8 warps x 64)
 constexpr int kRecOut = 1024;          // RECOMP task: outputs per task (256 threads x 4)
 constexpr int kRecRed = 512;           // RECOMP task: reduction points per task
 constexpr int kNodeThreads = 256;
-constexpr int kNodeChunk = 512;        // node update: support points per CTA
+constexpr int kNodePairs = 1024;       // node update: (owned edge, point) pairs per CTA
 constexpr int kBfCols = 256;           // BF16 COL task: columns per task (32 lanes x 8)
 constexpr int kBfRowTask = 256;        // BF16 ROW task: rows per task
 constexpr double kGrid = 1024.0;       // apply operands and frames live on a 2^-10 grid
@@ -73,6 +73,40 @@ struct NodeChunk {
   int32_t node, chunk, x0, cnt;
 };
 
+// Node update: points per CTA for a node of n points and degree deg, so that a
+// CTA holds at most kNodePairs (edge, point) pairs (a multiple of 32 points
+// when that is at least 32, and at least one point).
+inline int32_t node_chunk_points(int32_t n, int32_t deg) {
+  int32_t c = kNodePairs / (deg > 0 ? deg : 1);
+  if (c >= 32) c &= ~31;
+  if (c < 1) c = 1;
+  return c < n ? c : n;
+}
+
+// Node update: dynamic shared memory of one CTA (deg edges, cnt points), in
+// this order: edge records, neighbour normalisers, edge ids, drift flags,
+// per-edge stopping sums, per-pair messages and q, per-point s and mean q.
+// q and the sums are double for FP64 handles, float otherwise.
+struct NodeSmem {
+  uint32_t de, zn, di, dr, r, mi, q, s, qb, bytes;
+};
+__host__ __device__ inline uint32_t node_align16(uint32_t b) { return (b + 15u) & ~15u; }
+__host__ __device__ inline NodeSmem node_smem_layout(int32_t deg, int32_t cnt, bool f64) {
+  const uint32_t qs = f64 ? 8u : 4u, np = (uint32_t)deg * (uint32_t)cnt;
+  NodeSmem L;
+  L.de = 0;
+  L.zn = L.de + node_align16((uint32_t)deg * (uint32_t)sizeof(DEdgeD));
+  L.di = L.zn + node_align16((uint32_t)deg * 8u);
+  L.dr = L.di + node_align16((uint32_t)deg * 4u);
+  L.r = L.dr + node_align16((uint32_t)deg * 4u);
+  L.mi = L.r + node_align16((uint32_t)deg * qs);
+  L.q = L.mi + node_align16(np * 8u);
+  L.s = L.q + node_align16(np * qs);
+  L.qb = L.s + node_align16((uint32_t)cnt * 8u);
+  L.bytes = L.qb + node_align16((uint32_t)cnt * qs);
+  return L;
+}
+
 struct ProbD {
   double eps, inv_eps;
   double cost_scale;
@@ -114,8 +148,7 @@ struct ApplyArgs {
   const NodeD* nodes;
   const ProbD* probs;
   const int32_t* done;       // per problem: 1 = retired
-  const double* m;           // latest messages
-  const float* fr;           // their frames: log2 of the message on the 2^-10 grid (0 if not finite)
+  const float* fr;           // frames of the latest messages: log2 on the 2^-10 grid (0 if not finite)
   const float* hh;           // operand (f/eps + log gamma) * log2(e), high part
   const float* hl;           // low part
   const double* f;           // potentials (FP64 path)
@@ -163,6 +196,7 @@ struct AbsorbArgs {
 struct NodeArgs {
   const NodeChunk* chunks;   // CTAs of this launch: (node, chunk) pairs of the colour
   int32_t nchunks;
+  uint32_t smem;             // dynamic shared memory per CTA (the largest chunk of the colour)
   int32_t colour;
   const NodeD* nodes;
   const DEdgeD* dedges;
@@ -172,8 +206,7 @@ struct NodeArgs {
   int32_t* done;
   int64_t* done_at;
   double* f;
-  double* m;                 // merged message minus the neighbour's normaliser (node update scratch)
-  float* fr;                 // frame of m for the next apply (log2, 2^-10 grid)
+  float* fr;                 // frame of the merged message for the next apply (log2, 2^-10 grid)
   float* hh;
   float* hl;
   double* Z;                 // per node

@@ -1,13 +1,20 @@
 // Node update of one half-step (the block-update theorem thm:tree_dual_var, in log form),
 // fused with the stopping terms of the Bipartite Iterative Scaling algorithm.
 //
-// One CTA handles a chunk of up to kNodeChunk support points of one node j of
-// the active colour.  For each owned directed edge (j,k) it merges the apply
-// kernel's partial log-sum-exps into the message m_(j,k)(x) (subtracting the
-// neighbour's normaliser Z_k), then
+// One CTA handles a chunk of the support points of one node j of the active
+// colour, sized so that it holds at most kNodePairs (owned directed edge,
+// point) pairs; every pair's intermediate values stay in shared memory.  For
+// each owned directed edge (j,k) it merges the apply kernel's partial
+// log-sum-exps into the message m_(j,k)(x) (subtracting the neighbour's
+// normaliser Z_k), then
 //   fixed j:  f_(j,k) = -eps m_(j,k)                               (u = 1./(K u'))
 //   free  j:  s(x) = mean_k m_(j,k)(x);  f'_(j,k) = eps (s - m_(j,k));
 //             Z_j = LSE_x s(x);  rho_j = -|N(j)| Z_j              (f = f' - eps Z_j)
+// A free node takes three passes: over the pairs (merge, frames, the previous
+// iterate's q_k), over the points (s, mean q, the chunk's part of Z_j) and over
+// the pairs again (potentials, the next apply's operand, stopping terms); a
+// fixed leaf takes one.  Pairs are independent, so a CTA keeps many loads in
+// flight instead of walking each point's edges in turn.
 // Before overwriting, it evaluates the stopping terms of the iterate the
 // previous half-step produced (only this colour's terms are non-zero there):
 //   fixed j:  sum_x |q(x) - mu_j(x)|,        q = mu_j exp(f/eps + m)  (= B 1)
@@ -18,6 +25,7 @@
 // node of a problem records the stopping quantity and (when asked) retires the
 // problem, the last CTA of the launch advances the half-step counter.
 #include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -136,154 +144,201 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-// The merged message minus the neighbour's normaliser, m_(j,k)(x) - Z_k, is
-// stored in A.m (only this kernel reads it back, in the same thread); its
-// frame goes to A.fr.
+// merged message of pair (edge d, point x) minus Z_k; writes its frame
 template <bool F64>
-__device__ __forceinline__ double merge_store(const NodeArgs& A, const DEdgeD& d, int n_owner, int x, double Zk) {
-  double mi;
+__device__ __forceinline__ double merge_pair(const NodeArgs& A, const DEdgeD& d, int n_owner, int x, double Zk) {
   if constexpr (F64) {
     const double mr = merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
     A.fr[d.off + x] = frame64(mr);
-    mi = mr - Zk;
+    return mr - Zk;
   } else {
     const Msg32 mm = merge32(A.part32 + d.part_off + x, d.nsplit, n_owner);
     A.fr[d.off + x] = frame32(mm);
-    mi = msg_minus(mm, Zk);
+    return msg_minus(mm, Zk);
   }
-  A.m[d.off + x] = mi;
-  return mi;
 }
 
-template <bool F64>
-__device__ void fixed_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red) {
-  const DEdgeD d = A.dedges[A.node_dedges[nd.dedge_begin]];
-  const double Zn = A.Z[d.nbr];
-  double r = 0.0;
-  float r32 = 0.f;
-  bool bad = false;
-  // low-precision phase: flag the edge when the operand leaves its absorbed base
-  const bool track = A.absorbed && A.lowp[nd.prob] == 1;
-  bool drift = false;
-  for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
-    const int x = c.x0 + xi;
-    const double mi = merge_store<F64>(A, d, nd.n, x, Zn);
-    const double fo = A.f[d.off + x];
-    const double lg = A.logg[nd.node_off + x];
-    const double mu = A.mu[nd.node_off + x];
-    // stopping term mu |exp(f/eps + m) - 1| of the previous iterate
-    if (mu > 0.0) {
-      if constexpr (F64)
-        r += fabs(mu * exp(fo * P.inv_eps + mi) - mu);
-      else
-        r32 += (float)mu * fabsf(exp32(fma(fo, P.inv_eps, mi)) - 1.f);
-    }
-    A.f[d.off + x] = -P.eps * mi;
-    float hi, lo;
-    if (lg == -INFINITY) {
-      hi = -INFINITY;
-      lo = 0.f;
-    } else {
-      split2((lg - mi) * kLog2e, hi, lo);
-      if (!isfinite(mi)) bad = true;
-    }
-    A.hh[d.off + x] = hi;
-    A.hl[d.off + x] = lo;
-    if (track && hi > -INFINITY && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) drift = true;
-  }
-  if (bad) atomicOr(A.err, 1);
-  if (__syncthreads_or(drift) && threadIdx.x == 0) atomicOr(&A.drift[d.edge], 1);
-  r = block_sum(r + (double)r32, red);
-  if (threadIdx.x == 0) atomicAdd(&A.resid_acc[A.node_dedges[nd.dedge_begin]], r);
+template <typename Q>
+__device__ __forceinline__ Q warp_sum_q(Q v) {
+  if constexpr (sizeof(Q) == 8)
+    return warp_sum_d(v);
+  else
+    return warp_sum(v);
 }
 
-// q_k(x) = exp(f_(j,k)/eps + m_(j,k) - Z_j) of the previous iterate.  The FP32
-// path forms it once, in the first pass over the edges, and parks it in the
-// edge's hh slot (overwritten by the new operand in the second pass, by the
-// same thread).
+// walks the pairs q = tid, tid + T, ... of a chunk of cnt points: (edge i, point xi)
+struct PairWalk {
+  int i, xi, di, dx;
+  __device__ PairWalk(int cnt) {
+    i = (int)threadIdx.x / cnt;
+    xi = (int)threadIdx.x - i * cnt;
+    di = kNodeThreads / cnt;
+    dx = kNodeThreads - di * cnt;
+  }
+  __device__ void next(int cnt) {
+    i += di;
+    xi += dx;
+    if (xi >= cnt) {
+      xi -= cnt;
+      ++i;
+    }
+  }
+};
+
 template <bool F64>
-__device__ void free_chunk(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
-                           double* s_s, double* s_q, int node_id) {
-  const int deg = nd.deg;
-  const double Zold = A.Z[node_id];
+__device__ void chunk_update(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
+                             unsigned char* sm, int node_id) {
+  using Q = typename std::conditional<F64, double, float>::type;
+  const int deg = nd.deg, cnt = c.cnt, np = deg * cnt;
+  const NodeSmem L = node_smem_layout(deg, cnt, F64);
+  DEdgeD* s_de = reinterpret_cast<DEdgeD*>(sm + L.de);
+  double* s_zn = reinterpret_cast<double*>(sm + L.zn);
+  int* s_di = reinterpret_cast<int*>(sm + L.di);
+  int* s_dr = reinterpret_cast<int*>(sm + L.dr);
+  Q* s_r = reinterpret_cast<Q*>(sm + L.r);
+  double* s_mi = reinterpret_cast<double*>(sm + L.mi);
+  Q* s_q = reinterpret_cast<Q*>(sm + L.q);
+  double* s_s = reinterpret_cast<double*>(sm + L.s);
+  Q* s_qb = reinterpret_cast<Q*>(sm + L.qb);
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < deg; i += kNodeThreads) {
+    const int di = A.node_dedges[nd.dedge_begin + i];
+    const DEdgeD d = A.dedges[di];
+    s_de[i] = d;
+    s_zn[i] = A.Z[d.nbr];
+    s_di[i] = di;
+    s_dr[i] = 0;
+    s_r[i] = Q(0);
+  }
+  __syncthreads();
+  // low-precision phase: flag an edge when its operand leaves the absorbed base
   const bool track = A.absorbed && A.lowp[nd.prob] == 1;
-  const double inv_deg = 1.0 / (double)deg;
-  const float inv_deg32 = 1.f / (float)deg;
-  float* s_q32 = reinterpret_cast<float*>(s_q);
   bool bad = false;
-  double smax = -INFINITY;
-  for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
-    const int x = c.x0 + xi;
-    double ssum = 0.0, qsum = 0.0;
-    float qsum32 = 0.f;
-    for (int i = 0; i < deg; ++i) {
-      const DEdgeD d = A.dedges[A.node_dedges[nd.dedge_begin + i]];
-      const double mi = merge_store<F64>(A, d, nd.n, x, A.Z[d.nbr]);
+
+  if (nd.fixed) {  // a leaf: one edge, one pass
+    const DEdgeD& d = s_de[0];
+    Q r = Q(0);
+    bool drift = false;
+    for (int xi = tid; xi < cnt; xi += kNodeThreads) {
+      const int x = c.x0 + xi;
+      const double mi = merge_pair<F64>(A, d, nd.n, x, s_zn[0]);
       const double fo = A.f[d.off + x];
-      if constexpr (F64) {
-        qsum += exp((fo * P.inv_eps - Zold) + mi);
-      } else {
-        const float q = exp32(fma(fo, P.inv_eps, mi - Zold));
-        A.hh[d.off + x] = q;
-        qsum32 += q;
+      const double lg = A.logg[nd.node_off + x];
+      const double mu = A.mu[nd.node_off + x];
+      // stopping term mu |exp(f/eps + m) - 1| of the previous iterate
+      if (mu > 0.0) {
+        if constexpr (F64)
+          r += fabs(mu * exp(fo * P.inv_eps + mi) - mu);
+        else
+          r += (float)mu * fabsf(exp32(fma(fo, P.inv_eps, mi)) - 1.f);
       }
-      ssum += mi;
+      A.f[d.off + x] = -P.eps * mi;
+      float hi, lo;
+      if (lg == -INFINITY) {
+        hi = -INFINITY;
+        lo = 0.f;
+      } else {
+        split2((lg - mi) * kLog2e, hi, lo);
+        if (!isfinite(mi)) bad = true;
+      }
+      A.hh[d.off + x] = hi;
+      A.hl[d.off + x] = lo;
+      if (track && hi > -INFINITY && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) drift = true;
+    }
+    if (__syncthreads_or(drift) && tid == 0) atomicOr(&A.drift[d.edge], 1);
+    const double rs = block_sum((double)r, red);
+    if (tid == 0) atomicAdd(&A.resid_acc[s_di[0]], rs);
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
+    return;
+  }
+
+  const double Zold = A.Z[node_id];
+  // pass 1, pairs: message - Z_k, its frame, and q_k(x) = exp(f_(j,k)/eps + m_(j,k) - Z_j)
+  {
+    PairWalk w(cnt);
+    for (int q = tid; q < np; q += kNodeThreads, w.next(cnt)) {
+      const DEdgeD& d = s_de[w.i];
+      const int x = c.x0 + w.xi;
+      const double mi = merge_pair<F64>(A, d, nd.n, x, s_zn[w.i]);
+      s_mi[q] = mi;
+      const double fo = A.f[d.off + x];
+      if constexpr (F64)
+        s_q[q] = exp((fo * P.inv_eps - Zold) + mi);
+      else
+        s_q[q] = exp32(fma(fo, P.inv_eps, mi - Zold));
+    }
+  }
+  __syncthreads();
+  // pass 2, points: s(x), mean q, and the chunk's (max, sum of exp) of s
+  const double inv_deg = 1.0 / (double)deg;
+  double smax = -INFINITY;
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) {
+    double ssum = 0.0;
+    Q qsum = Q(0);
+    for (int i = 0; i < deg; ++i) {
+      ssum += s_mi[i * cnt + xi];
+      qsum += s_q[i * cnt + xi];
     }
     const double s = ssum * inv_deg;
     if (!isfinite(s)) bad = true;
     s_s[xi] = s;
-    if constexpr (F64)
-      s_q[xi] = qsum * inv_deg;
-    else
-      s_q32[xi] = qsum32 * inv_deg32;
+    s_qb[xi] = qsum * (Q)inv_deg;
     smax = fmax(smax, s);
   }
-  smax = block_max(smax, red);
-  double se = 0.0;
-  float se32 = 0.f;
-  for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
+  smax = block_max(smax, red);  // its barriers also publish s_s and s_qb
+  Q se = Q(0);
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) {
     if constexpr (F64)
       se += exp(s_s[xi] - smax);
     else
-      se32 += exp32(s_s[xi] - smax);
+      se += exp32(s_s[xi] - smax);
   }
-  se = block_sum(se + (double)se32, red);
-  if (threadIdx.x == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2(smax, se);
-  for (int i = 0; i < deg; ++i) {
-    const int di = A.node_dedges[nd.dedge_begin + i];
-    const DEdgeD d = A.dedges[di];
-    double r = 0.0;
-    float r32 = 0.f;
-    bool drift = false;
-    for (int xi = threadIdx.x; xi < c.cnt; xi += kNodeThreads) {
-      const int x = c.x0 + xi;
-      const double mi = A.m[d.off + x];
-      if constexpr (F64) {
-        const double fo = A.f[d.off + x];
-        r += fabs(exp((fo * P.inv_eps - Zold) + mi) - s_q[xi]);
-      } else {
-        r32 += fabsf(A.hh[d.off + x] - s_q32[xi]);
+  const double sse = block_sum((double)se, red);
+  if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2(smax, sse);
+  // pass 3, pairs: f'_(j,k)/eps = s - m, the next apply's operand, |q_k - mean q|
+  {
+    PairWalk w(cnt);
+    for (int q0 = 0; q0 < np; q0 += kNodeThreads) {  // warp-uniform trip count
+      const int q = q0 + tid;
+      const bool on = q < np;
+      const int i = on ? w.i : -1;
+      Q r = Q(0);
+      if (on) {
+        const DEdgeD& d = s_de[i];
+        const int x = c.x0 + w.xi;
+        const double mi = s_mi[q];
+        r = s_q[q] > s_qb[w.xi] ? s_q[q] - s_qb[w.xi] : s_qb[w.xi] - s_q[q];
+        const double g = s_s[w.xi] - mi;
+        A.f[d.off + x] = P.eps * g;
+        float hi, lo;
+        split2(g * kLog2e, hi, lo);
+        A.hh[d.off + x] = hi;
+        A.hl[d.off + x] = lo;
+        if (track && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) s_dr[i] = 1;
+        w.next(cnt);
       }
-      const double g = s_s[xi] - mi;  // f'/eps
-      A.f[d.off + x] = P.eps * g;
-      float hi, lo;
-      split2(g * kLog2e, hi, lo);
-      A.hh[d.off + x] = hi;
-      A.hl[d.off + x] = lo;
-      if (track && fabsf((hi - A.bh[d.off + x]) + (lo - A.bl[d.off + x])) > A.tau) drift = true;
+      // per-edge sums: one shared-memory atomic per warp when the warp's pairs share an edge
+      const int i0 = __shfl_sync(0xffffffffu, i, 0);
+      if (__all_sync(0xffffffffu, i == i0)) {
+        r = warp_sum_q(r);
+        if (lane == 0 && i0 >= 0) atomicAdd(&s_r[i0], r);
+      } else if (on) {
+        atomicAdd(&s_r[i], r);
+      }
     }
-    if (__syncthreads_or(drift) && threadIdx.x == 0) atomicOr(&A.drift[d.edge], 1);
-    r = block_sum(r + (double)r32, red);
-    if (threadIdx.x == 0) atomicAdd(&A.resid_acc[di], r);
   }
-  if (bad) atomicOr(A.err, 1);
+  __syncthreads();
+  for (int i = tid; i < deg; i += kNodeThreads) {
+    atomicAdd(&A.resid_acc[s_di[i]], (double)s_r[i]);
+    if (s_dr[i]) atomicOr(&A.drift[s_de[i].edge], 1);
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
 }
 
 template <bool F64>
 __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
+  extern __shared__ __align__(16) unsigned char node_sm[];
   __shared__ double red[kNodeThreads / 32];
-  __shared__ double s_s[kNodeChunk];
-  __shared__ double s_q[kNodeChunk];
   const NodeChunk c = A.chunks[blockIdx.x];
   const NodeD nd = A.nodes[c.node];
   const int p = nd.prob;
@@ -291,12 +346,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
   const int64_t t_now = *((volatile const int64_t*)A.hs);
   const int slot = (int)(t_now % kResidRing);
   const bool skip = A.done[p] != 0;
-  if (!skip) {
-    if (nd.fixed)
-      fixed_chunk<F64>(A, nd, c, P, red);
-    else
-      free_chunk<F64>(A, nd, c, P, red, s_s, s_q, c.node);
-  }
+  if (!skip) chunk_update<F64>(A, nd, c, P, red, node_sm, c.node);
   __syncthreads();
   if (threadIdx.x != 0) return;
   __threadfence();
@@ -371,10 +421,20 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
 
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s) {
   if (a.nchunks <= 0) return cudaSuccess;
+  // more than the default 48 KB of dynamic shared memory only for nodes of very high degree
+  static uint32_t opted[2] = {48u * 1024, 48u * 1024};
+  if (a.smem > opted[fp64 ? 1 : 0]) {
+    const cudaError_t e =
+        fp64 ? cudaFuncSetAttribute(node_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem)
+             : cudaFuncSetAttribute(node_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)a.smem);
+    if (e != cudaSuccess) return e;
+    opted[fp64 ? 1 : 0] = a.smem;
+  }
   if (fp64)
-    node_update_kernel<true><<<a.nchunks, kNodeThreads, 0, s>>>(a);
+    node_update_kernel<true><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
   else
-    node_update_kernel<false><<<a.nchunks, kNodeThreads, 0, s>>>(a);
+    node_update_kernel<false><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
   return cudaGetLastError();
 }
 
