@@ -307,6 +307,42 @@ def test_edge_cases_small_supports_and_free_leaf(T):
     assert O.final_check(p, got)["max_marginal_l1"] <= 1e-6
 
 
+def high_degree_star(L, seed=29, eps=0.05):
+    """Star with L leaves (free centre) and small unequal supports."""
+    rng = np.random.default_rng(seed)
+    edges = np.array([[0, l] for l in range(1, L + 1)], np.int32)
+    n = np.concatenate([[37], rng.integers(1, 9, size=L)]).astype(np.int32)
+    fixed = np.ones(L + 1, bool)
+    fixed[0] = False
+    coords = [rng.random((int(n[j]), 2)).astype(np.float32) for j in range(L + 1)]
+    marg = {j: gen.dirichlet_marginal(int(n[j]), rng) for j in range(1, L + 1)}
+    return TreeProblem(name=f"star{L}", edges=edges, n=n, fixed=fixed, marginals=marg, eps=eps, coords=coords,
+                       cost_scale=1.0, cost_kind="sqeuclid")
+
+
+@pytest.mark.parametrize("precision,tol,mtol", [("fp32", 1e-4, 1e-5), ("fp64", 1e-11, 1e-9)])
+def test_high_degree_node_update(T, precision, tol, mtol):
+    """A 400-leaf star: the centre's chunks hold two points and 400 edges, so the
+    node update's warps mix edges (per-lane stopping-term sums)."""
+    p = high_degree_star(400)
+    ref = O.run_half_steps(p, 5)
+    with T.Solver([p], T.options(precision=precision)) as s:
+        s.half_steps(5)
+        got = s.potentials(0)
+        res = s.check()
+    assert rel_err(got, ref, p.eps) <= tol
+    ref_res = O.final_check(p, ref)
+    assert marginal_gap(p, got, ref) <= mtol
+    assert abs(res[0]["max_marginal_l1"] - ref_res["max_marginal_l1"]) <= mtol
+
+
+def test_degree_limit_is_reported(T):
+    """A node of degree 2700 does not fit the node update's shared memory."""
+    with pytest.raises(T.TreeOTError) as ei:
+        T.Solver([high_degree_star(2700)], T.options())
+    assert ei.value.kind == "ARG"
+
+
 def test_nan_cost_is_rejected(T):
     p = gen.chain_problem(seed=1004, n=16)
     p.dense_cost(0)
