@@ -351,13 +351,15 @@ def run_batched(args):
 
 
 def run_warmstart(args):
-    """Learned warm start on barycenter stars (8 fixed leaves on a side x side grid,
-    free centre, eps log-uniform in [0.0025, 0.01] for training): solve the
-    training stars from u = 1 on the GPU, train the MLP on their leaf potentials
-    with the library's own kernels, then solve the held-out stars (eps = 0.005)
-    from u = 1 and from the predicted leaf potentials, each to max marginal L1
-    <= 1e-6 in one batched handle.  The JSON line reports the warm-start wall
-    time (prediction included) with the zero-init time beside it."""
+    """Learned warm start and the shared-kernel BF16 phase on barycenter stars
+    (8 fixed leaves on a side x side grid, free centre, eps log-uniform in
+    [0.0025, 0.01] for training): solve the training stars from u = 1 on the
+    GPU, train the MLP on their leaf potentials with the library's own kernels,
+    then solve the held-out stars (eps = 0.005, one shared Gibbs kernel) to max
+    marginal L1 <= 1e-6 in one batched handle, four ways: plain FP32 from u = 1,
+    FP32 from the predicted potentials, and both again with the BF16 phase.
+    The JSON line's value is the BF16 + warm-start time (prediction included);
+    the plain FP32 time and the other two forms stand beside it."""
     import torch
 
     import gen
@@ -383,30 +385,54 @@ def run_warmstart(args):
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t1
     test = gen.warmstart_stars(9_000_000, args.test_trees, side=side, eps=0.005)
-    W.zero_solve(test[:4])[1].close()  # first-use costs (autotuner cache) outside the timed solves
-    tzd, twd = {}, {}
+    # first-use costs (autotuner cache, function attributes) outside the timed solves
+    W.zero_solve(test[:16])[1].close()
+    W.zero_solve(test[:16], apply_mode="bf16", lowp_start=0, refine_tol=args.refine_tol)[1].close()
+    tzd, twd, tzbd, twbd = {}, {}, {}, {}
     with ClockSampler(0) as clk:
         torch.cuda.synchronize(dev)
         rz, s, tz = W.zero_solve(test, timing=tzd)
         s.close()
         rw, fallbacks, tw = ws.warm_solve(test, timing=twd)
+        # the same, with the shared-kernel BF16 phase from the first half-step
+        bf = dict(apply_mode="bf16", lowp_start=0, refine_tol=args.refine_tol)
+        rzb, s, _ = W.zero_solve(test, timing=tzbd, **bf)
+        s.close()
+        rwb, fallbacks_b, _ = ws.warm_solve(test, timing=twbd, **bf)
     clocks = clk.summary()
     # the handle's creation (upload, planning) is the same for both starts: compare the rest
     tz_run = tzd["solve"]
     tw_run = twd["predict"] + twd["solve"] + twd["fallback"]
+    tzb_run = tzbd["solve"]
+    twb_run = twbd["predict"] + twbd["solve"] + twbd["fallback"]
     hz = np.array([r["half_steps"] for r in rz], dtype=np.float64)
     hw = np.array([r["half_steps"] for r in rw], dtype=np.float64)
+
+    def summary(res, seconds):
+        hs = np.array([r["half_steps"] for r in res], dtype=np.float64)
+        lp = np.array([r["lowp_half_steps"] for r in res], dtype=np.float64)
+        return {"seconds": seconds, "half_steps_mean": float(hs.mean()), "bf16_half_steps_mean": float(lp.mean()),
+                "converged": int(sum(r["status"] == 0 for r in res)),
+                "worst_max_marginal_l1": max(r["max_marginal_l1"] for r in res)}
+
     line = {
-        "metric": "time to max marginal L1 <= 1e-6, warm start vs u = 1", "value": tw_run, "unit": "s",
-        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": tw_run * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 solve, bf16 MLP", "data": "synthetic",
+        "metric": "time to max marginal L1 <= 1e-6: BF16 shared-kernel phase + warm start vs plain FP32 from u = 1",
+        "value": twb_run, "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": twb_run * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 tensor-core phase + f32 solve, bf16 MLP",
+        "data": "synthetic",
+        "plain_fp32_seconds": tz_run, "speedup_vs_plain": tz_run / twb_run,
+        "forms": {"plain_fp32_zero": summary(rz, tz_run), "fp32_warm": summary(rw, tw_run),
+                  "bf16_zero": summary(rzb, tzb_run), "bf16_warm": summary(rwb, twb_run),
+                  "bf16_warm_fallbacks": fallbacks_b},
         "config": {"workload": f"warmstart_star{side * side}_train{args.train_trees}_test{args.test_trees}",
                    "leaves": 8, "n": side * side, "train_eps": [0.0025, 0.01], "test_eps": 0.005,
                    "mlp": f"{side * side + 1}-512-512-{side * side} GELU, bf16 weights, fp32 master + Adam",
                    "epochs": args.epochs},
-        "zero_init_seconds": tz_run, "speedup": tz_run / tw_run,
-        "seconds_split": {"warm": twd, "zero": tzd, "note": "value = predict (inputs, network, set) + solve "
-                          "+ fallback; zero_init_seconds = solve; handle creation excluded from both"},
+        "warm_fp32_seconds": tw_run, "zero_init_seconds": tz_run, "speedup_warm_fp32": tz_run / tw_run,
+        "seconds_split": {"warm": twd, "zero": tzd, "bf16_warm": twbd, "bf16_zero": tzbd,
+                          "note": "warm forms: predict (inputs, network, set) + solve + fallback; zero forms: "
+                                  "solve; handle creation excluded from all"},
         "half_steps": {"zero_mean": float(hz.mean()), "warm_mean": float(hw.mean()),
                        "zero_median": float(np.median(hz)), "warm_median": float(np.median(hw)),
                        "zero_max": int(hz.max()), "warm_max": int(hw.max()),
@@ -453,6 +479,8 @@ def main():
     ap.add_argument("--test-trees", type=int, default=2000, help="warmstart: held-out stars")
     ap.add_argument("--side", type=int, default=32, help="warmstart: grid side (n = side^2)")
     ap.add_argument("--epochs", type=int, default=30, help="warmstart: training epochs")
+    ap.add_argument("--refine-tol", type=float, default=1.5e-6,
+                    help="warmstart: stopping quantity at which the BF16 forms hand over to FP32")
     ap.add_argument("--unit-rates", action="store_true",
                     help="only build and run the FP32 / MUFU unit-rate microbenchmark")
     ap.add_argument("--trees", type=int, default=512, help="batched workload: number of trees")

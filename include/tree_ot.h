@@ -96,8 +96,12 @@ typedef struct tree_ot_problem {
 
 #define TREE_OT_APPLY_AUTO       0
 #define TREE_OT_APPLY_LSE        1  /* log-sum-exp on C (stored or recomputed)             */
-#define TREE_OT_APPLY_BF16       2  /* stored costs: absorbed BF16 kernel, then FP32 LSE
-                                       refinement (see refine_tol, absorb_tau, lowp_start)  */
+#define TREE_OT_APPLY_BF16       2  /* BF16 phase, then FP32 LSE refinement (see refine_tol,
+                                       absorb_tau, lowp_start): stored costs use an absorbed
+                                       BF16 kernel per edge; squared-Euclidean problems whose
+                                       directed edges share supports, scale and eps (at least
+                                       8 per kernel) use one shared kernel on the tensor cores;
+                                       other problems run FP32 throughout                    */
 
 /* options.flags: which kernel streams stored costs (FP32 path).  With neither
  * bit the autotuner (autotune = 1) times both and keeps the faster; with
@@ -134,15 +138,23 @@ typedef struct tree_ot_options {
     int32_t check_every;      /* half-steps between convergence read-backs (even, >= 2)  */
     int32_t use_graph;        /* 1: replay each chunk of half-steps as a CUDA graph      */
     uint32_t flags;           /* TREE_OT_OPT_* bits, 0 by default                        */
-    /* APPLY_BF16 only (problems with stored costs):
-     * the first lowp_start half-steps use the FP32 kernel; then the potentials
-     * are absorbed into a BF16 copy of the Gibbs kernel,
+    /* APPLY_BF16 only.  The first lowp_start half-steps use the FP32 kernels.
+     * Stored costs: the potentials are then absorbed into a BF16 copy of the
+     * Gibbs kernel,
      *     Kt(x,y) = 2^(A(x) + B(y) - C(x,y) log2(e)/eps - rho(x))   (row max 1),
      * A, B the apply operands at absorption time, and each apply multiplies Kt
      * by 2^(h - base) on the reduction side (FP32 accumulation).  An edge whose
      * operand drifts more than absorb_tau (log2 units) from its base is
-     * re-absorbed on the device.  When a problem's stopping quantity falls below
-     * refine_tol it switches to the FP32 log-sum-exp kernel for good. */
+     * re-absorbed on the device.
+     * Shared squared-Euclidean kernels: each half-step, one colour's messages of
+     * a group are S = K' V' with K'(x,y) = 2^(b(y) - R(x) - s C(x,y)) and
+     * V'(y,j) = 2^(h_j(y) - b(y)), b the envelope of the columns' operands and
+     * R its row frame, both factors split into two BF16 parts and multiplied on
+     * the tensor cores with FP32 accumulation (three products); outputs whose
+     * sum falls below 2^-96 are recomputed exactly.
+     * A problem leaves the phase for the FP32 kernels for good when its stopping
+     * quantity falls below refine_tol, or when it has not fallen by 10 % for 128
+     * half-steps; refine_tol = 0 keeps it in the phase (the phase alone). */
     double refine_tol;        /* default 1e-5                                            */
     double absorb_tau;        /* default 48                                              */
     int32_t lowp_start;       /* default 16                                              */
@@ -162,7 +174,7 @@ typedef struct tree_ot_result {
     double dual;                /* -eps f(u,rho) of eq. tree_dual_mass_consv              */
     double transport_cost;      /* sum_e <C_e,B_e>                                       */
     double wall_ms;             /* host wall time of the solve call                      */
-    int64_t lowp_half_steps;    /* APPLY_BF16: half-steps spent in the absorbed BF16 phase */
+    int64_t lowp_half_steps;    /* APPLY_BF16: half-steps spent in the BF16 phase            */
     int64_t absorptions;        /* APPLY_BF16: edge absorptions performed (whole handle)  */
 } tree_ot_result;
 

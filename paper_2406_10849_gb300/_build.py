@@ -15,7 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtreeot.so")
-SOURCES = ["api.cpp", "mlp_api.cpp", "apply_f32.cu", "apply_bf16.cu", "apply_tma.cu", "apply_f64.cu", "node_update.cu",
+SOURCES = ["api.cpp", "mlp_api.cpp", "apply_f32.cu", "apply_bf16.cu", "apply_tma.cu", "apply_sk.cu", "apply_f64.cu",
+           "node_update.cu",
            "check.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",

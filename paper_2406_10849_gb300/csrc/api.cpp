@@ -11,12 +11,14 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
 
 #include "../../include/tree_ot.h"
 #include "internal.h"
+#include "sk.h"
 
 using namespace treeot;
 
@@ -182,7 +184,17 @@ struct tree_ot_handle {
   std::vector<Task> check_tasks;
   std::vector<Task> btasks[2];             // absorbed BF16 apply tasks per colour
   std::vector<Task> atasks;                // absorption blocks (dedge 2e, 64 rows)
-  bool lowp = false;                       // handle built for the absorbed BF16 phase
+  bool lowp = false;                       // handle built for a BF16 phase (absorbed or shared-kernel)
+  // shared-kernel BF16 phase (squared-Euclidean costs): groups of directed edges
+  // with one Gibbs kernel, their columns per colour, and the problems all of
+  // whose directed edges are grouped (only those enter the phase)
+  struct SkGroup {
+    std::vector<SkCol> cols[2];
+    int32_t owner_rep = 0, nbr_rep = 0, prob_rep = 0;  // representative nodes / problem
+    SkArgs args[2]{};
+  };
+  std::vector<SkGroup> sk;
+  std::vector<uint8_t> sk_prob;
   std::vector<int32_t> prob_node_base, prob_edge_base, prob_nodes;
   std::vector<std::vector<double>> mu;  // per global node (fixed nodes), host copy
   int64_t vec_len = 0, node_len = 0, part_len = 0, coord_len = 0;
@@ -211,7 +223,9 @@ struct tree_ot_handle {
   int64_t task_cap[2] = {0, 0};            // device capacity of d_tasks
   Task* d_atasks = nullptr;
   int32_t *d_lowp = nullptr, *d_drift = nullptr;
-  int64_t* d_lowp_span = nullptr;          // per problem: [begin, end) half-steps of the BF16 phase
+  int64_t* d_lowp_span = nullptr;          // per problem: [begin, end) half-steps of the BF16 phase (-1: none)
+  double* d_lowp_best = nullptr;           // per problem: the phase's stall detector (node update)
+  int64_t* d_lowp_best_t = nullptr;
   unsigned long long* d_absorb_count = nullptr;
   std::vector<int64_t> h_lowp_span;
   unsigned long long h_absorb_count = 0;
@@ -416,6 +430,8 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.tau = (float)h->opt.absorb_tau;
   a.lowp_start = h->opt.lowp_start;
   a.lowp_span = h->d_lowp_span;
+  a.lowp_best = h->d_lowp_best;
+  a.lowp_best_t = h->d_lowp_best_t;
   return a;
 }
 
@@ -481,6 +497,11 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
     cudaError_t e = launch_apply_bf16(a, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "absorbed apply launch");
   }
+  if (!only_stored)
+    for (const auto& g : h->sk) {
+      cudaError_t e = launch_sk(g.args[colour], s);
+      if (e != cudaSuccess) return cuda_fail(e, "shared-kernel apply launch");
+    }
   return TREE_OT_OK;
 }
 
@@ -542,19 +563,27 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, (int32_t)h->dedges.size(),
                           kLog2e, true, h->d_hh, h->d_hl, s));
   // phase of every problem: absorbed BF16 phase (1), waiting for it (2), or FP32 (0)
-  CUDA_TRY(cudaMemsetAsync(h->d_lowp_span, 0, sizeof(int64_t) * 2 * h->nprob, s));
   CUDA_TRY(cudaMemsetAsync(h->d_absorb_count, 0, sizeof(unsigned long long), s));
   {
     std::vector<int32_t> lp(h->nprob, 0);
     std::vector<int32_t> dr(h->edges.size(), 0);
+    std::vector<int64_t> span(2 * h->nprob, -1), best_t(h->nprob, 0);
+    std::vector<double> best(h->nprob, INFINITY);
     for (int p = 0; p < h->nprob; ++p) {
-      if (!h->lowp || h->probs[p].cost_kind != TREE_OT_COST_DENSE_F32) continue;
+      const bool sk = !h->sk_prob.empty() && h->sk_prob[p];
+      if (!h->lowp || (h->probs[p].cost_kind != TREE_OT_COST_DENSE_F32 && !sk)) continue;
       lp[p] = h->opt.lowp_start == 0 ? 1 : 2;
-      if (lp[p] == 1)
+      if (lp[p] == 1) {
+        span[2 * p] = 0;
         for (int k = 0; k < h->probs[p].edge_count; ++k) dr[h->probs[p].edge_begin + k] = 1;
+      }
     }
     CUDA_TRY(cudaMemcpyAsync(h->d_lowp, lp.data(), sizeof(int32_t) * lp.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(h->d_drift, dr.data(), sizeof(int32_t) * dr.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h->d_lowp_span, span.data(), sizeof(int64_t) * span.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h->d_lowp_best, best.data(), sizeof(double) * best.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(
+        cudaMemcpyAsync(h->d_lowp_best_t, best_t.data(), sizeof(int64_t) * best_t.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     RC_TRY(launch_absorb_step(h, s));
   }
@@ -723,9 +752,9 @@ void fill_results(tree_ot_handle* h, tree_ot_result* res) {
     r.half_steps = done ? h->h_done_at[p] : h->hs_host;
     r.status = (h->last_status.empty() ? TREE_OT_OK : h->last_status[p]);
     r.wall_ms = h->last_wall_ms;
-    if (!h->h_lowp_span.empty() && h->h_lowp_span[2 * p] > 0) {
-      const int64_t end = h->h_lowp_span[2 * p + 1] > 0 ? h->h_lowp_span[2 * p + 1] : r.half_steps;
-      r.lowp_half_steps = end - h->h_lowp_span[2 * p];
+    if (!h->h_lowp_span.empty() && h->h_lowp_span[2 * p] >= 0) {
+      const int64_t end = h->h_lowp_span[2 * p + 1] >= 0 ? h->h_lowp_span[2 * p + 1] : r.half_steps;
+      r.lowp_half_steps = std::max<int64_t>(0, end - h->h_lowp_span[2 * p]);
     }
     r.absorptions = (int64_t)h->h_absorb_count;
     res[p] = r;
@@ -895,6 +924,151 @@ int autotune_dense(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaStreamSynchronize(s));
   if (err & 2) return fail(TREE_OT_ERR_TIMEOUT, "a bounded wait in the staged edge apply ran out");
   h->dense_tma = ms[1] < ms[0] ? 1 : 0;
+  return TREE_OT_OK;
+}
+
+// Shared-kernel BF16 phase: group the directed edges of squared-Euclidean
+// problems by (owner support, neighbour support, cost scale, eps) — equal
+// supports compared by value — and keep the problems all of whose directed
+// edges found a group of at least kSkMinCols.  Columns are listed per colour
+// of the owner.
+constexpr int kSkMinCols = 8;
+
+int plan_shared_kernels(tree_ot_handle* h, const tree_ot_problem* probs, int32_t num_probs) {
+  h->sk.clear();
+  h->sk_prob.assign(num_probs, 0);
+  const size_t NN = h->nodes.size();
+  std::vector<std::vector<float>> pts(NN);
+  std::vector<uint64_t> hash(NN, 0);
+  for (int32_t p = 0; p < num_probs; ++p) {
+    const tree_ot_problem& P = probs[p];
+    const ProbD& pd = h->probs[p];
+    if (P.cost_kind != TREE_OT_COST_SQEUCLID || !P.coords || pd.dim <= 0) continue;
+    for (int32_t j = 0; j < P.num_nodes; ++j) {
+      const int32_t g = h->prob_node_base[p] + j;
+      const size_t cnt = (size_t)h->nodes[g].n * (size_t)pd.dim;
+      pts[g].resize(cnt);
+      if (P.flags & TREE_OT_INPUT_DEVICE) {
+        cudaError_t e = cudaMemcpy(pts[g].data(), P.coords[j], cnt * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(supports for grouping)");
+      } else {
+        std::memcpy(pts[g].data(), P.coords[j], cnt * sizeof(float));
+      }
+      uint64_t hv = 1469598103934665603ull;  // FNV-1a over 32-bit words
+      for (size_t i = 0; i < cnt; ++i) {
+        uint32_t w;
+        std::memcpy(&w, &pts[g][i], 4);
+        hv = (hv ^ w) * 1099511628211ull;
+      }
+      hash[g] = hv;
+    }
+  }
+  using Key = std::tuple<int32_t, int32_t, int32_t, uint64_t, uint64_t, uint64_t, uint64_t>;
+  std::map<Key, int> index;
+  std::vector<int> dgroup(h->dedges.size(), -1);
+  for (size_t di = 0; di < h->dedges.size(); ++di) {
+    const DEdgeD& d = h->dedges[di];
+    if (pts[d.owner].empty() || pts[d.nbr].empty()) continue;
+    const ProbD& pd = h->probs[d.prob];
+    uint64_t sb, eb;
+    std::memcpy(&sb, &pd.cost_scale, 8);
+    std::memcpy(&eb, &pd.eps, 8);
+    const Key key{h->nodes[d.owner].n, h->nodes[d.nbr].n, pd.dim, hash[d.owner], hash[d.nbr], sb, eb};
+    auto it = index.find(key);
+    int gi;
+    if (it == index.end()) {
+      gi = (int)h->sk.size();
+      index.emplace(key, gi);
+      h->sk.emplace_back();
+      h->sk[gi].owner_rep = d.owner;
+      h->sk[gi].nbr_rep = d.nbr;
+      h->sk[gi].prob_rep = d.prob;
+    } else {
+      gi = it->second;
+      const auto& G = h->sk[gi];
+      if (pts[d.owner] != pts[G.owner_rep] || pts[d.nbr] != pts[G.nbr_rep]) continue;  // equal hashes only
+    }
+    dgroup[di] = gi;
+  }
+  // a kernel shared by fewer than kSkMinCols directed edges is cheaper recomputed
+  std::vector<int> gsize(h->sk.size(), 0);
+  for (int g : dgroup)
+    if (g >= 0) ++gsize[g];
+  for (int& g : dgroup)
+    if (g >= 0 && gsize[g] < kSkMinCols) g = -1;
+  std::vector<uint8_t> ok(num_probs, 0);
+  for (int32_t p = 0; p < num_probs; ++p)
+    ok[p] = probs[p].cost_kind == TREE_OT_COST_SQEUCLID && probs[p].coords && h->probs[p].dim > 0;
+  for (size_t di = 0; di < h->dedges.size(); ++di)
+    if (dgroup[di] < 0) ok[h->dedges[di].prob] = 0;
+  for (size_t di = 0; di < h->dedges.size(); ++di) {
+    const DEdgeD& d = h->dedges[di];
+    if (!ok[d.prob]) continue;
+    h->sk[dgroup[di]].cols[h->nodes[d.owner].colour].push_back(SkCol{d.rev_off, d.part_off, d.prob, d.nsplit});
+  }
+  std::vector<tree_ot_handle::SkGroup> kept;
+  for (auto& g : h->sk)
+    if (!g.cols[0].empty() || !g.cols[1].empty()) kept.push_back(std::move(g));
+  h->sk = std::move(kept);
+  h->sk_prob = ok;
+  return TREE_OT_OK;
+}
+
+// device buffers and launch arguments of the shared-kernel groups
+int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
+  int rc;
+  for (auto& g : h->sk) {
+    const NodeD& own = h->nodes[g.owner_rep];
+    const NodeD& nbn = h->nodes[g.nbr_rep];
+    const ProbD& pd = h->probs[g.prob_rep];
+    const int32_t mp = (int32_t)align_up(own.n, kSkTileM), kd = (int32_t)align_up(nbn.n, kSkTileK);
+    const int64_t maxc = (int64_t)std::max(g.cols[0].size(), g.cols[1].size());
+    float *b = nullptr, *rf = nullptr, *cmax = nullptr;
+    __nv_bfloat16 *khi = nullptr, *klo = nullptr, *vhi = nullptr, *vlo = nullptr;
+    SkCol* dc[2] = {nullptr, nullptr};
+    int32_t* fix_count = nullptr;
+    int2* fix_list = nullptr;
+    if ((rc = h->alloc(&b, kd)) || (rc = h->alloc(&rf, mp)) || (rc = h->alloc(&cmax, maxc)) ||
+        (rc = h->alloc(&khi, (int64_t)mp * kd)) ||
+        (rc = h->alloc(&klo, (int64_t)mp * kd)) || (rc = h->alloc(&vhi, maxc * kd)) ||
+        (rc = h->alloc(&vlo, maxc * kd)) || (rc = h->alloc(&dc[0], (int64_t)g.cols[0].size())) ||
+        (rc = h->alloc(&dc[1], (int64_t)g.cols[1].size())) || (rc = h->alloc(&fix_count, 1)) ||
+        (rc = h->alloc(&fix_list, (int64_t)own.n * maxc)))
+      return rc;
+    CUDA_TRY(cudaMemsetAsync(fix_count, 0, sizeof(int32_t), s));
+    for (int c = 0; c < 2; ++c) {
+      if (!g.cols[c].empty())
+        CUDA_TRY(cudaMemcpyAsync(dc[c], g.cols[c].data(), sizeof(SkCol) * g.cols[c].size(), cudaMemcpyHostToDevice,
+                                 s));
+      SkArgs& a = g.args[c];
+      a.cols = dc[c];
+      a.ncols = (int32_t)g.cols[c].size();
+      a.nx = own.n;
+      a.ny = nbn.n;
+      a.dim = pd.dim;
+      a.mp = mp;
+      a.kd = kd;
+      a.hh = h->d_hh;
+      a.hl = h->d_hl;
+      a.done = h->d_done;
+      a.lowp = h->d_lowp;
+      a.xc = h->d_coords + own.coord_off;
+      a.yc = h->d_coords + nbn.coord_off;
+      a.s_hi = pd.s2_scaled;
+      a.s_lo = pd.s2_scaled_lo;
+      a.b = b;
+      a.cmax = cmax;
+      a.rf = rf;
+      a.khi = khi;
+      a.klo = klo;
+      a.vhi = vhi;
+      a.vlo = vlo;
+      a.part32 = h->d_part32;
+      a.fix_count = fix_count;
+      a.fix_list = fix_list;
+    }
+    CUDA_TRY(launch_sk_reset(b, kd, s));
+  }
   return TREE_OT_OK;
 }
 
@@ -1150,6 +1324,10 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     }
     h->lowp = any;
   }
+  if (o.apply_mode == TREE_OT_APPLY_BF16 && !h->fp64) {
+    if ((rc = plan_shared_kernels(h, probs, num_probs))) return bail(rc);
+    if (!h->sk.empty()) h->lowp = true;
+  }
   h->node_smem[0] = h->node_smem[1] = 0;
   for (size_t j = 0; j < h->nodes.size(); ++j) {
     const NodeD& nd = h->nodes[j];
@@ -1202,7 +1380,8 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     if ((rc = h->alloc(&h->d_part32, h->part_len))) return bail(rc);
   }
   if ((rc = h->alloc(&h->d_lowp, num_probs)) || (rc = h->alloc(&h->d_drift, NE)) ||
-      (rc = h->alloc(&h->d_lowp_span, 2 * (int64_t)num_probs)) || (rc = h->alloc(&h->d_absorb_count, 1)))
+      (rc = h->alloc(&h->d_lowp_span, 2 * (int64_t)num_probs)) || (rc = h->alloc(&h->d_absorb_count, 1)) ||
+      (rc = h->alloc(&h->d_lowp_best, num_probs)) || (rc = h->alloc(&h->d_lowp_best_t, num_probs)))
     return bail(rc);
   if (h->lowp) {
     if ((rc = h->alloc(&h->d_bh, h->vec_len)) || (rc = h->alloc(&h->d_bl, h->vec_len)) ||
@@ -1217,6 +1396,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       if ((rc = h->alloc(&ed.K, (int64_t)ed.na * ed.ldk))) return bail(rc);
     }
   }
+  if ((rc = setup_shared_kernels(h, s))) return bail(rc);
 
   auto up = [&](void* dst, const void* src, size_t bytes) -> int {
     if (bytes == 0) return TREE_OT_OK;
@@ -1345,6 +1525,8 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "operand memset"));
   }
   if ((rc = reset_state(h, s))) return bail(rc);
+  // the autotuners time the FP32 kernels: no problem in a BF16 phase meanwhile
+  CUDA_TRY(cudaMemsetAsync(h->d_lowp, 0, sizeof(int32_t) * h->nprob, s));
   if (o.autotune && !h->fp64 && (rc = autotune_recompute(h, s))) return bail(rc);
   if (!h->fp64) {
     if ((rc = upload_stream_tasks(h, s))) return bail(rc);
@@ -1355,6 +1537,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       return bail(rc);
     }
   }
+  if (h->lowp && (rc = reset_state(h, s))) return bail(rc);  // the BF16 phases back
   {
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize(create)"));

@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(kApplyThreads, MINB) apply_recomp_kernel(Apply
     if (ti >= A.ntasks) break;
     const Task t = A.tasks[ti];
     const int prob = A.dedges[t.dedge].prob;
-    if (A.done[prob]) continue;
+    if (A.done[prob] || A.lowp[prob] == 1) continue;  // retired, or in a BF16 phase
     if (EXACT && A.exact[prob])  // block-uniform: refined past the plain recomputation's floor
       recomp_task_exact<D>(A, t, sm);
     else

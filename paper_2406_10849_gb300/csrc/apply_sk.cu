@@ -1,0 +1,374 @@
+// Shared-kernel BF16 phase: for a group of directed edges that share one
+// squared-Euclidean Gibbs kernel, one colour's messages are one matrix product
+// on the tensor cores (sk.h states the arithmetic).  Five launches per group
+// and colour:
+//   sk_envelope_kernel  M_j = max_y h_j(y), b(y) = max over the active columns of h_j(y) - M_j
+//   sk_kbuild_kernel    R(x) and K'(x,y) = 2^(b(y) - R(x) - s C(x,y)), BF16 hi + lo
+//   sk_vbuild_kernel    V'(y,j) = 2^(h_j(y) - M_j - b(y)), BF16 hi + lo
+//   sk_gemm_kernel      S = K'hi V'hi + K'hi V'lo + K'lo V'hi (mma.sync m16n8k16,
+//                       FP32 accumulation); partial (R(x) + M_j, S(x,j)) per output
+//   sk_fixup_kernel     outputs with S < 2^-96 recomputed as an FP32 log-sum-exp
+// M, b and R live on the 2^-10 grid, so b - R and h - M - b are exact and the cost
+// term is formed as in the recomputed-cost apply (FMAs with s = s_hi + s_lo).
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "ptx.cuh"
+#include "sk.h"
+
+namespace treeot {
+namespace {
+
+#define kInf (__int_as_float(0x7f800000))
+
+__device__ __forceinline__ float quant(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
+
+__device__ __forceinline__ bool col_active(const SkArgs& A, const SkCol& c) {
+  return !A.done[c.prob] && A.lowp[c.prob] == 1;
+}
+
+// max of floats through integer atomics on their bit patterns
+__device__ __forceinline__ void atomic_max_float(float* addr, float v) {
+  if (!(v > -kInf)) return;  // -inf and NaN change nothing
+  if (v >= 0.f)
+    atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
+  else
+    atomicMin(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+
+constexpr int kEnvCols = 32;  // columns per envelope CTA
+
+// one CTA per kEnvCols columns: each warp finds the maxima of 4 columns, then
+// every thread folds its points' normalised values into the envelope
+__global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
+  __shared__ float s_m[kEnvCols];
+  __shared__ int64_t s_off[kEnvCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * kEnvCols, nc = min(kEnvCols, A.ncols - c0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.fix_count = 0;  // the previous fix-up is done
+  for (int k = warp; k < kEnvCols; k += 8) {
+    float m = -kInf;
+    int64_t off = 0;
+    if (k < nc) {
+      const SkCol col = A.cols[c0 + k];
+      off = col.h_off;
+      if (col_active(A, col))
+        for (int y = lane; y < A.ny; y += 32) m = fmaxf(m, A.hh[off + y] + A.hl[off + y]);
+    }
+    m = warp_max(m);
+    if (lane == 0) {
+      const float mq = m > -kInf ? quant(m) : -kInf;
+      s_m[k] = mq;
+      s_off[k] = off;
+      if (k < nc) A.cmax[c0 + k] = mq;
+    }
+  }
+  __syncthreads();
+  for (int y = threadIdx.x; y < A.ny; y += 256) {
+    float e = -kInf;
+    for (int k = 0; k < nc; ++k)
+      if (s_m[k] > -kInf) e = fmaxf(e, (A.hh[s_off[k] + y] - s_m[k]) + A.hl[s_off[k] + y]);
+    atomic_max_float(&A.b[y], e);
+  }
+}
+
+__device__ __forceinline__ float sqdist(const float* p, const float* q, int dim) {
+  float c = 0.f;
+  for (int d = 0; d < dim; ++d) {
+    const float t = p[d] - q[d];
+    c = fmaf(t, t, c);
+  }
+  return c;
+}
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// one warp per row x (8 rows per CTA); rows past nx and columns past ny are zero
+__global__ void __launch_bounds__(256) sk_kbuild_kernel(SkArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int x = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (x >= A.mp) return;
+  __nv_bfloat16* khi = A.khi + (int64_t)x * A.kd;
+  __nv_bfloat16* klo = A.klo + (int64_t)x * A.kd;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  if (x >= A.nx) {
+    for (int y = lane; y < A.kd; y += 32) {
+      khi[y] = zero;
+      klo[y] = zero;
+    }
+    if (lane == 0) A.rf[x] = 0.f;
+    return;
+  }
+  float p[3] = {0.f, 0.f, 0.f};
+  for (int d = 0; d < A.dim; ++d) p[d] = A.xc[(int64_t)x * A.dim + d];
+  float env = -kInf;
+  for (int y = lane; y < A.ny; y += 32)
+    env = fmaxf(env, fmaf(-sqdist(p, A.yc + (int64_t)y * A.dim, A.dim), A.s_hi, quant(A.b[y])));
+  env = warp_max(env);
+  const float R = env > -kInf ? quant(env) : 0.f;
+  if (lane == 0) A.rf[x] = R;
+  for (int y = lane; y < A.kd; y += 32) {
+    float v = 0.f;
+    if (y < A.ny && env > -kInf) {
+      const float c = sqdist(p, A.yc + (int64_t)y * A.dim, A.dim);
+      float t = fmaf(-c, A.s_hi, quant(A.b[y]) - R);
+      t = fmaf(-c, A.s_lo, t);
+      v = ex2(t);
+    }
+    split_bf16(v, khi[y], klo[y]);
+  }
+}
+
+// one CTA per column; inactive columns are left alone (their outputs are not stored)
+__global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
+  const int j = blockIdx.x;
+  const SkCol col = A.cols[j];
+  const float M = A.cmax[j];
+  if (!col_active(A, col) || !(M > -kInf)) return;
+  __nv_bfloat16* vhi = A.vhi + (int64_t)j * A.kd;
+  __nv_bfloat16* vlo = A.vlo + (int64_t)j * A.kd;
+  for (int y = threadIdx.x; y < A.kd; y += 256) {
+    float v = 0.f;
+    if (y < A.ny) {
+      const float hh = A.hh[col.h_off + y];
+      if (hh > -kInf) v = ex2(((hh - M) - quant(A.b[y])) + A.hl[col.h_off + y]);
+    }
+    split_bf16(v, vhi[y], vlo[y]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the product: CTA tile 128 rows x 128 columns, 8 warps of 32 x 64, k-stages of
+// 32 in a double-buffered cp.async pipeline, fragments by ldmatrix
+// ---------------------------------------------------------------------------
+
+constexpr int kSkThreads = 256;
+constexpr int kSkLd = kSkTileK + 8;                    // row stride in shared memory (80 bytes)
+constexpr int kSkMat = kSkTileM * kSkLd;               // one operand tile (TileM == TileN)
+constexpr int kSkStage = 4 * kSkMat;                   // khi, klo, vhi, vlo
+constexpr size_t kSkSmem = 2 * kSkStage * sizeof(__nv_bfloat16);  // 80 KB
+static_assert(kSkTileM == kSkTileN, "operand tiles share one shape");
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t* r, const void* smem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+
+// D += A (16x16 bf16, row) * B (16x8 bf16, col), FP32
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void load_stage(const SkArgs& A, __nv_bfloat16* st, int m0, int n0, int k0) {
+  for (int i = threadIdx.x; i < 4 * kSkTileM * (kSkTileK / 8); i += kSkThreads) {
+    const int mat = i / (kSkTileM * (kSkTileK / 8));
+    const int r = (i / (kSkTileK / 8)) % kSkTileM, ch = i % (kSkTileK / 8);
+    __nv_bfloat16* dst = st + mat * kSkMat + r * kSkLd + ch * 8;
+    if (mat < 2) {
+      const __nv_bfloat16* src = (mat == 0 ? A.khi : A.klo) + (int64_t)(m0 + r) * A.kd + k0 + ch * 8;
+      cp_async16(dst, src, true);
+    } else {
+      const int j = n0 + r;
+      const bool valid = j < A.ncols;
+      const __nv_bfloat16* src = (mat == 2 ? A.vhi : A.vlo) + (int64_t)(valid ? j : 0) * A.kd + k0 + ch * 8;
+      cp_async16(dst, src, valid);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
+  extern __shared__ __align__(128) unsigned char sk_smem[];
+  __nv_bfloat16* stages = reinterpret_cast<__nv_bfloat16*>(sk_smem);
+  __shared__ SkCol s_cols[kSkTileN];
+  __shared__ int s_act[kSkTileN];
+  __shared__ float s_cm[kSkTileN];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.y * kSkTileM, n0 = blockIdx.x * kSkTileN;
+  if (blockIdx.x == 0 && blockIdx.y == 0)  // the envelope is consumed: reset it for the next product
+    for (int y = tid; y < A.kd; y += kSkThreads) A.b[y] = -kInf;
+  bool any = false;
+  if (tid < kSkTileN) {
+    const int j = n0 + tid;
+    int act = 0;
+    if (j < A.ncols) {
+      s_cols[tid] = A.cols[j];
+      s_cm[tid] = A.cmax[j];
+      act = col_active(A, s_cols[tid]) && s_cm[tid] > -kInf ? 1 : 0;
+    }
+    s_act[tid] = act;
+    any = act != 0;
+  }
+  if (!__syncthreads_or(any)) return;
+
+  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 64;
+  float acc[2][8][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+
+  const int nk = A.kd / kSkTileK;
+  load_stage(A, stages, m0, n0, 0);
+  cp_async_commit();
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) load_stage(A, stages + ((kt + 1) & 1) * kSkStage, m0, n0, (kt + 1) * kSkTileK);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const __nv_bfloat16* st = stages + (kt & 1) * kSkStage;
+    const __nv_bfloat16* sAh = st;
+    const __nv_bfloat16* sAl = st + kSkMat;
+    const __nv_bfloat16* sBh = st + 2 * kSkMat;
+    const __nv_bfloat16* sBl = st + 3 * kSkMat;
+#pragma unroll
+    for (int ks = 0; ks < kSkTileK; ks += 16) {
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int off = (wm + 16 * i + (lane & 15)) * kSkLd + ks + (lane >> 4) * 8;
+        ldmatrix_x4(ah[i], sAh + off);
+        ldmatrix_x4(al[i], sAl + off);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; jj += 2) {
+        uint32_t bh[4], bl[4];
+        const int off = (wn + 8 * jj + (lane & 7) + ((lane >> 4) << 3)) * kSkLd + ks + ((lane >> 3) & 1) * 8;
+        ldmatrix_x4(bh, sBh + off);
+        ldmatrix_x4(bl, sBl + off);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][jj], ah[i], bh);
+          mma_bf16(acc[i][jj], ah[i], bl);
+          mma_bf16(acc[i][jj], al[i], bh);
+          mma_bf16(acc[i][jj + 1], ah[i], bh + 2);
+          mma_bf16(acc[i][jj + 1], ah[i], bl + 2);
+          mma_bf16(acc[i][jj + 1], al[i], bh + 2);
+        }
+      }
+    }
+    __syncthreads();  // this stage is refilled by the next iteration's loads
+  }
+
+  // epilogue: partial (R(x), S(x,j)) into piece 0, the other pieces emptied
+  const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int x = m0 + wm + 16 * i + gid + (r >= 2 ? 8 : 0);
+        const int cl = wn + 8 * j + 2 * tig + (r & 1);
+        if (x >= A.nx || !s_act[cl]) continue;
+        const SkCol& col = s_cols[cl];
+        const float S = acc[i][j][r];
+        if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
+          const int slot = atomicAdd(A.fix_count, 1);
+          A.fix_list[slot] = make_int2(x, n0 + cl);
+          continue;
+        }
+        A.part32[col.part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
+        for (int sp = 1; sp < col.nsplit; ++sp) A.part32[col.part_off + (int64_t)sp * A.nx + x] = make_float2(0.f, 0.f);
+      }
+}
+
+// one warp per listed output: frame = the largest term on the 2^-10 grid, then
+// the sum of 2^(term - frame) with the recomputed-cost apply's argument
+__global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int nfix = *A.fix_count;
+  for (int w = blockIdx.x * 8 + (threadIdx.x >> 5); w < nfix; w += gridDim.x * 8) {
+    const int2 e = A.fix_list[w];
+    const int x = e.x;
+    const SkCol col = A.cols[e.y];
+    const float* hh = A.hh + col.h_off;
+    const float* hl = A.hl + col.h_off;
+    float p[3] = {0.f, 0.f, 0.f};
+    for (int d = 0; d < A.dim; ++d) p[d] = A.xc[(int64_t)x * A.dim + d];
+    float mx = -kInf;
+    for (int y = lane; y < A.ny; y += 32)
+      mx = fmaxf(mx, fmaf(-sqdist(p, A.yc + (int64_t)y * A.dim, A.dim), A.s_hi, hh[y]));
+    mx = warp_max(mx);
+    float R = 0.f, S = 0.f;
+    if (mx > -kInf) {
+      R = quant(mx);
+      for (int y = lane; y < A.ny; y += 32) {
+        if (!(hh[y] > -kInf)) continue;
+        const float c = sqdist(p, A.yc + (int64_t)y * A.dim, A.dim);
+        float t = fmaf(-c, A.s_hi, hh[y] - R);
+        t = fmaf(-c, A.s_lo, t);
+        S += ex2(t + hl[y]);
+      }
+      S = warp_sum(S);
+    }
+    if (lane == 0) {
+      A.part32[col.part_off + x] = make_float2(R, S);
+      for (int sp = 1; sp < col.nsplit; ++sp) A.part32[col.part_off + (int64_t)sp * A.nx + x] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+__global__ void sk_reset_kernel(float* b, int32_t kd) {
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < kd; y += gridDim.x * blockDim.x) b[y] = -kInf;
+}
+
+// dynamic shared memory above 48 KB is a per-device function attribute
+bool sk_gemm_ready() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> state[kMaxDevices];  // 0 unknown, 1 set, 2 refused
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  int st = state[dev].load();
+  if (st == 0) {
+    st = cudaFuncSetAttribute(sk_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSkSmem) ==
+                 cudaSuccess
+             ? 1
+             : 2;
+    state[dev].store(st);
+  }
+  return st == 1;
+}
+
+}  // namespace
+
+cudaError_t launch_sk(const SkArgs& a, cudaStream_t s) {
+  if (a.ncols <= 0) return cudaSuccess;
+  if (!sk_gemm_ready()) return cudaErrorInvalidConfiguration;
+  sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
+  sk_kbuild_kernel<<<a.mp / 8, 256, 0, s>>>(a);
+  sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
+  sk_gemm_kernel<<<dim3((a.ncols + kSkTileN - 1) / kSkTileN, a.mp / kSkTileM), kSkThreads, kSkSmem, s>>>(a);
+  sk_fixup_kernel<<<152 * 8, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sk_reset(float* b, int32_t kd, cudaStream_t s) {
+  if (kd <= 0) return cudaSuccess;
+  sk_reset_kernel<<<(kd + 255) / 256, 256, 0, s>>>(b, kd);
+  return cudaGetLastError();
+}
+
+}  // namespace treeot

@@ -29,6 +29,7 @@
 // consumer warp skips its work but still arrives on every barrier and reaches
 // every named barrier of the CTA, so nothing waits forever.  Before exiting,
 // the producer waits (bounded) until every copy it issued has landed.
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
@@ -444,19 +445,25 @@ __global__ void __launch_bounds__(kTmaThreads, 1) apply_dense_tma_kernel(ApplyAr
 
 }  // namespace
 
+// Function attributes are per device: the answer is kept per device id.
 bool apply_tma_available() {
-  static int ok = -1;
-  if (ok < 0) {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> state[kMaxDevices];  // 0 unknown, 1 available, 2 not
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  int st = state[dev].load();
+  if (st == 0) {
     int blocks = 0;
-    ok = cudaFuncSetAttribute(apply_dense_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) ==
-                     cudaSuccess &&
-                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, apply_dense_tma_kernel, kTmaThreads,
-                                                               kTmaSmem) == cudaSuccess &&
-                 blocks >= 1
-             ? 1
-             : 0;
+    const bool ok =
+        cudaFuncSetAttribute(apply_dense_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, apply_dense_tma_kernel, kTmaThreads, kTmaSmem) ==
+            cudaSuccess &&
+        blocks >= 1;
+    st = ok ? 1 : 2;
+    state[dev].store(st);
   }
-  return ok == 1;
+  return st == 1;
 }
 
 cudaError_t launch_apply_tma(const ApplyArgs& a, int grid, cudaStream_t s) {

@@ -30,6 +30,8 @@ constexpr int kNodePairs = 1024;       // node update: (owned edge, point) pairs
 constexpr int kBfCols = 256;           // BF16 COL task: columns per task (32 lanes x 8)
 constexpr int kBfRowTask = 256;        // BF16 ROW task: rows per task
 constexpr double kGrid = 1024.0;       // apply operands and frames live on a 2^-10 grid
+constexpr int64_t kLowpStall = 128;    // a BF16 phase whose stopping quantity has not fallen by 10 %
+                                       // for this many half-steps hands the problem to FP32
 
 enum TaskKind : int32_t {
   TASK_ROW = 0,     // stored matrix, owner is the row node: reduce along a row
@@ -239,7 +241,9 @@ struct NodeArgs {
   double refine_tol;
   float tau;                 // drift limit (log2 units)
   int32_t lowp_start;
-  int64_t* lowp_span;        // per problem: half-steps at which the BF16 phase began / ended
+  int64_t* lowp_span;        // per problem: half-steps at which the BF16 phase began / ended (-1: not yet)
+  double* lowp_best;         // per problem: smallest stopping quantity seen in the BF16 phase
+  int64_t* lowp_best_t;      // per problem: the half-step of that last improvement
 };
 
 // FP64-grade check of the current potentials.  Per element the exponent

@@ -391,11 +391,20 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
         // enter the low-precision phase: absorb every edge of the problem next
         A.lowp[p] = 1;
         A.lowp_span[2 * p] = t_now + 1;
+        A.lowp_best[p] = INFINITY;
+        A.lowp_best_t[p] = t_now + 1;
         for (int k = 0; k < P.edge_count; ++k) A.drift[P.edge_begin + k] = 1;
       } else if (lp == 1) {
-        // the absorbed kernel's accuracy is enough until the stopping quantity
-        // reaches refine_tol; from then on the FP32 kernel refines
-        if (crit < A.refine_tol) {
+        // the phase's accuracy is enough until the stopping quantity reaches
+        // refine_tol; from then on (or once the phase stops improving) the FP32
+        // kernel refines.  refine_tol = 0 keeps a problem in the phase.
+        if (crit < A.refine_tol || !(crit == crit)) {
+          A.lowp[p] = 0;
+          A.lowp_span[2 * p + 1] = t_now + 1;
+        } else if (crit < 0.9 * A.lowp_best[p]) {
+          A.lowp_best[p] = crit;
+          A.lowp_best_t[p] = t_now;
+        } else if (A.refine_tol > 0.0 && t_now - A.lowp_best_t[p] > kLowpStall) {
           A.lowp[p] = 0;
           A.lowp_span[2 * p + 1] = t_now + 1;
         }
@@ -421,15 +430,14 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
 
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s) {
   if (a.nchunks <= 0) return cudaSuccess;
-  // more than the default 48 KB of dynamic shared memory only for nodes of very high degree
-  static uint32_t opted[2] = {48u * 1024, 48u * 1024};
-  if (a.smem > opted[fp64 ? 1 : 0]) {
+  // more than the default 48 KB of dynamic shared memory only for nodes of very
+  // high degree; the attribute is per device and cheap to set again
+  if (a.smem > 48u * 1024) {
     const cudaError_t e =
         fp64 ? cudaFuncSetAttribute(node_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem)
              : cudaFuncSetAttribute(node_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)a.smem);
     if (e != cudaSuccess) return e;
-    opted[fp64 ? 1 : 0] = a.smem;
   }
   if (fp64)
     node_update_kernel<true><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
