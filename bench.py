@@ -450,6 +450,74 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stars(args):
+    """The shared-kernel BF16 phase on a batch of barycenter stars (8 fixed
+    leaves on a side x side grid, free centre, eps 0.005: every directed edge of
+    every star shares one Gibbs kernel).  Times a half-step of the phase and of
+    the FP32 recomputed-cost path with CUDA events on the launching stream, and
+    (unless --no-converge) the whole batch to a certified max marginal L1 <= 1e-6
+    in each form."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+
+    T.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    probs = gen.warmstart_stars(9_000_000, args.stars, side=args.side, eps=0.005)
+    n = args.side * args.side
+    cols = 8 * args.stars  # directed edges per half-step
+    forms = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0, refine_tol=0.0)}
+    res = {}
+    for name, kw in forms.items():
+        s = T.Solver(probs, T.options(**kw), stream=stream)
+        s.half_steps(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            s.half_steps(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        res[name] = {"ms_per_half_step": e0.elapsed_time(e1) / args.steps, "clocks": clk.summary()}
+        s.close()
+    if not args.no_converge:
+        solve = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0,
+                                                               refine_tol=args.refine_tol)}
+        for name, kw in solve.items():
+            s = T.Solver(probs, T.options(tol=1e-6, tol_kind="max", max_half_steps=20000, **kw), stream=stream)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc, out = s.solve()
+            dt = time.perf_counter() - t0
+            s.close()
+            hs = np.array([r["half_steps"] for r in out], dtype=np.float64)
+            res[name]["time_to_1e-6_s"] = dt
+            res[name]["half_steps_mean"] = float(hs.mean())
+            res[name]["bf16_half_steps_mean"] = float(np.mean([r["lowp_half_steps"] for r in out]))
+            res[name]["certified"] = int(sum(r["status"] == 0 for r in out))
+            res[name]["worst_max_marginal_l1"] = max(r["max_marginal_l1"] for r in out)
+    ms = res["bf16_shared_kernel"]["ms_per_half_step"]
+    line = {
+        "metric": "edge-kernel applies/sec, shared-kernel BF16 phase (stars on one grid)",
+        "value": cols / (ms / 1e3), "unit": "edge_applies/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3 tensor-core product, f32 node update", "data": "synthetic",
+        "config": {"workload": f"stars{args.stars}_grid{n}_eps0.005", "stars": args.stars, "leaves": 8, "n": n,
+                   "step": "one half-step over all stars", "refine_tol": args.refine_tol},
+        "plain_fp32_edge_applies_per_s": cols / (res["plain_fp32"]["ms_per_half_step"] / 1e3),
+        "speedup_per_half_step": res["plain_fp32"]["ms_per_half_step"] / ms,
+        "product_flops_per_half_step": 3 * 2 * n * n * cols,
+        "forms": res,
+    }
+    if not args.no_converge:
+        line["speedup_time_to_1e-6"] = (res["plain_fp32"]["time_to_1e-6_s"]
+                                        / res["bf16_shared_kernel"]["time_to_1e-6_s"])
+    print(json.dumps(line), flush=True)
+
+
 def run_unit_rates():
     """Build and run the unit-rate microbenchmark (csrc/unit_rates.cu): FP32 FMA
     lanes, packed f32x2 lanes and MUFU ex2 per clock and SM, ex2.approx error."""
@@ -471,10 +539,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-1e-6 solve")
     ap.add_argument("--nodes", type=int, default=NODES, help="tree size (64 = the benchmark workload)")
-    ap.add_argument("--workload", default="prufer", choices=["prufer", "batched", "warmstart"],
+    ap.add_argument("--workload", default="prufer", choices=["prufer", "batched", "warmstart", "stars"],
                     help="prufer: the 64-node stored-cost tree (default); batched: independent random trees "
                          "with costs recomputed from 2-D points (measured against the MUFU ex2 roofline); "
-                         "warmstart: learned warm start on barycenter stars, warm vs u = 1")
+                         "warmstart: learned warm start on barycenter stars, warm vs u = 1; "
+                         "stars: the shared-kernel BF16 phase on a batch of stars")
+    ap.add_argument("--stars", type=int, default=2000, help="stars workload: number of stars")
     ap.add_argument("--train-trees", type=int, default=20000, help="warmstart: training stars")
     ap.add_argument("--test-trees", type=int, default=2000, help="warmstart: held-out stars")
     ap.add_argument("--side", type=int, default=32, help="warmstart: grid side (n = side^2)")
@@ -497,6 +567,8 @@ def main():
         return run_batched(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "stars":
+        return run_stars(args)
 
     import torch
 

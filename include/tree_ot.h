@@ -125,6 +125,10 @@ typedef struct tree_ot_problem {
  * kernel returns normally and tree_ot_solve reports TREE_OT_ERR_TIMEOUT.
  * Implies TREE_OT_OPT_DENSE_TMA.  No GPU fault is involved. */
 #define TREE_OT_OPT_TEST_STALL   16u
+#define TREE_OT_OPT_SK_MMA_SYNC 32u /* shared-kernel BF16 phase: multiply with the legacy
+                                       mma.sync kernel instead of tcgen05 (tensor memory
+                                       accumulators); for comparison and for devices
+                                       without tcgen05                                     */
 
 #define TREE_OT_TOL_SUM          0  /* the paper's stopping sum (Bipartite Iterative Scaling) */
 #define TREE_OT_TOL_MAX          1  /* the largest single term of that sum                 */

@@ -192,6 +192,7 @@ struct tree_ot_handle {
     std::vector<SkCol> cols[2];
     int32_t owner_rep = 0, nbr_rep = 0, prob_rep = 0;  // representative nodes / problem
     SkArgs args[2]{};
+    SkMaps maps[2]{};  // tensor maps of the tcgen05 product's operands, per colour
   };
   std::vector<SkGroup> sk;
   std::vector<uint8_t> sk_prob;
@@ -233,6 +234,7 @@ struct tree_ot_handle {
   int bf16_grid = 1;
   float* d_fr = nullptr;                   // frames of the messages (FP32, log2 on the 2^-10 grid)
   double *d_f = nullptr, *d_Z = nullptr, *d_rho = nullptr, *d_logg = nullptr, *d_mu = nullptr;
+  float4* d_lgf = nullptr;                 // per node point: log2 mu (hi on the grid, lo), mu (FP32 node update)
   double *d_resid_acc = nullptr, *d_resid_dedge = nullptr, *d_res_sum = nullptr, *d_marg = nullptr;
   double *d_edge_tc = nullptr, *d_edge_mass = nullptr;
   float *d_hh = nullptr, *d_hl = nullptr, *d_ah = nullptr, *d_al = nullptr, *d_coords = nullptr;
@@ -406,6 +408,7 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.part64 = h->d_part64;
   a.logg = h->d_logg;
   a.mu = h->d_mu;
+  a.lgf = h->d_lgf;
   a.zpart = h->d_zpart;
   a.resid_acc = h->d_resid_acc;
   a.resid_dedge = h->d_resid_dedge;
@@ -499,7 +502,7 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
   }
   if (!only_stored)
     for (const auto& g : h->sk) {
-      cudaError_t e = launch_sk(g.args[colour], s);
+      cudaError_t e = launch_sk(g.args[colour], g.args[colour].use_tc ? &g.maps[colour] : nullptr, s);
       if (e != cudaSuccess) return cuda_fail(e, "shared-kernel apply launch");
     }
   return TREE_OT_OK;
@@ -1021,7 +1024,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
     const NodeD& own = h->nodes[g.owner_rep];
     const NodeD& nbn = h->nodes[g.nbr_rep];
     const ProbD& pd = h->probs[g.prob_rep];
-    const int32_t mp = (int32_t)align_up(own.n, kSkTileM), kd = (int32_t)align_up(nbn.n, kSkTileK);
+    const int32_t mp = (int32_t)align_up(own.n, kSkTileM), kd = (int32_t)align_up(nbn.n, kSkPadK);
     const int64_t maxc = (int64_t)std::max(g.cols[0].size(), g.cols[1].size());
     float *b = nullptr, *rf = nullptr, *cmax = nullptr;
     __nv_bfloat16 *khi = nullptr, *klo = nullptr, *vhi = nullptr, *vlo = nullptr;
@@ -1066,7 +1069,14 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       a.part32 = h->d_part32;
       a.fix_count = fix_count;
       a.fix_list = fix_list;
+      a.err = h->d_err;
+      a.use_tc = !(h->opt.flags & TREE_OT_OPT_SK_MMA_SYNC) && sk_tc_available() ? 1 : 0;
     }
+    // the tcgen05 product needs tensor maps of its operands; without them both colours use mma.sync
+    bool tc = g.args[0].use_tc != 0;
+    for (int c = 0; c < 2 && tc; ++c)
+      if (g.args[c].ncols > 0 && !sk_encode_maps(g.args[c], &g.maps[c])) tc = false;
+    for (int c = 0; c < 2; ++c) g.args[c].use_tc = tc ? 1 : 0;
     CUDA_TRY(launch_sk_reset(b, kd, s));
   }
   return TREE_OT_OK;
@@ -1361,7 +1371,8 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = h->alloc(&h->d_hl, h->vec_len)) || (rc = h->alloc(&h->d_ah, h->vec_len)) ||
       (rc = h->alloc(&h->d_al, h->vec_len)) || (rc = h->alloc(&h->d_marg, h->vec_len)) ||
       (rc = h->alloc(&h->d_Z, NN)) || (rc = h->alloc(&h->d_rho, NN)) || (rc = h->alloc(&h->d_logg, h->node_len)) ||
-      (rc = h->alloc(&h->d_mu, h->node_len)) || (rc = h->alloc(&h->d_coords, h->coord_len)) ||
+      (rc = h->alloc(&h->d_mu, h->node_len)) || (rc = h->alloc(&h->d_lgf, h->node_len)) ||
+      (rc = h->alloc(&h->d_coords, h->coord_len)) ||
       (rc = h->alloc(&h->d_coords_hi, h->coord_len)) || (rc = h->alloc(&h->d_coords_lo, h->coord_len)) ||
       (rc = h->alloc(&h->d_cmax, num_probs)) || (rc = h->alloc(&h->d_exact, num_probs)) ||
       (rc = h->alloc(&h->d_zpart, h->nzchunks)) || (rc = h->alloc(&h->d_resid_acc, ND)) ||
@@ -1407,6 +1418,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   // node vectors: log gamma and mu (FP64)
   {
     std::vector<double> lg(h->node_len, 0.0), mu(h->node_len, 0.0);
+    std::vector<float4> lgf(h->node_len, float4{0.f, 0.f, 0.f, 0.f});
     for (size_t j = 0; j < h->nodes.size(); ++j) {
       const NodeD& nd = h->nodes[j];
       if (!nd.fixed) continue;
@@ -1414,10 +1426,20 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
         const double v = h->mu[j][x];
         mu[nd.node_off + x] = v;
         lg[nd.node_off + x] = v > 0.0 ? std::log(v) : -INFINITY;
+        // log2 mu as (hi on the 2^-10 grid, lo), as the device splits values
+        float4& g = lgf[nd.node_off + x];
+        if (v > 0.0) {
+          const double l2 = std::log(v) * kLog2e;
+          const float hi = std::rint((float)l2 * 1024.f) * (1.f / 1024.f);
+          g = float4{hi, (float)(l2 - (double)hi), (float)v, 0.f};
+        } else {
+          g = float4{-INFINITY, 0.f, 0.f, 0.f};
+        }
       }
     }
     if ((rc = up(h->d_logg, lg.data(), sizeof(double) * lg.size())) ||
-        (rc = up(h->d_mu, mu.data(), sizeof(double) * mu.size())))
+        (rc = up(h->d_mu, mu.data(), sizeof(double) * mu.size())) ||
+        (rc = up(h->d_lgf, lgf.data(), sizeof(float4) * lgf.size())))
       return bail(rc);
     CUDA_TRY(cudaStreamSynchronize(s));
   }

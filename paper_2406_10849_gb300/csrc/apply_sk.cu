@@ -10,6 +10,7 @@
 //   sk_fixup_kernel     outputs with S < 2^-96 recomputed as an FP32 log-sum-exp
 // M, b and R live on the 2^-10 grid, so b - R and h - M - b are exact and the cost
 // term is formed as in the recomputed-cost apply (FMAs with s = s_hi + s_lo).
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled (the encoder is fetched through the runtime)
 #include <cuda_bf16.h>
 
 #include <atomic>
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
   __shared__ int s_act[kSkTileN];
   __shared__ float s_cm[kSkTileN];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.y * kSkTileM, n0 = blockIdx.x * kSkTileN;
+  // row tiles vary fastest: the CTAs that share a column tile of V' run together (L2 reuse)
+  const int m0 = blockIdx.x * kSkTileM, n0 = blockIdx.y * kSkTileN;
   if (blockIdx.x == 0 && blockIdx.y == 0)  // the envelope is consumed: reset it for the next product
     for (int y = tid; y < A.kd; y += kSkThreads) A.b[y] = -kInf;
   bool any = false;
@@ -295,6 +297,238 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
       }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 variant of the product.  One CTA of 4 warps per 128 x 128 output
+// tile.  A stage holds 64 reduction points of K'hi, K'lo, V'hi and V'lo, each a
+// 128 x 64 BF16 box brought by one TMA copy (cp.async.bulk.tensor) in the
+// 128-byte-swizzled K-major layout the MMA descriptors describe (measured
+// faster than six stages of 64-byte-swizzled 128 x 32 boxes: 223 against 255 us
+// per product on 2000 stars).  Thread 0
+// keeps kTcStages stages in flight: it waits for a stage's copies (full
+// barrier, transaction count), issues its 12 MMAs (kind::f16: BF16 operands
+// from shared memory, FP32 accumulators in tensor memory, 128 x 128 x 16
+// each), commits them to the stage's empty barrier, and refills the previous
+// stage's buffer once that stage's MMAs are done (one stage of MMAs always
+// queued behind the running one).  The accumulators
+// come back with tcgen05.ld, one output row per thread.  Every wait is
+// bounded; a wait that runs out sets bit 1 of the error word.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 128;
+constexpr int kTcK = 64;                              // reduction points per stage (128-byte rows)
+constexpr int kTcTileBytes = kSkTileM * kTcK * 2;     // 16 KB
+constexpr int kTcStageBytes = 4 * kTcTileBytes;       // 64 KB
+constexpr int kTcStages = 3;
+constexpr size_t kTcSmem = kTcStages * kTcStageBytes + 1024;  // stages + alignment slack
+constexpr uint32_t kTcCols = kSkTileN;                        // tensor memory columns (N FP32 accumulators per row)
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSkTileN >> 3) << 17) |
+                              ((uint32_t)(kSkTileM >> 4) << 24);
+constexpr uint64_t kTcWaitNs = 250ull * 1000 * 1000;  // a wait gives up after 250 ms
+static_assert(kSkTileM == 128 && kSkTileN == 128 && kSkPadK % kTcK == 0, "the tcgen05 tile is 128 x 128 x 64");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: 128-byte-swizzled K-major tile, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// one 2-D box (x = reduction index, y = row) into shared memory, completion on bar
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait on an mbarrier phase: kTcWaitNs of wall time, 2^24 polls at most
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  uint64_t start = 0;
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 63) == 63) {
+      uint64_t now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (start == 0)
+        start = now;
+      else if (now - start > kTcWaitNs)
+        return false;
+      __nanosleep(256);
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    sk_gemm_tc_kernel(const __grid_constant__ SkArgs A, const __grid_constant__ CUtensorMap tkhi,
+                      const __grid_constant__ CUtensorMap tklo, const __grid_constant__ CUtensorMap tvhi,
+                      const __grid_constant__ CUtensorMap tvlo) {
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  __shared__ SkCol s_cols[kSkTileN];
+  __shared__ int s_act[kSkTileN];
+  __shared__ float s_cm[kSkTileN];
+  __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // row tiles vary fastest: the CTAs that share a column tile of V' run together (L2 reuse)
+  const int m0 = blockIdx.x * kSkTileM, n0 = blockIdx.y * kSkTileN;
+  if (blockIdx.x == 0 && blockIdx.y == 0)  // the envelope is consumed: reset it for the next product
+    for (int y = tid; y < A.kd; y += kTcThreads) A.b[y] = -kInf;
+  bool any = false;
+  {
+    const int j = n0 + tid;  // one column per thread
+    int act = 0;
+    if (j < A.ncols) {
+      s_cols[tid] = A.cols[j];
+      s_cm[tid] = A.cmax[j];
+      act = col_active(A, s_cols[tid]) && s_cm[tid] > -kInf ? 1 : 0;
+    }
+    s_act[tid] = act;
+    any = act != 0;
+  }
+  if (!__syncthreads_or(any)) return;
+
+  // stages on a 1024-byte boundary (the swizzle pattern follows the address bits)
+  const uint32_t raw = smem_u32(tc_raw);
+  const uint32_t stage0 = (raw + 1023u) & ~1023u;
+  if (tid == 0) {
+    for (int i = 0; i < kTcStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[i])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const int nk = A.kd / kTcK;
+
+  if (tid == 0) {
+    auto issue = [&](int kt) {
+      const int b = kt % kTcStages;
+      const uint32_t dst = stage0 + b * kTcStageBytes;
+      tc_expect(&s_full[b], kTcStageBytes);
+      tma_box(dst, &tkhi, kt * kTcK, m0, &s_full[b]);
+      tma_box(dst + kTcTileBytes, &tklo, kt * kTcK, m0, &s_full[b]);
+      tma_box(dst + 2 * kTcTileBytes, &tvhi, kt * kTcK, n0, &s_full[b]);
+      tma_box(dst + 3 * kTcTileBytes, &tvlo, kt * kTcK, n0, &s_full[b]);
+    };
+    int issued = 0;
+    for (; issued < kTcStages && issued < nk; ++issued) issue(issued);
+    bool ok = true;
+    int kt = 0;
+    for (; kt < nk; ++kt) {
+      const int b = kt % kTcStages;
+      const uint32_t par = (kt / kTcStages) & 1;
+      if (!tc_wait(&s_full[b], par)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = stage0 + b * kTcStageBytes;
+      const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + kTcTileBytes);
+      const uint64_t bh = sw128_desc(sa + 2 * kTcTileBytes), bl = sw128_desc(sa + 3 * kTcTileBytes);
+      for (int k = 0; k < kTcK / 16; ++k) {
+        const uint64_t dk = (uint64_t)((k * 32) >> 4);  // 16 BF16 further along K
+        tc_mma(tmem, ah + dk, bh + dk, (kt | k) != 0 ? 1u : 0u);
+        tc_mma(tmem, ah + dk, bl + dk, 1u);
+        tc_mma(tmem, al + dk, bh + dk, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&s_empty[b]))
+                   : "memory");
+      // refill the previous stage's buffer once its MMAs (queued ahead of this
+      // stage's, so the tensor pipe never runs dry) have read it
+      if (kt >= 1 && issued < nk) {
+        const int pb = (kt - 1) % kTcStages;
+        if (!tc_wait(&s_empty[pb], ((kt - 1) / kTcStages) & 1)) {
+          ok = false;
+          ++kt;
+          break;
+        }
+        issue(issued++);
+      }
+    }
+    if (!ok) {
+      // let every copy already issued land before the CTA may leave (bounded)
+      for (int q = kt; q < issued; ++q) (void)tc_wait(&s_full[q % kTcStages], (q / kTcStages) & 1);
+      s_ok = 0;
+    }
+  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  // the last commit covers every MMA issued before it
+  if (ok) ok = tc_wait(&s_empty[(nk - 1) % kTcStages], ((nk - 1) / kTcStages) & 1);
+  ok = __syncthreads_and(ok);
+  if (!ok) {
+    if (tid == 0) atomicOr(A.err, 2);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int x = m0 + warp * 32 + lane;  // tensor-memory lane = output row
+    for (int c0 = 0; c0 < kSkTileN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (x >= A.nx) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int cl = c0 + i;
+        if (!s_act[cl]) continue;
+        const SkCol& col = s_cols[cl];
+        const float S = __uint_as_float(v[i]);
+        if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
+          const int slot = atomicAdd(A.fix_count, 1);
+          A.fix_list[slot] = make_int2(x, n0 + cl);
+          continue;
+        }
+        A.part32[col.part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
+        for (int sp = 1; sp < col.nsplit; ++sp)
+          A.part32[col.part_off + (int64_t)sp * A.nx + x] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
 // one warp per listed output: frame = the largest term on the 2^-10 grid, then
 // the sum of 2^(term - frame) with the recomputed-cost apply's argument
 __global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
@@ -352,15 +586,68 @@ bool sk_gemm_ready() {
   return st == 1;
 }
 
+bool sk_tc_ready() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> state[kMaxDevices];  // 0 unknown, 1 available, 2 not
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  int st = state[dev].load();
+  if (st == 0) {
+    int blocks = 0;
+    const bool ok =
+        cudaFuncSetAttribute(sk_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sk_gemm_tc_kernel, kTcThreads, kTcSmem) ==
+            cudaSuccess &&
+        blocks >= 1;
+    st = ok ? 1 : 2;
+    state[dev].store(st);
+  }
+  return st == 1;
+}
+
 }  // namespace
 
-cudaError_t launch_sk(const SkArgs& a, cudaStream_t s) {
+bool sk_tc_available() { return sk_tc_ready(); }
+
+bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::atomic<int> state{0};  // 0 unknown, 1 found, 2 not
+  if (state.load() == 0) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                        cudaSuccess &&
+                    q == cudaDriverEntryPointSuccess && fn != nullptr;
+    if (ok) encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    state.store(ok ? 1 : 2);
+  }
+  if (state.load() != 1 || a.ncols <= 0) return false;
+  auto make = [&](CUtensorMap* map, const void* base, int64_t rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.kd, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.kd * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kSkTileM};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  return make(&m->khi, a.khi, a.mp) && make(&m->klo, a.klo, a.mp) && make(&m->vhi, a.vhi, a.ncols) &&
+         make(&m->vlo, a.vlo, a.ncols);
+}
+
+cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s) {
   if (a.ncols <= 0) return cudaSuccess;
-  if (!sk_gemm_ready()) return cudaErrorInvalidConfiguration;
+  if (a.use_tc && !maps) return cudaErrorInvalidValue;
+  if (!(a.use_tc ? sk_tc_ready() : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
   sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
   sk_kbuild_kernel<<<a.mp / 8, 256, 0, s>>>(a);
   sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
-  sk_gemm_kernel<<<dim3((a.ncols + kSkTileN - 1) / kSkTileN, a.mp / kSkTileM), kSkThreads, kSkSmem, s>>>(a);
+  const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
+  if (a.use_tc)
+    sk_gemm_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo);
+  else
+    sk_gemm_kernel<<<grid, kSkThreads, kSkSmem, s>>>(a);
   sk_fixup_kernel<<<152 * 8, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

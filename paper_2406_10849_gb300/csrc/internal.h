@@ -217,6 +217,7 @@ struct NodeArgs {
   const double2* part64;
   const double* logg;
   const double* mu;
+  const float4* lgf;         // FP32 path, per node point: log2 mu as (hi on the grid, lo), mu, 0
   double2* zpart;            // per node chunk: (max, sum) of the chunk's s values
   double* resid_acc;         // per directed edge: stopping term being accumulated
   double* resid_dedge;       // per directed edge: latest complete stopping term

@@ -25,7 +25,6 @@
 // node of a problem records the stopping quantity and (when asked) retires the
 // problem, the last CTA of the launch advances the half-step counter.
 #include <cmath>
-#include <type_traits>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -33,60 +32,15 @@
 namespace treeot {
 namespace {
 
-// Two paths.  FP64 handles merge FP64 partials and work in double throughout.
-// FP32 handles keep the potentials and messages in double (their magnitudes
-// reach hundreds, their accuracy must not) but do everything that needs only
-// FP32 accuracy in FP32: the merge, the frames, the operand split and the
-// stopping terms.  GB300 executes FP64 arithmetic and float <-> double
-// conversions at a small fraction of its FP32 rate, so the FP32 path counts
-// every FP64-pipe instruction (about 15 per output and edge).
-
-constexpr float kLn2f = 0.693147180559945309f;
-constexpr float kLog2ef = 1.442695040888963407f;
+// Two paths.  FP64 handles merge FP64 partials and work in double throughout
+// (chunk_update64).  FP32 handles (chunk_update32) work in log2 units on
+// two-float values and use FP64 arithmetic only to form the stored potential:
+// GB300 executes FP64 arithmetic and float <-> double conversions at a small
+// fraction of its FP32 rate.
 
 __device__ __forceinline__ float quant(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
 
-// merge the apply's (frame, sum) pieces of one output (FP32 partials); empty
-// pieces (sum 0) carry no frame.  The message is returned as a pair:
-//   m = t ln2 + l,   t = R + e (largest frame plus the sum's binary exponent),
-//   l = ln of the sum's mantissa plus the rounding error of t, |l| < 1.
-// t is exact when the frames lie on the 2^-10 grid (every FP32 kernel's do).
-struct Msg32 {
-  float t, l;
-};
-
-__device__ __forceinline__ Msg32 merge32(const float2* part, int nsplit, int64_t stride) {
-  float Rm = -INFINITY;
-  for (int p = 0; p < nsplit; ++p) {
-    const float2 v = part[p * stride];
-    if (v.y > 0.f) Rm = fmaxf(Rm, v.x);
-  }
-  if (Rm == -INFINITY) return Msg32{-INFINITY, 0.f};
-  float S = 0.f;
-  for (int p = 0; p < nsplit; ++p) {
-    const float2 v = part[p * stride];
-    if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
-  }
-  if (!isfinite(S) || !(S > 0.f)) return Msg32{(S > 0.f) ? INFINITY : -INFINITY, 0.f};
-  int e;
-  const float mant = frexpf(S, &e);  // S = mant * 2^e, mant in [0.5, 1)
-  const float ef = (float)e;
-  const float t = Rm + ef;  // TwoSum: err is what t lost
-  const float bb = t - Rm;
-  const float err = (Rm - (t - bb)) + (ef - bb);
-  return Msg32{t, fmaf(err, kLn2f, logf(mant))};
-}
-
-// the message minus the neighbour's normaliser, in double
-__device__ __forceinline__ double msg_minus(const Msg32& mm, double Z) {
-  return fma((double)mm.t, kLn2, (double)mm.l - Z);
-}
-
 // frame of a message for the next apply: log2 of it on the 2^-10 grid (0 when not finite)
-__device__ __forceinline__ float frame32(const Msg32& mm) {
-  return isfinite(mm.t) ? quant(fmaf(mm.l, kLog2ef, mm.t)) : 0.f;
-}
-
 __device__ __forceinline__ float frame64(double m) {
   return isfinite(m) ? (float)(rint(m * (kLog2e * kGrid)) * (1.0 / kGrid)) : 0.f;
 }
@@ -116,9 +70,6 @@ __device__ __forceinline__ double merge64(const double2* part, int nsplit, int64
   return M + log(S);
 }
 
-// exp at FP32 accuracy (the argument scaled to log2 units in double, then rounded once)
-__device__ __forceinline__ float exp32(double a) { return ex2((float)(a * kLog2e)); }
-
 // block-wide sum / max of a double (kNodeThreads threads); result valid in all threads
 __device__ double block_sum(double v, double* red) {
   v = warp_sum_d(v);
@@ -144,26 +95,11 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-// merged message of pair (edge d, point x) minus Z_k; writes its frame
-template <bool F64>
-__device__ __forceinline__ double merge_pair(const NodeArgs& A, const DEdgeD& d, int n_owner, int x, double Zk) {
-  if constexpr (F64) {
-    const double mr = merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
-    A.fr[d.off + x] = frame64(mr);
-    return mr - Zk;
-  } else {
-    const Msg32 mm = merge32(A.part32 + d.part_off + x, d.nsplit, n_owner);
-    A.fr[d.off + x] = frame32(mm);
-    return msg_minus(mm, Zk);
-  }
-}
-
-template <typename Q>
-__device__ __forceinline__ Q warp_sum_q(Q v) {
-  if constexpr (sizeof(Q) == 8)
-    return warp_sum_d(v);
-  else
-    return warp_sum(v);
+// merged message of pair (edge d, point x) minus Z_k (FP64 partials); writes its frame
+__device__ __forceinline__ double merge_pair64(const NodeArgs& A, const DEdgeD& d, int n_owner, int x, double Zk) {
+  const double mr = merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
+  A.fr[d.off + x] = frame64(mr);
+  return mr - Zk;
 }
 
 // walks the pairs q = tid, tid + T, ... of a chunk of cnt points: (edge i, point xi)
@@ -185,12 +121,12 @@ struct PairWalk {
   }
 };
 
-template <bool F64>
-__device__ void chunk_update(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
-                             unsigned char* sm, int node_id) {
-  using Q = typename std::conditional<F64, double, float>::type;
+// FP64 handles: three passes over the chunk's pairs / points in double
+__device__ void chunk_update64(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
+                               unsigned char* sm, int node_id) {
+  using Q = double;
   const int deg = nd.deg, cnt = c.cnt, np = deg * cnt;
-  const NodeSmem L = node_smem_layout(deg, cnt, F64);
+  const NodeSmem L = node_smem_layout(deg, cnt, true);
   DEdgeD* s_de = reinterpret_cast<DEdgeD*>(sm + L.de);
   double* s_zn = reinterpret_cast<double*>(sm + L.zn);
   int* s_di = reinterpret_cast<int*>(sm + L.di);
@@ -221,17 +157,12 @@ __device__ void chunk_update(const NodeArgs& A, const NodeD& nd, const NodeChunk
     bool drift = false;
     for (int xi = tid; xi < cnt; xi += kNodeThreads) {
       const int x = c.x0 + xi;
-      const double mi = merge_pair<F64>(A, d, nd.n, x, s_zn[0]);
+      const double mi = merge_pair64(A, d, nd.n, x, s_zn[0]);
       const double fo = A.f[d.off + x];
       const double lg = A.logg[nd.node_off + x];
       const double mu = A.mu[nd.node_off + x];
       // stopping term mu |exp(f/eps + m) - 1| of the previous iterate
-      if (mu > 0.0) {
-        if constexpr (F64)
-          r += fabs(mu * exp(fo * P.inv_eps + mi) - mu);
-        else
-          r += (float)mu * fabsf(exp32(fma(fo, P.inv_eps, mi)) - 1.f);
-      }
+      if (mu > 0.0) r += fabs(mu * exp(fo * P.inv_eps + mi) - mu);
       A.f[d.off + x] = -P.eps * mi;
       float hi, lo;
       if (lg == -INFINITY) {
@@ -259,13 +190,10 @@ __device__ void chunk_update(const NodeArgs& A, const NodeD& nd, const NodeChunk
     for (int q = tid; q < np; q += kNodeThreads, w.next(cnt)) {
       const DEdgeD& d = s_de[w.i];
       const int x = c.x0 + w.xi;
-      const double mi = merge_pair<F64>(A, d, nd.n, x, s_zn[w.i]);
+      const double mi = merge_pair64(A, d, nd.n, x, s_zn[w.i]);
       s_mi[q] = mi;
       const double fo = A.f[d.off + x];
-      if constexpr (F64)
-        s_q[q] = exp((fo * P.inv_eps - Zold) + mi);
-      else
-        s_q[q] = exp32(fma(fo, P.inv_eps, mi - Zold));
+      s_q[q] = exp((fo * P.inv_eps - Zold) + mi);
     }
   }
   __syncthreads();
@@ -287,13 +215,8 @@ __device__ void chunk_update(const NodeArgs& A, const NodeD& nd, const NodeChunk
   }
   smax = block_max(smax, red);  // its barriers also publish s_s and s_qb
   Q se = Q(0);
-  for (int xi = tid; xi < cnt; xi += kNodeThreads) {
-    if constexpr (F64)
-      se += exp(s_s[xi] - smax);
-    else
-      se += exp32(s_s[xi] - smax);
-  }
-  const double sse = block_sum((double)se, red);
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) se += exp(s_s[xi] - smax);
+  const double sse = block_sum(se, red);
   if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2(smax, sse);
   // pass 3, pairs: f'_(j,k)/eps = s - m, the next apply's operand, |q_k - mean q|
   {
@@ -320,7 +243,194 @@ __device__ void chunk_update(const NodeArgs& A, const NodeD& nd, const NodeChunk
       // per-edge sums: one shared-memory atomic per warp when the warp's pairs share an edge
       const int i0 = __shfl_sync(0xffffffffu, i, 0);
       if (__all_sync(0xffffffffu, i == i0)) {
-        r = warp_sum_q(r);
+        r = warp_sum_d(r);
+        if (lane == 0 && i0 >= 0) atomicAdd(&s_r[i0], r);
+      } else if (on) {
+        atomicAdd(&s_r[i], r);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < deg; i += kNodeThreads) {
+    atomicAdd(&A.resid_acc[s_di[i]], (double)s_r[i]);
+    if (s_dr[i]) atomicOr(&A.drift[s_de[i].edge], 1);
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 handles: the same three passes in log2 units on two-float values (hi on
+// the 2^-10 grid, so sums and differences of hi parts are exact; lo small).
+// Messages come from the merge as t + l (t = frame + exponent, exact), the
+// normalisers Z as two-floats formed once per CTA, and the previous iterate's
+// exponent f/eps from the operand (hh + hl) the previous update wrote.  The
+// only FP64 arithmetic per pair forms the stored potential f = eps ln2 g.
+// ---------------------------------------------------------------------------
+
+// a value in log2 units as a two-float: hi on the grid, lo the rest
+__device__ __forceinline__ float2 split_l2(double v) {
+  if (!isfinite(v)) return make_float2((float)v, 0.f);
+  const float hi = quant((float)v);
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// the merged message in log2 units, m log2(e) = t + l with t on the grid
+__device__ __forceinline__ float2 merge32_l2(const float2* part, int nsplit, int64_t stride) {
+  float Rm = -INFINITY;
+  for (int p = 0; p < nsplit; ++p) {
+    const float2 v = part[p * stride];
+    if (v.y > 0.f) Rm = fmaxf(Rm, v.x);
+  }
+  if (Rm == -INFINITY) return make_float2(-INFINITY, 0.f);
+  float S = 0.f;
+  for (int p = 0; p < nsplit; ++p) {
+    const float2 v = part[p * stride];
+    if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
+  }
+  if (!isfinite(S) || !(S > 0.f)) return make_float2((S > 0.f) ? INFINITY : -INFINITY, 0.f);
+  int e;
+  const float mant = frexpf(S, &e);  // S = mant * 2^e, mant in [0.5, 1)
+  const float ef = (float)e;
+  const float t = Rm + ef;  // TwoSum: err is what t lost
+  const float bb = t - Rm;
+  const float err = (Rm - (t - bb)) + (ef - bb);
+  return make_float2(t, log2f(mant) + err);
+}
+
+// (hi, lo) of hi + lo with the grid part of lo moved into hi
+__device__ __forceinline__ float2 regrid(float hi, float lo) {
+  const float q = quant(lo);
+  return make_float2(hi + q, lo - q);
+}
+
+__device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
+                               unsigned char* sm, int node_id) {
+  const int deg = nd.deg, cnt = c.cnt, np = deg * cnt;
+  const NodeSmem L = node_smem_layout(deg, cnt, false);
+  DEdgeD* s_de = reinterpret_cast<DEdgeD*>(sm + L.de);
+  float2* s_zk = reinterpret_cast<float2*>(sm + L.zn);  // Z_k log2(e) as two-floats
+  int* s_di = reinterpret_cast<int*>(sm + L.di);
+  int* s_dr = reinterpret_cast<int*>(sm + L.dr);
+  float* s_r = reinterpret_cast<float*>(sm + L.r);
+  float2* s_mi = reinterpret_cast<float2*>(sm + L.mi);  // (m - Z_k) log2(e)
+  float* s_q = reinterpret_cast<float*>(sm + L.q);
+  float2* s_s = reinterpret_cast<float2*>(sm + L.s);    // s log2(e)
+  float* s_qb = reinterpret_cast<float*>(sm + L.qb);
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < deg; i += kNodeThreads) {
+    const int di = A.node_dedges[nd.dedge_begin + i];
+    const DEdgeD d = A.dedges[di];
+    s_de[i] = d;
+    s_zk[i] = split_l2(A.Z[d.nbr] * kLog2e);
+    s_di[i] = di;
+    s_dr[i] = 0;
+    s_r[i] = 0.f;
+  }
+  __syncthreads();
+  const bool track = A.absorbed && A.lowp[nd.prob] == 1;
+  const double eps_ln2 = P.eps * kLn2;
+  bool bad = false;
+
+  if (nd.fixed) {  // a leaf: one edge, one pass
+    const DEdgeD& d = s_de[0];
+    const float2 zk = s_zk[0];
+    float r = 0.f;
+    bool drift = false;
+    for (int xi = tid; xi < cnt; xi += kNodeThreads) {
+      const int x = c.x0 + xi;
+      const float2 mm = merge32_l2(A.part32 + d.part_off + x, d.nsplit, nd.n);
+      A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+      const float mh = mm.x - zk.x, ml = mm.y - zk.y;  // (m - Z_k) log2(e)
+      const float4 lg = A.lgf[nd.node_off + x];       // log2 mu (hi, lo), mu
+      const float oh = A.hh[d.off + x], ol = A.hl[d.off + x];
+      // stopping term mu |exp(f/eps + m) - 1| of the previous iterate; f/eps log2(e) = h - log2 mu
+      if (lg.z > 0.f) r += lg.z * fabsf(ex2(((oh - lg.x) + mh) + ((ol - lg.y) + ml)) - 1.f);
+      A.f[d.off + x] = -eps_ln2 * ((double)mh + (double)ml);
+      float2 h2;
+      if (lg.x == -INFINITY) {
+        h2 = make_float2(-INFINITY, 0.f);
+      } else {
+        h2 = regrid(lg.x - mh, lg.y - ml);
+        if (!isfinite(mh)) bad = true;
+      }
+      A.hh[d.off + x] = h2.x;
+      A.hl[d.off + x] = h2.y;
+      if (track && h2.x > -INFINITY && fabsf((h2.x - A.bh[d.off + x]) + (h2.y - A.bl[d.off + x])) > A.tau)
+        drift = true;
+    }
+    if (__syncthreads_or(drift) && tid == 0) atomicOr(&A.drift[d.edge], 1);
+    const double rs = block_sum((double)r, red);
+    if (tid == 0) atomicAdd(&A.resid_acc[s_di[0]], rs);
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
+    return;
+  }
+
+  const float2 zo = split_l2(A.Z[node_id] * kLog2e);
+  // pass 1, pairs: (m - Z_k) log2(e), its frame, and q_k = exp(f_(j,k)/eps + m_(j,k) - Z_j)
+  {
+    PairWalk w(cnt);
+    for (int q = tid; q < np; q += kNodeThreads, w.next(cnt)) {
+      const DEdgeD& d = s_de[w.i];
+      const int x = c.x0 + w.xi;
+      const float2 mm = merge32_l2(A.part32 + d.part_off + x, d.nsplit, nd.n);
+      A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+      const float2 zk = s_zk[w.i];
+      const float mh = mm.x - zk.x, ml = mm.y - zk.y;
+      s_mi[q] = make_float2(mh, ml);
+      const float oh = A.hh[d.off + x], ol = A.hl[d.off + x];  // f/eps log2(e) of the previous iterate
+      s_q[q] = ex2(((oh + mh) - zo.x) + ((ol + ml) - zo.y));
+    }
+  }
+  __syncthreads();
+  // pass 2, points: s = mean_k (m - Z_k), mean q, and the chunk's part of Z_j
+  const float fdeg = (float)deg, inv_deg = 1.f / fdeg;
+  float smax = -INFINITY;
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) {
+    float sh = 0.f, sl = 0.f, qsum = 0.f;
+    for (int i = 0; i < deg; ++i) {
+      const float2 v = s_mi[i * cnt + xi];
+      const float t = sh + v.x;  // TwoSum of the hi parts
+      const float bb = t - sh;
+      sl += ((sh - (t - bb)) + (v.x - bb)) + v.y;
+      sh = t;
+      qsum += s_q[i * cnt + xi];
+    }
+    const float mh = quant(sh * inv_deg);
+    const float ml = (fmaf(-mh, fdeg, sh) + sl) * inv_deg;
+    if (!isfinite(mh)) bad = true;
+    s_s[xi] = make_float2(mh, ml);
+    s_qb[xi] = qsum * inv_deg;
+    smax = fmaxf(smax, mh + ml);
+  }
+  smax = (float)block_max((double)smax, red);  // its barriers also publish s_s and s_qb
+  const float sq = isfinite(smax) ? quant(smax) : 0.f;
+  float se = 0.f;
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) se += ex2((s_s[xi].x - sq) + s_s[xi].y);
+  const double sse = block_sum((double)se, red);
+  if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2((double)sq * kLn2, sse);
+  // pass 3, pairs: g = s - (m - Z_k) (f'/eps in log2), the operand, f = eps ln2 g, |q_k - mean q|
+  {
+    PairWalk w(cnt);
+    for (int q0 = 0; q0 < np; q0 += kNodeThreads) {  // warp-uniform trip count
+      const int q = q0 + tid;
+      const bool on = q < np;
+      const int i = on ? w.i : -1;
+      float r = 0.f;
+      if (on) {
+        const DEdgeD& d = s_de[i];
+        const int x = c.x0 + w.xi;
+        const float2 mi = s_mi[q], sv = s_s[w.xi];
+        r = fabsf(s_q[q] - s_qb[w.xi]);
+        const float2 g = regrid(sv.x - mi.x, sv.y - mi.y);
+        A.f[d.off + x] = eps_ln2 * ((double)g.x + (double)g.y);
+        A.hh[d.off + x] = g.x;
+        A.hl[d.off + x] = g.y;
+        if (track && fabsf((g.x - A.bh[d.off + x]) + (g.y - A.bl[d.off + x])) > A.tau) s_dr[i] = 1;
+        w.next(cnt);
+      }
+      const int i0 = __shfl_sync(0xffffffffu, i, 0);
+      if (__all_sync(0xffffffffu, i == i0)) {
+        r = warp_sum(r);
         if (lane == 0 && i0 >= 0) atomicAdd(&s_r[i0], r);
       } else if (on) {
         atomicAdd(&s_r[i], r);
@@ -346,7 +456,12 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
   const int64_t t_now = *((volatile const int64_t*)A.hs);
   const int slot = (int)(t_now % kResidRing);
   const bool skip = A.done[p] != 0;
-  if (!skip) chunk_update<F64>(A, nd, c, P, red, node_sm, c.node);
+  if (!skip) {
+    if constexpr (F64)
+      chunk_update64(A, nd, c, P, red, node_sm, c.node);
+    else
+      chunk_update32(A, nd, c, P, red, node_sm, c.node);
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
   __threadfence();

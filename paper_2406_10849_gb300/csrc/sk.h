@@ -17,6 +17,7 @@
 // with K' and V' each split into two BF16 parts (hi + lo) and
 // S = K'hi V'hi + K'hi V'lo + K'lo V'hi accumulated in FP32 on the tensor cores.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the type only; the encoder is fetched through the runtime)
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -26,7 +27,8 @@ namespace treeot {
 
 constexpr int kSkTileM = 128;  // rows (x) per GEMM CTA
 constexpr int kSkTileN = 128;  // columns (directed edges) per GEMM CTA
-constexpr int kSkTileK = 32;   // reduction points (y) per stage
+constexpr int kSkTileK = 32;   // reduction points (y) per stage (mma.sync variant)
+constexpr int kSkPadK = 64;    // reduction length padding (a multiple of both products' stages)
 
 // Outputs whose sum S(x,j) falls below 2^-96 (the column's message more than
 // ~96 binades under the row frame R(x), where its terms' factors may have left
@@ -46,7 +48,8 @@ struct SkArgs {
   const SkCol* cols;
   int32_t ncols;
   int32_t nx, ny, dim;
-  int32_t mp, kd;         // rows padded to kSkTileM, reduction length padded to kSkTileK
+  int32_t mp, kd;         // rows padded to kSkTileM, reduction length padded to kSkPadK
+  int32_t use_tc;         // 1: tcgen05 product (tensor memory accumulators), 0: mma.sync
   const float* hh;
   const float* hl;
   const int32_t* done;
@@ -64,10 +67,21 @@ struct SkArgs {
   float2* part32;
   int32_t* fix_count;     // outputs listed for the exact fix-up (reset by the envelope launch)
   int2* fix_list;         // (x, column), capacity nx * ncols
+  int32_t* err;           // error word: bit 1 = a bounded wait of the tcgen05 product ran out
 };
 
+// tensor maps of the tcgen05 product's operands (128 x 64 BF16 boxes, 128-byte swizzle)
+struct SkMaps {
+  CUtensorMap khi, klo, vhi, vlo;
+};
+// fills `m` for the operands of `a`; false when the driver cannot encode them
+bool sk_encode_maps(const SkArgs& a, SkMaps* m);
+
+// whether the tcgen05 product can run on the current device
+bool sk_tc_available();
+
 // the five launches of one group and colour (nothing to do when ncols == 0)
-cudaError_t launch_sk(const SkArgs& a, cudaStream_t s);
+cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s);
 // b := -inf (once at create; afterwards each product resets it)
 cudaError_t launch_sk_reset(float* b, int32_t kd, cudaStream_t s);
 

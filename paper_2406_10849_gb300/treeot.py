@@ -246,12 +246,14 @@ class _Marshalled:
 
 def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, check_every=32, use_graph=True,
             apply_mode="auto", refine_tol=None, absorb_tau=None, lowp_start=None, autotune=None,
-            dense_kernel="auto", exact_dist=False, transpose=True, test_stall=False) -> Options:
+            dense_kernel="auto", exact_dist=False, transpose=True, test_stall=False, sk_product="auto") -> Options:
     """tree_ot_options with the defaults of tree_ot_default_options; dense_kernel picks the
     stored-cost apply ("auto": the autotuner's choice, "tma": bulk-copy staged, "ldg": plain loads);
     exact_dist: recompute squared distances exactly from the first half-step;
     transpose: keep stored costs also transposed when the device has room;
-    test_stall: test hook, the staged kernel's producer issues nothing (its waits run out)."""
+    test_stall: test hook, the staged kernel's producer issues nothing (its waits run out);
+    sk_product: the shared-kernel BF16 phase's product ("auto": tcgen05 where available,
+    "mma": the legacy mma.sync kernel)."""
     load()
     o = Options()
     _lib.tree_ot_default_options(C.byref(o))
@@ -271,7 +273,7 @@ def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, c
     if autotune is not None:
         o.autotune = 1 if autotune else 0
     o.flags = ({"auto": 0, "tma": 1, "ldg": 2}[dense_kernel] | (4 if exact_dist else 0) | (0 if transpose else 8)
-               | (16 if test_stall else 0))
+               | (16 if test_stall else 0) | {"auto": 0, "mma": 32}[sk_product])
     return o
 
 

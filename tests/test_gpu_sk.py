@@ -96,3 +96,18 @@ def test_mixed_batch(T):
     assert rc == 0, [(p.name, r["status"], r["max_marginal_l1"], r["half_steps"], r["lowp_half_steps"])
                      for p, r in zip(probs, res)]
     assert [r["lowp_half_steps"] > 0 for r in res] == [True] * 7 + [False]
+
+
+def test_tensor_memory_product_matches_mma_sync(T):
+    """The tcgen05 product (tensor-memory accumulators) and the mma.sync product
+    form the same split-BF16 sums in a different order: 40 stars (320 columns
+    per colour, a ragged third column tile, two row tiles) agree after six
+    half-steps."""
+    probs = stars(40, side=16, eps=0.01, seed=7_400_000)
+    got = {}
+    for prod in ("auto", "mma"):
+        with T.Solver(probs, T.options(apply_mode="bf16", lowp_start=0, refine_tol=0.0, sk_product=prod)) as s:
+            s.half_steps(6)
+            got[prod] = [s.potentials(i) for i in (0, 17, 39)]
+    for a, b, i in zip(got["auto"], got["mma"], (0, 17, 39)):
+        assert rel_err(a, b, probs[i].eps) <= 1e-5
