@@ -19,7 +19,7 @@ SOURCES = ["api.cpp", "mlp_api.cpp", "apply_f32.cu", "apply_bf16.cu", "apply_tma
            "node_update.cu",
            "check.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-Xcompiler", "-pthread",
          f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
 
 
@@ -63,7 +63,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
     if force or procs or _stale(LIB, objs):
-        cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs]
+        cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", LIB, *objs]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)

@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -693,8 +694,28 @@ inline double true_f(const tree_ot_handle* h, const DEdgeD& d, int32_t x) {
   return h->h_f[d.off + x] - h->probs[d.prob].eps * h->h_Z[d.owner];
 }
 
+void fill_result(tree_ot_handle* h, tree_ot_result* res, int p);
+
+// per-problem results from the check's marginals; problems are independent, so
+// large batches are split across host threads
 void fill_results(tree_ot_handle* h, tree_ot_result* res) {
-  for (int p = 0; p < h->nprob; ++p) {
+  const int64_t work = h->vec_len;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = (int)std::min<int64_t>({(int64_t)(hw == 0 ? 1 : hw), 16, (int64_t)h->nprob, work / (1 << 18) + 1});
+  if (nt <= 1) {
+    for (int p = 0; p < h->nprob; ++p) fill_result(h, res, p);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([h, res, t, nt] {
+      for (int p = t; p < h->nprob; p += nt) fill_result(h, res, p);
+    });
+  for (auto& th : pool) th.join();
+}
+
+void fill_result(tree_ot_handle* h, tree_ot_result* res, int p) {
+  {
     tree_ot_result r{};
     const ProbD& P = h->probs[p];
     double rsum = 0.0, rmax = 0.0, tc = 0.0, pr = 0.0, du = 0.0, mass_total = 0.0;

@@ -21,18 +21,21 @@ struct DF {
   float hi, lo;
 };
 
+// The error-free transformations below use the _rn intrinsics, which the
+// compiler never contracts into FMAs: a product fused into a neighbouring
+// addition would no longer be the rounded value the error term was taken from.
 __device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  const float e = (a - (s - bb)) + (b - bb);
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
   return {s, e};
 }
 
 // exact-ish square of (p - q) as a double-float
 __device__ __forceinline__ DF sq_diff(float p, float q) {
   const DF d = two_sum(p, -q);
-  const float h = d.hi * d.hi;
-  const float e = fmaf(d.hi, d.hi, -h) + 2.f * d.hi * d.lo;
+  const float h = __fmul_rn(d.hi, d.hi);
+  const float e = fmaf(2.f * d.hi, d.lo, fmaf(d.hi, d.hi, -h));
   return {h, e};
 }
 
@@ -55,7 +58,7 @@ __device__ __forceinline__ DF cost_df(const CheckArgs& A, const EdgeD& e, const 
 __device__ __forceinline__ float plan_entry(float ah, float al, float bh, float bl, DF c, float kh, float kl,
                                             float& cost_out) {
   const DF s = two_sum(ah, bh);
-  const float p = c.hi * kh;
+  const float p = __fmul_rn(c.hi, kh);  // the rounded product; pe holds what it lost
   const float pe = fmaf(c.hi, kl, fmaf(c.lo, kh, fmaf(c.hi, kh, -p)));
   const DF d = two_sum(s.hi, -p);
   const float lo = (s.lo + d.lo) + (al + bl) - pe;
@@ -64,100 +67,105 @@ __device__ __forceinline__ float plan_entry(float ah, float al, float bh, float 
   return E == 0.f ? 0.f : E * (1.f + lo);
 }
 
+// One pass over every plan entry.  A ROW task covers up to 64 rows of an edge
+// (8 warps x 8 rows); the warps walk the columns together, 32 at a time (a lane
+// per column), and evaluate each entry once: row sums (and the transport cost)
+// stay in the lanes' registers until the task ends, column sums are combined
+// across the warps in shared memory and added to the column marginal with one
+// FP64 atomic per column and task.  Sums inside a task use Kahan compensation.
+// COL tasks belong to the FP64 check and are skipped here.
+constexpr int kChkRows = 8;  // rows per warp
+
 __global__ void __launch_bounds__(256) check_kernel(CheckArgs A) {
-  __shared__ float sbh[256], sbl[256];
-  __shared__ float sq[256 * 3];
+  __shared__ float s_col[8][32];
+  __shared__ float s_cmp[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
+    if (t.kind != TASK_ROW) continue;  // block-uniform
     const DEdgeD d = A.dedges[t.dedge];
     if (A.mask && !A.mask[d.prob]) continue;  // block-uniform
     const EdgeD e = A.edges[d.edge];
     const ProbD P = A.probs[d.prob];
     const double kd = (P.cost_kind == 0 ? 1.0 : P.cost_scale) * P.inv_eps;
     const float kh = (float)kd, kl = (float)(kd - (double)kh);
+    const float cscale = P.cost_kind == 0 ? 1.f : (float)P.cost_scale;
     const NodeD na = A.nodes[e.a], nb = A.nodes[e.b];
     // a-side operand: rows (owner a, dedge 2e) ; b-side: columns (owner b, dedge 2e+1)
     const int64_t a_off = d.dir == 0 ? d.off : d.rev_off;
     const int64_t b_off = d.dir == 0 ? d.rev_off : d.off;
     const int D = P.dim;
+    // this warp's rows
+    float rah[kChkRows], ral[kChkRows], rp[kChkRows][3];
+    float rs[kChkRows], rc[kChkRows], ts[kChkRows], tcmp[kChkRows];
+#pragma unroll
+    for (int r = 0; r < kChkRows; ++r) {
+      const int xr = warp * kChkRows + r;
+      const bool on = xr < t.ocount;
+      const int x = t.o0 + (on ? xr : 0);
+      rah[r] = on ? A.ah[a_off + x] : -INFINITY;
+      ral[r] = on ? A.al[a_off + x] : 0.f;
+      for (int k = 0; k < 3; ++k) rp[r][k] = (na.coord_off >= 0 && k < D) ? A.coords[na.coord_off + (int64_t)x * D + k] : 0.f;
+      rs[r] = rc[r] = ts[r] = tcmp[r] = 0.f;
+    }
+    for (int y0 = 0; y0 < e.nb; y0 += 32) {
+      const int y = y0 + lane;
+      const bool on = y < e.nb;
+      const float bh = on ? A.ah[b_off + y] : -INFINITY;
+      const float bl = on ? A.al[b_off + y] : 0.f;
+      float pb[3] = {0.f, 0.f, 0.f};
+      if (on && nb.coord_off >= 0)
+        for (int k = 0; k < D; ++k) pb[k] = A.coords[nb.coord_off + (int64_t)y * D + k];
+      float cs = 0.f, cc = 0.f;  // this column's sum over the warp's rows (Kahan)
+      if (bh > -INFINITY) {
+#pragma unroll
+        for (int r = 0; r < kChkRows; ++r) {
+          if (!(rah[r] > -INFINITY)) continue;
+          const int x = t.o0 + warp * kChkRows + r;
+          float cst;
+          const float B = plan_entry(rah[r], ral[r], bh, bl, cost_df(A, e, P, x, y, rp[r], pb), kh, kl, cst);
+          float y1 = B - rc[r];
+          float t1 = rs[r] + y1;
+          rc[r] = (t1 - rs[r]) - y1;
+          rs[r] = t1;
+          const float cb = cst * cscale * B;
+          y1 = cb - tcmp[r];
+          t1 = ts[r] + y1;
+          tcmp[r] = (t1 - ts[r]) - y1;
+          ts[r] = t1;
+          y1 = B - cc;
+          t1 = cs + y1;
+          cc = (t1 - cs) - y1;
+          cs = t1;
+        }
+      }
+      s_col[warp][lane] = cs;
+      s_cmp[warp][lane] = cc;
+      __syncthreads();
+      if (warp == 0 && on) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v += (double)s_col[w][lane] - (double)s_cmp[w][lane];
+        if (v != 0.0) atomicAdd(&A.marg[b_off + y], v);
+      }
+      __syncthreads();
+    }
     double tc_acc = 0.0, mass_acc = 0.0;
-    if (t.kind == TASK_ROW) {
-      // warp per row x in [o0, o0+ocount) of node a; lanes stride the columns
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int r = warp; r < t.ocount; r += 8) {
-        const int x = t.o0 + r;
-        const float ah = A.ah[a_off + x], al = A.al[a_off + x];
-        const float* pa = A.coords + (na.coord_off >= 0 ? na.coord_off + (int64_t)x * D : 0);
-        float sum = 0.f, comp = 0.f, tcs = 0.f, tcc = 0.f;
-        if (ah > -INFINITY) {
-          for (int y = lane; y < e.nb; y += 32) {
-            const float* pb = A.coords + (nb.coord_off >= 0 ? nb.coord_off + (int64_t)y * D : 0);
-            const float bh = A.ah[b_off + y], bl = A.al[b_off + y];
-            if (!(bh > -INFINITY)) continue;
-            float cst;
-            const float B = plan_entry(ah, al, bh, bl, cost_df(A, e, P, x, y, pa, pb), kh, kl, cst);
-            // Kahan sums
-            const float y1 = B - comp;
-            const float t1 = sum + y1;
-            comp = (t1 - sum) - y1;
-            sum = t1;
-            const float cb = (P.cost_kind == 0 ? cst : cst * (float)P.cost_scale) * B;
-            const float y2 = cb - tcc;
-            const float t2 = tcs + y2;
-            tcc = (t2 - tcs) - y2;
-            tcs = t2;
-          }
-        }
-        const double rs = warp_sum_d((double)sum - (double)comp);
-        const double tr = warp_sum_d((double)tcs - (double)tcc);
-        if (lane == 0) {
-          A.marg[a_off + x] = rs;
-          tc_acc += tr;
-          mass_acc += rs;
-        }
-      }
-    } else {
-      // thread per column y in [o0, o0+ocount) of node b; rows staged by 256
-      const int ycol = t.o0 + threadIdx.x;
-      const bool on = threadIdx.x < t.ocount;
-      const float bh = on ? A.ah[b_off + ycol] : -INFINITY;
-      const float bl = on ? A.al[b_off + ycol] : 0.f;
-      const float* pb = A.coords + ((nb.coord_off >= 0 && on) ? nb.coord_off + (int64_t)ycol * D : 0);
-      float sum = 0.f, comp = 0.f;
-      for (int x0 = 0; x0 < e.na; x0 += 256) {
-        __syncthreads();
-        const int xl = x0 + threadIdx.x;
-        if (xl < e.na) {
-          sbh[threadIdx.x] = A.ah[a_off + xl];
-          sbl[threadIdx.x] = A.al[a_off + xl];
-          if (na.coord_off >= 0)
-            for (int k = 0; k < D; ++k) sq[threadIdx.x * 3 + k] = A.coords[na.coord_off + (int64_t)xl * D + k];
-        }
-        __syncthreads();
-        const int cnt = min(256, e.na - x0);
-        if (on && bh > -INFINITY) {
-          for (int i = 0; i < cnt; ++i) {
-            const float ahx = sbh[i];
-            if (!(ahx > -INFINITY)) continue;
-            float cst;
-            const float B = plan_entry(ahx, sbl[i], bh, bl, cost_df(A, e, P, x0 + i, ycol, sq + 3 * i, pb), kh,
-                                       kl, cst);
-            const float y1 = B - comp;
-            const float t1 = sum + y1;
-            comp = (t1 - sum) - y1;
-            sum = t1;
-          }
-        }
-      }
-      if (on) A.marg[b_off + ycol] = (double)sum - (double)comp;
-    }
-    if (t.kind == TASK_ROW) {
-      if ((threadIdx.x & 31) == 0 && (tc_acc != 0.0 || mass_acc != 0.0)) {
-        atomicAdd(&A.edge_tc[d.edge], tc_acc);
-        atomicAdd(&A.edge_mass[d.edge], mass_acc);
+#pragma unroll
+    for (int r = 0; r < kChkRows; ++r) {
+      const int xr = warp * kChkRows + r;
+      const double row = warp_sum_d((double)rs[r] - (double)rc[r]);
+      const double tr = warp_sum_d((double)ts[r] - (double)tcmp[r]);
+      if (lane == 0 && xr < t.ocount) {
+        A.marg[a_off + t.o0 + xr] = row;
+        tc_acc += tr;
+        mass_acc += row;
       }
     }
-    __syncthreads();
+    if (lane == 0 && (tc_acc != 0.0 || mass_acc != 0.0)) {
+      atomicAdd(&A.edge_tc[d.edge], tc_acc);
+      atomicAdd(&A.edge_mass[d.edge], mass_acc);
+    }
   }
 }
 
