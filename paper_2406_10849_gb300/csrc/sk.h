@@ -74,7 +74,7 @@ struct SkArgs {
 struct SkMaps {
   CUtensorMap khi, klo, vhi, vlo;
 };
-// fills `m` for the operands of `a`; false when the driver cannot encode them
+// fills `m` for the operands of `a`; false when cuTensorMapEncodeTiled is unavailable or refuses them
 bool sk_encode_maps(const SkArgs& a, SkMaps* m);
 
 // whether the tcgen05 product can run on the current device
