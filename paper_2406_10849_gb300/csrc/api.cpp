@@ -265,6 +265,7 @@ struct tree_ot_handle {
   int sms = 1;
 
   bool have_check = false;
+  bool f_stale = false;  // FP32 handles: the node update has advanced the operand past d_f
   std::vector<double> h_marg, h_f, h_Z, h_rho, h_tc, h_mass;
   std::vector<int32_t> h_done;
   std::vector<int64_t> h_done_at;
@@ -512,6 +513,17 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
 int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
   cudaError_t e = launch_node_update(node_args(h, colour, retire), h->fp64, s);
   if (e != cudaSuccess) return cuda_fail(e, "node update launch");
+  if (!h->fp64) h->f_stale = true;
+  return TREE_OT_OK;
+}
+
+// d_f up to date before anything reads or partly overwrites it (FP32 handles
+// keep the potentials in the operand between node updates)
+int sync_potentials(tree_ot_handle* h, cudaStream_t s) {
+  if (!h->f_stale) return TREE_OT_OK;
+  CUDA_TRY(launch_materialise_f(h->d_dedges, (int32_t)h->dedges.size(), h->d_nodes, h->d_probs, h->d_lgf, h->d_hh,
+                                h->d_hl, h->d_f, s));
+  h->f_stale = false;
   return TREE_OT_OK;
 }
 
@@ -566,6 +578,7 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
   // apply operand of u = 1: h = log gamma * log2(e)
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, (int32_t)h->dedges.size(),
                           kLog2e, true, h->d_hh, h->d_hl, s));
+  h->f_stale = false;
   // phase of every problem: absorbed BF16 phase (1), waiting for it (2), or FP32 (0)
   CUDA_TRY(cudaMemsetAsync(h->d_absorb_count, 0, sizeof(unsigned long long), s));
   {
@@ -633,6 +646,7 @@ int run_check(tree_ot_handle* h, cudaStream_t s, const std::vector<int32_t>* onl
     keep_mass = h->h_mass;
     CUDA_TRY(cudaMemcpyAsync(h->d_chk_mask, only->data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
   }
+  RC_TRY(sync_potentials(h, s));
   CUDA_TRY(launch_operand(h->d_f, h->d_Z, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, nd, 1.0, false, h->d_ah,
                           h->d_al, s));
   CUDA_TRY(cudaMemsetAsync(h->d_edge_tc, 0, sizeof(double) * h->edges.size(), s));
@@ -1028,7 +1042,7 @@ int plan_shared_kernels(tree_ot_handle* h, const tree_ot_problem* probs, int32_t
   for (size_t di = 0; di < h->dedges.size(); ++di) {
     const DEdgeD& d = h->dedges[di];
     if (!ok[d.prob]) continue;
-    h->sk[dgroup[di]].cols[h->nodes[d.owner].colour].push_back(SkCol{d.rev_off, d.part_off, d.prob, d.nsplit});
+    h->sk[dgroup[di]].cols[h->nodes[d.owner].colour].push_back(SkCol{d.rev_off, d.part_off, d.prob});
   }
   std::vector<tree_ot_handle::SkGroup> kept;
   for (auto& g : h->sk)
@@ -1659,6 +1673,7 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
       if (use_graph && left >= G) {
         CUDA_TRY(cudaGraphLaunch(h->graph, s));
         h->hs_host += G;
+        h->f_stale = !h->fp64;
       } else {
         RC_TRY(queue_half_steps(h, std::min<int64_t>(G, left), true, s));
       }
@@ -1823,6 +1838,7 @@ int tree_ot_get_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, i
   const DEdgeD& d = h->dedges[2 * h->prob_edge_base[prob] + dedge];
   const int32_t n = h->nodes[d.owner].n;
   double z = 0.0;
+  RC_TRY(sync_potentials(h, s));
   CUDA_TRY(cudaMemcpyAsync(out, h->d_f + d.off, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(&z, h->d_Z + d.owner, sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1847,6 +1863,7 @@ int tree_ot_set_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, i
   std::vector<double> v(in, in + n);
   const double eps = h->probs[prob].eps;
   for (int32_t x = 0; x < n; ++x) v[x] += eps * z;
+  RC_TRY(sync_potentials(h, s));
   CUDA_TRY(cudaMemcpyAsync(h->d_f + d.off, v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges + di, h->d_nodes, h->d_probs, 1, kLog2e, true,
                           h->d_hh, h->d_hl, s));
@@ -1898,6 +1915,7 @@ int tree_ot_get_potentials_batch(tree_ot_handle* h, void* cuda_stream, int32_t c
   int32_t* d_dlist = nullptr;
   DEdgeD* d_picked = nullptr;
   RC_TRY(stage_items(h, s, count, probs, dedges, ld, &d_dlist, &d_picked));
+  RC_TRY(sync_potentials(h, s));
   CUDA_TRY(launch_get_potentials(d_dlist, count, h->d_dedges, h->d_nodes, h->d_probs, h->d_Z, h->d_f, values, ld,
                                  (flags & TREE_OT_GET_CENTRED) != 0, s));
   return TREE_OT_OK;
@@ -1920,6 +1938,7 @@ int tree_ot_set_potentials_batch(tree_ot_handle* h, void* cuda_stream, int32_t c
   CUDA_TRY(cudaMemcpyAsync(&bad, h->d_scan, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (bad) return fail(TREE_OT_ERR_NONFINITE, "potential entries must be finite");
+  RC_TRY(sync_potentials(h, s));
   CUDA_TRY(launch_set_potentials(values, ld, d_dlist, count, h->d_dedges, h->d_nodes, h->d_probs, h->d_Z, h->d_f,
                                  d_picked, h->d_scan, true, s));
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, d_picked, h->d_nodes, h->d_probs, count, kLog2e, true, h->d_hh,

@@ -293,7 +293,6 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
           continue;
         }
         A.part32[col.part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
-        for (int sp = 1; sp < col.nsplit; ++sp) A.part32[col.part_off + (int64_t)sp * A.nx + x] = make_float2(0.f, 0.f);
       }
 }
 
@@ -519,8 +518,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           continue;
         }
         A.part32[col.part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
-        for (int sp = 1; sp < col.nsplit; ++sp)
-          A.part32[col.part_off + (int64_t)sp * A.nx + x] = make_float2(0.f, 0.f);
       }
     }
   }
@@ -558,10 +555,7 @@ __global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
       }
       S = warp_sum(S);
     }
-    if (lane == 0) {
-      A.part32[col.part_off + x] = make_float2(R, S);
-      for (int sp = 1; sp < col.nsplit; ++sp) A.part32[col.part_off + (int64_t)sp * A.nx + x] = make_float2(0.f, 0.f);
-    }
+    if (lane == 0) A.part32[col.part_off + x] = make_float2(R, S);
   }
 }
 

@@ -280,6 +280,9 @@ bool apply_tma_available();
 cudaError_t launch_apply_tma(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_apply_f64(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s);
+// FP32 handles: the stored potentials f from the operand (hh, hl) and log2 mu
+cudaError_t launch_materialise_f(const DEdgeD* dedges, int32_t ndedges, const NodeD* nodes, const ProbD* probs,
+                                 const float4* lgf, const float* hh, const float* hl, double* f, cudaStream_t s);
 // v = (f'/eps - Z_owner + log gamma) * scale as FP32 (hi, lo); Z may be null.
 // quantize: hi on the 2^-10 grid (the apply operand), else hi = nearest float.
 cudaError_t launch_set_potentials(const float* values, int64_t ld, const int32_t* dlist, int32_t count,

@@ -24,6 +24,7 @@
 // the last chunk of a node merges Z_j and the node's stopping terms, the last
 // node of a problem records the stopping quantity and (when asked) retires the
 // problem, the last CTA of the launch advances the half-step counter.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -264,7 +265,10 @@ __device__ void chunk_update64(const NodeArgs& A, const NodeD& nd, const NodeChu
 // Messages come from the merge as t + l (t = frame + exponent, exact), the
 // normalisers Z as two-floats formed once per CTA, and the previous iterate's
 // exponent f/eps from the operand (hh + hl) the previous update wrote.  The
-// only FP64 arithmetic per pair forms the stored potential f = eps ln2 g.
+// stored potentials f are not written here: the operand holds them exactly
+// (f = eps ln2 (hh + hl), minus eps log mu on a fixed node), and
+// materialise_f_kernel forms them in FP64 when they are read.  Only points of
+// a fixed node with mu = 0, whose operand is -inf, keep f written per update.
 // ---------------------------------------------------------------------------
 
 // a value in log2 units as a two-float: hi on the grid, lo the rest
@@ -274,17 +278,32 @@ __device__ __forceinline__ float2 split_l2(double v) {
   return make_float2(hi, (float)(v - (double)hi));
 }
 
+// the first two partials of a pair (frame, sum), loaded ahead of the merge so
+// that a thread keeps several pairs' loads in flight
+struct Part2 {
+  float2 a, b;
+};
+__device__ __forceinline__ Part2 load_part2(const float2* part, int nsplit, int64_t stride) {
+  Part2 v;
+  v.a = part[0];
+  v.b = nsplit > 1 ? part[stride] : make_float2(0.f, 0.f);
+  return v;
+}
+
 // the merged message in log2 units, m log2(e) = t + l with t on the grid
-__device__ __forceinline__ float2 merge32_l2(const float2* part, int nsplit, int64_t stride) {
+// (pieces 0 and 1 from v, the rest read from part)
+__device__ __forceinline__ float2 merge32_l2(const Part2& v01, const float2* part, int nsplit, int64_t stride) {
   float Rm = -INFINITY;
-  for (int p = 0; p < nsplit; ++p) {
+  if (v01.a.y > 0.f) Rm = v01.a.x;
+  if (v01.b.y > 0.f) Rm = fmaxf(Rm, v01.b.x);
+  for (int p = 2; p < nsplit; ++p) {
     const float2 v = part[p * stride];
     if (v.y > 0.f) Rm = fmaxf(Rm, v.x);
   }
   if (Rm == -INFINITY) return make_float2(-INFINITY, 0.f);
   float S = 0.f;
   for (int p = 0; p < nsplit; ++p) {
-    const float2 v = part[p * stride];
+    const float2 v = p == 0 ? v01.a : p == 1 ? v01.b : part[p * stride];
     if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
   }
   if (!isfinite(S) || !(S > 0.f)) return make_float2((S > 0.f) ? INFINITY : -INFINITY, 0.f);
@@ -327,36 +346,58 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
     s_r[i] = 0.f;
   }
   __syncthreads();
-  const bool track = A.absorbed && A.lowp[nd.prob] == 1;
-  const double eps_ln2 = P.eps * kLn2;
+  // the shared-kernel phase leaves one partial per output; drift from an
+  // absorbed base is tracked on stored-cost problems, the only ones absorbed
+  const int lp = A.absorbed ? A.lowp[nd.prob] : 0;
+  const bool track = lp == 1 && P.cost_kind == 0;
+  const bool one_piece = lp == 1 && P.cost_kind != 0;
   bool bad = false;
+  // a thread loads all its pairs of a pass before it stores anything (at most
+  // kIt pairs per thread, as a chunk holds at most kNodePairs pairs)
+  constexpr int kIt = kNodePairs / kNodeThreads;
 
   if (nd.fixed) {  // a leaf: one edge, one pass
     const DEdgeD& d = s_de[0];
     const float2 zk = s_zk[0];
+    const int ns = one_piece ? 1 : d.nsplit;
+    const double eps_ln2 = P.eps * kLn2;
     float r = 0.f;
     bool drift = false;
-    for (int xi = tid; xi < cnt; xi += kNodeThreads) {
-      const int x = c.x0 + xi;
-      const float2 mm = merge32_l2(A.part32 + d.part_off + x, d.nsplit, nd.n);
-      A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
-      const float mh = mm.x - zk.x, ml = mm.y - zk.y;  // (m - Z_k) log2(e)
-      const float4 lg = A.lgf[nd.node_off + x];       // log2 mu (hi, lo), mu
-      const float oh = A.hh[d.off + x], ol = A.hl[d.off + x];
-      // stopping term mu |exp(f/eps + m) - 1| of the previous iterate; f/eps log2(e) = h - log2 mu
-      if (lg.z > 0.f) r += lg.z * fabsf(ex2(((oh - lg.x) + mh) + ((ol - lg.y) + ml)) - 1.f);
-      A.f[d.off + x] = -eps_ln2 * ((double)mh + (double)ml);
-      float2 h2;
-      if (lg.x == -INFINITY) {
-        h2 = make_float2(-INFINITY, 0.f);
-      } else {
-        h2 = regrid(lg.x - mh, lg.y - ml);
-        if (!isfinite(mh)) bad = true;
+    for (int xb = 0; xb < cnt; xb += kIt * kNodeThreads) {
+      Part2 pv[kIt];
+      float4 lg[kIt];
+      float oh[kIt], ol[kIt];
+#pragma unroll
+      for (int k = 0; k < kIt; ++k) {
+        const int x = c.x0 + min(xb + tid + k * kNodeThreads, cnt - 1);  // past the end: reload the last point
+        pv[k] = load_part2(A.part32 + d.part_off + x, ns, nd.n);
+        lg[k] = A.lgf[nd.node_off + x];  // log2 mu (hi, lo), mu
+        oh[k] = A.hh[d.off + x];
+        ol[k] = A.hl[d.off + x];
       }
-      A.hh[d.off + x] = h2.x;
-      A.hl[d.off + x] = h2.y;
-      if (track && h2.x > -INFINITY && fabsf((h2.x - A.bh[d.off + x]) + (h2.y - A.bl[d.off + x])) > A.tau)
-        drift = true;
+#pragma unroll
+      for (int k = 0; k < kIt; ++k) {
+        const int xi = xb + tid + k * kNodeThreads;
+        if (xi >= cnt) break;
+        const int x = c.x0 + xi;
+        const float2 mm = merge32_l2(pv[k], A.part32 + d.part_off + x, ns, nd.n);
+        A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+        const float mh = mm.x - zk.x, ml = mm.y - zk.y;  // (m - Z_k) log2(e)
+        // stopping term mu |exp(f/eps + m) - 1| of the previous iterate; f/eps log2(e) = h - log2 mu
+        if (lg[k].z > 0.f) r += lg[k].z * fabsf(ex2(((oh[k] - lg[k].x) + mh) + ((ol[k] - lg[k].y) + ml)) - 1.f);
+        float2 h2;
+        if (lg[k].x == -INFINITY) {
+          A.f[d.off + x] = -eps_ln2 * ((double)mh + (double)ml);  // mu = 0: the operand cannot carry f
+          h2 = make_float2(-INFINITY, 0.f);
+        } else {
+          h2 = regrid(lg[k].x - mh, lg[k].y - ml);
+          if (!isfinite(mh)) bad = true;
+        }
+        A.hh[d.off + x] = h2.x;
+        A.hl[d.off + x] = h2.y;
+        if (track && h2.x > -INFINITY && fabsf((h2.x - A.bh[d.off + x]) + (h2.y - A.bl[d.off + x])) > A.tau)
+          drift = true;
+      }
     }
     if (__syncthreads_or(drift) && tid == 0) atomicOr(&A.drift[d.edge], 1);
     const double rs = block_sum((double)r, red);
@@ -369,16 +410,35 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   // pass 1, pairs: (m - Z_k) log2(e), its frame, and q_k = exp(f_(j,k)/eps + m_(j,k) - Z_j)
   {
     PairWalk w(cnt);
-    for (int q = tid; q < np; q += kNodeThreads, w.next(cnt)) {
-      const DEdgeD& d = s_de[w.i];
-      const int x = c.x0 + w.xi;
-      const float2 mm = merge32_l2(A.part32 + d.part_off + x, d.nsplit, nd.n);
-      A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
-      const float2 zk = s_zk[w.i];
-      const float mh = mm.x - zk.x, ml = mm.y - zk.y;
-      s_mi[q] = make_float2(mh, ml);
-      const float oh = A.hh[d.off + x], ol = A.hl[d.off + x];  // f/eps log2(e) of the previous iterate
-      s_q[q] = ex2(((oh + mh) - zo.x) + ((ol + ml) - zo.y));
+    for (int qb = 0; qb < np; qb += kIt * kNodeThreads) {
+      Part2 pv[kIt];
+      float oh[kIt], ol[kIt];
+      int pi[kIt], px[kIt];
+#pragma unroll
+      for (int k = 0; k < kIt; ++k) {
+        const bool on = qb + tid + k * kNodeThreads < np;
+        pi[k] = on ? w.i : 0;  // past the end: reload pair (0, 0)
+        px[k] = on ? w.xi : 0;
+        if (on) w.next(cnt);
+        const DEdgeD& d = s_de[pi[k]];
+        const int x = c.x0 + px[k];
+        pv[k] = load_part2(A.part32 + d.part_off + x, one_piece ? 1 : d.nsplit, nd.n);
+        oh[k] = A.hh[d.off + x];  // f/eps log2(e) of the previous iterate
+        ol[k] = A.hl[d.off + x];
+      }
+#pragma unroll
+      for (int k = 0; k < kIt; ++k) {
+        const int q = qb + tid + k * kNodeThreads;
+        if (q >= np) break;
+        const DEdgeD& d = s_de[pi[k]];
+        const int x = c.x0 + px[k];
+        const float2 mm = merge32_l2(pv[k], A.part32 + d.part_off + x, one_piece ? 1 : d.nsplit, nd.n);
+        A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+        const float2 zk = s_zk[pi[k]];
+        const float mh = mm.x - zk.x, ml = mm.y - zk.y;
+        s_mi[q] = make_float2(mh, ml);
+        s_q[q] = ex2(((oh[k] + mh) - zo.x) + ((ol[k] + ml) - zo.y));
+      }
     }
   }
   __syncthreads();
@@ -408,7 +468,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   for (int xi = tid; xi < cnt; xi += kNodeThreads) se += ex2((s_s[xi].x - sq) + s_s[xi].y);
   const double sse = block_sum((double)se, red);
   if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2((double)sq * kLn2, sse);
-  // pass 3, pairs: g = s - (m - Z_k) (f'/eps in log2), the operand, f = eps ln2 g, |q_k - mean q|
+  // pass 3, pairs: g = s - (m - Z_k) (f'/eps in log2, the operand; f' = eps ln2 g), |q_k - mean q|
   {
     PairWalk w(cnt);
     for (int q0 = 0; q0 < np; q0 += kNodeThreads) {  // warp-uniform trip count
@@ -422,7 +482,6 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
         const float2 mi = s_mi[q], sv = s_s[w.xi];
         r = fabsf(s_q[q] - s_qb[w.xi]);
         const float2 g = regrid(sv.x - mi.x, sv.y - mi.y);
-        A.f[d.off + x] = eps_ln2 * ((double)g.x + (double)g.y);
         A.hh[d.off + x] = g.x;
         A.hl[d.off + x] = g.y;
         if (track && fabsf((g.x - A.bh[d.off + x]) + (g.y - A.bl[d.off + x])) > A.tau) s_dr[i] = 1;
@@ -541,6 +600,30 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
   }
 }
 
+// stored potentials of an FP32 handle from the operand the node update keeps:
+// f' = eps ln2 (hh + hl) on a free owner, eps ln2 ((hh + hl) - log2 mu) on a
+// fixed one (points with mu = 0 keep the f the update wrote).  One CTA per
+// directed edge at a time; the two-floats are summed exactly in FP64.
+__global__ void __launch_bounds__(256) materialise_f_kernel(const DEdgeD* dedges, int32_t ndedges, const NodeD* nodes,
+                                                            const ProbD* probs, const float4* lgf, const float* hh,
+                                                            const float* hl, double* f) {
+  for (int di = blockIdx.x; di < ndedges; di += gridDim.x) {
+    const DEdgeD d = dedges[di];
+    const NodeD nd = nodes[d.owner];
+    const double eps_ln2 = probs[d.prob].eps * kLn2;
+    for (int x = threadIdx.x; x < nd.n; x += blockDim.x) {
+      const double h = (double)hh[d.off + x] + (double)hl[d.off + x];
+      if (nd.fixed) {
+        const float4 lg = lgf[nd.node_off + x];
+        if (lg.x == -INFINITY) continue;
+        f[d.off + x] = eps_ln2 * (h - ((double)lg.x + (double)lg.y));
+      } else {
+        f[d.off + x] = eps_ln2 * h;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s) {
@@ -558,6 +641,13 @@ cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s) {
     node_update_kernel<true><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
   else
     node_update_kernel<false><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_materialise_f(const DEdgeD* dedges, int32_t ndedges, const NodeD* nodes, const ProbD* probs,
+                                 const float4* lgf, const float* hh, const float* hl, double* f, cudaStream_t s) {
+  if (ndedges <= 0) return cudaSuccess;
+  materialise_f_kernel<<<std::min(ndedges, 4096), 256, 0, s>>>(dedges, ndedges, nodes, probs, lgf, hh, hl, f);
   return cudaGetLastError();
 }
 

@@ -39,9 +39,9 @@ constexpr float kSkFixBelow = 1.2621774e-29f;  // 2^-96
 // one column of a group: a directed edge of one colour
 struct SkCol {
   int64_t h_off;     // its operand (hh, hl of the reverse directed edge), length ny
-  int64_t part_off;  // its partials: part32[part_off + split * nx + x]
+  int64_t part_off;  // its partial: part32[part_off + x] (piece 0; the node update
+                     // merges that piece alone for a problem in the phase)
   int32_t prob;
-  int32_t nsplit;    // partial pieces per output; the phase writes piece 0, empties the rest
 };
 
 struct SkArgs {
