@@ -43,8 +43,25 @@ __device__ __forceinline__ void atomic_max_float(float* addr, float v) {
 
 constexpr int kEnvCols = 32;  // columns per envelope CTA
 
+// h + l of four consecutive points from a, b (16-byte aligned when y0 + 4 <= n)
+__device__ __forceinline__ void load_sum4(const float* a, const float* b, int y0, int n, float* v) {
+  if (y0 + 4 <= n) {
+    const float4 h = *reinterpret_cast<const float4*>(a + y0);
+    const float4 l = *reinterpret_cast<const float4*>(b + y0);
+    v[0] = h.x + l.x;
+    v[1] = h.y + l.y;
+    v[2] = h.z + l.z;
+    v[3] = h.w + l.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = y0 + i < n ? a[y0 + i] + b[y0 + i] : -kInf;
+  }
+}
+
 // one CTA per kEnvCols columns: each warp finds the maxima of 4 columns, then
-// every thread folds its points' normalised values into the envelope
+// every thread folds its points' normalised values into the envelope.  A
+// column's operand starts at a multiple of 32 points, so a thread reads four
+// consecutive points with one 16-byte load of each of hh and hl.
 __global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
   __shared__ float s_m[kEnvCols];
   __shared__ int64_t s_off[kEnvCols];
@@ -58,7 +75,11 @@ __global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
       const SkCol col = A.cols[c0 + k];
       off = col.h_off;
       if (col_active(A, col))
-        for (int y = lane; y < A.ny; y += 32) m = fmaxf(m, A.hh[off + y] + A.hl[off + y]);
+        for (int y0 = 4 * lane; y0 < A.ny; y0 += 4 * 32) {
+          float v[4];
+          load_sum4(A.hh + off, A.hl + off, y0, A.ny, v);
+          m = fmaxf(m, fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3])));
+        }
     }
     m = warp_max(m);
     if (lane == 0) {
@@ -69,11 +90,28 @@ __global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
     }
   }
   __syncthreads();
-  for (int y = threadIdx.x; y < A.ny; y += 256) {
-    float e = -kInf;
-    for (int k = 0; k < nc; ++k)
-      if (s_m[k] > -kInf) e = fmaxf(e, (A.hh[s_off[k] + y] - s_m[k]) + A.hl[s_off[k] + y]);
-    atomic_max_float(&A.b[y], e);
+  for (int y0 = 4 * (int)threadIdx.x; y0 < A.ny; y0 += 4 * 256) {
+    float e[4] = {-kInf, -kInf, -kInf, -kInf};
+    for (int k = 0; k < nc; ++k) {
+      if (!(s_m[k] > -kInf)) continue;
+      const float* hh = A.hh + s_off[k];
+      const float* hl = A.hl + s_off[k];
+      if (y0 + 4 <= A.ny) {
+        const float4 h = *reinterpret_cast<const float4*>(hh + y0);
+        const float4 l = *reinterpret_cast<const float4*>(hl + y0);
+        e[0] = fmaxf(e[0], (h.x - s_m[k]) + l.x);
+        e[1] = fmaxf(e[1], (h.y - s_m[k]) + l.y);
+        e[2] = fmaxf(e[2], (h.z - s_m[k]) + l.z);
+        e[3] = fmaxf(e[3], (h.w - s_m[k]) + l.w);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (y0 + i < A.ny) e[i] = fmaxf(e[i], (hh[y0 + i] - s_m[k]) + hl[y0 + i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (y0 + i < A.ny) atomic_max_float(&A.b[y0 + i], e[i]);
   }
 }
 
@@ -91,43 +129,61 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// one warp per row x (8 rows per CTA); rows past nx and columns past ny are zero
+// four BF16 (hi, lo) splits of consecutive values, packed for one 8-byte store each
+__device__ __forceinline__ void store_split4(const float* v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_bf16(v[i], h[i], l[i]);
+  *reinterpret_cast<uint2*>(hi) = *reinterpret_cast<const uint2*>(h);
+  *reinterpret_cast<uint2*>(lo) = *reinterpret_cast<const uint2*>(l);
+}
+
+// one CTA per row x, four consecutive columns y per thread and pass (kd is a
+// multiple of kSkPadK); rows past nx and columns past ny are zero
 __global__ void __launch_bounds__(256) sk_kbuild_kernel(SkArgs A) {
-  const int lane = threadIdx.x & 31;
-  const int x = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (x >= A.mp) return;
+  __shared__ float s_red[8];
+  const int x = blockIdx.x;
   __nv_bfloat16* khi = A.khi + (int64_t)x * A.kd;
   __nv_bfloat16* klo = A.klo + (int64_t)x * A.kd;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
   if (x >= A.nx) {
-    for (int y = lane; y < A.kd; y += 32) {
-      khi[y] = zero;
-      klo[y] = zero;
-    }
-    if (lane == 0) A.rf[x] = 0.f;
+    const float z[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int y0 = 4 * (int)threadIdx.x; y0 < A.kd; y0 += 4 * 256) store_split4(z, khi + y0, klo + y0);
+    if (threadIdx.x == 0) A.rf[x] = 0.f;
     return;
   }
   float p[3] = {0.f, 0.f, 0.f};
   for (int d = 0; d < A.dim; ++d) p[d] = A.xc[(int64_t)x * A.dim + d];
   float env = -kInf;
-  for (int y = lane; y < A.ny; y += 32)
+  for (int y = threadIdx.x; y < A.ny; y += 256)
     env = fmaxf(env, fmaf(-sqdist(p, A.yc + (int64_t)y * A.dim, A.dim), A.s_hi, quant(A.b[y])));
   env = warp_max(env);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = env;
+  __syncthreads();
+  env = s_red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) env = fmaxf(env, s_red[w]);
   const float R = env > -kInf ? quant(env) : 0.f;
-  if (lane == 0) A.rf[x] = R;
-  for (int y = lane; y < A.kd; y += 32) {
-    float v = 0.f;
-    if (y < A.ny && env > -kInf) {
-      const float c = sqdist(p, A.yc + (int64_t)y * A.dim, A.dim);
-      float t = fmaf(-c, A.s_hi, quant(A.b[y]) - R);
-      t = fmaf(-c, A.s_lo, t);
-      v = ex2(t);
+  if (threadIdx.x == 0) A.rf[x] = R;
+  for (int y0 = 4 * (int)threadIdx.x; y0 < A.kd; y0 += 4 * 256) {
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int y = y0 + i;
+      v[i] = 0.f;
+      if (y < A.ny && env > -kInf) {
+        const float c = sqdist(p, A.yc + (int64_t)y * A.dim, A.dim);
+        float t = fmaf(-c, A.s_hi, quant(A.b[y]) - R);
+        t = fmaf(-c, A.s_lo, t);
+        v[i] = ex2(t);
+      }
     }
-    split_bf16(v, khi[y], klo[y]);
+    store_split4(v, khi + y0, klo + y0);
   }
 }
 
-// one CTA per column; inactive columns are left alone (their outputs are not stored)
+// one CTA per column, four consecutive points per thread and pass (the
+// operand's offset is a multiple of 32 points, kd of kSkPadK); inactive
+// columns are left alone (their outputs are not stored)
 __global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
   const int j = blockIdx.x;
   const SkCol col = A.cols[j];
@@ -135,13 +191,27 @@ __global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
   if (!col_active(A, col) || !(M > -kInf)) return;
   __nv_bfloat16* vhi = A.vhi + (int64_t)j * A.kd;
   __nv_bfloat16* vlo = A.vlo + (int64_t)j * A.kd;
-  for (int y = threadIdx.x; y < A.kd; y += 256) {
-    float v = 0.f;
-    if (y < A.ny) {
-      const float hh = A.hh[col.h_off + y];
-      if (hh > -kInf) v = ex2(((hh - M) - quant(A.b[y])) + A.hl[col.h_off + y]);
+  const float* hh = A.hh + col.h_off;
+  const float* hl = A.hl + col.h_off;
+  for (int y0 = 4 * (int)threadIdx.x; y0 < A.kd; y0 += 4 * 256) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (y0 + 4 <= A.ny) {
+      const float4 h4 = *reinterpret_cast<const float4*>(hh + y0);
+      const float4 l4 = *reinterpret_cast<const float4*>(hl + y0);
+      const float4 b4 = *reinterpret_cast<const float4*>(A.b + y0);
+      const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+      const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (hv[i] > -kInf) v[i] = ex2(((hv[i] - M) - quant(bv[i])) + lv[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int y = y0 + i;
+        if (y < A.ny && hh[y] > -kInf) v[i] = ex2(((hh[y] - M) - quant(A.b[y])) + hl[y]);
+      }
     }
-    split_bf16(v, vhi[y], vlo[y]);
+    store_split4(v, vhi + y0, vlo + y0);
   }
 }
 
@@ -635,7 +705,7 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s) {
   if (a.use_tc && !maps) return cudaErrorInvalidValue;
   if (!(a.use_tc ? sk_tc_ready() : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
   sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
-  sk_kbuild_kernel<<<a.mp / 8, 256, 0, s>>>(a);
+  sk_kbuild_kernel<<<a.mp, 256, 0, s>>>(a);
   sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
   const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
   if (a.use_tc)

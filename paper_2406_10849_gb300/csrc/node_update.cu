@@ -96,6 +96,60 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
+// FP32 block reductions for the FP32 path (FP64 adds run at a small fraction
+// of the FP32 rate on GB300).  block_max_f: result in every thread.
+__device__ float block_max_f(float v, float* red) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float r = red[0];
+#pragma unroll
+  for (int i = 1; i < kNodeThreads / 32; ++i) r = fmaxf(r, red[i]);
+  return r;
+}
+
+// plain sum, valid in thread 0 (the stopping terms)
+__device__ float block_sum_f0(float v, float* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < kNodeThreads / 32; ++i) r += red[i];
+  return r;
+}
+
+// (hi, lo) + (hi, lo) with the rounding error of the hi sum kept (TwoSum)
+__device__ __forceinline__ float2 add_f2(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (b.x - bb);
+  return make_float2(s, (a.y + b.y) + err);
+}
+
+// compensated sum as (hi, lo), valid in thread 0 (the normaliser's partial
+// sums: a few units of 2^-40 relative for non-negative terms)
+__device__ float2 block_sum2_f0(float v, float2* red) {
+  float2 a = make_float2(v, 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    a = add_f2(a, make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = a;
+  __syncthreads();
+  float2 r = make_float2(0.f, 0.f);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < kNodeThreads / 32; ++i) r = add_f2(r, red[i]);
+  return r;
+}
+
 // merged message of pair (edge d, point x) minus Z_k (FP64 partials); writes its frame
 __device__ __forceinline__ double merge_pair64(const NodeArgs& A, const DEdgeD& d, int n_owner, int x, double Zk) {
   const double mr = merge64(A.part64 + d.part_off + x, d.nsplit, n_owner);
@@ -400,8 +454,8 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
       }
     }
     if (__syncthreads_or(drift) && tid == 0) atomicOr(&A.drift[d.edge], 1);
-    const double rs = block_sum((double)r, red);
-    if (tid == 0) atomicAdd(&A.resid_acc[s_di[0]], rs);
+    const float rs = block_sum_f0(r, reinterpret_cast<float*>(red));
+    if (tid == 0) atomicAdd(&A.resid_acc[s_di[0]], (double)rs);
     if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
     return;
   }
@@ -462,12 +516,12 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
     s_qb[xi] = qsum * inv_deg;
     smax = fmaxf(smax, mh + ml);
   }
-  smax = (float)block_max((double)smax, red);  // its barriers also publish s_s and s_qb
+  smax = block_max_f(smax, reinterpret_cast<float*>(red));  // its barriers also publish s_s and s_qb
   const float sq = isfinite(smax) ? quant(smax) : 0.f;
   float se = 0.f;
   for (int xi = tid; xi < cnt; xi += kNodeThreads) se += ex2((s_s[xi].x - sq) + s_s[xi].y);
-  const double sse = block_sum((double)se, red);
-  if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2((double)sq * kLn2, sse);
+  const float2 sse = block_sum2_f0(se, reinterpret_cast<float2*>(red));
+  if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2((double)sq * kLn2, (double)sse.x + (double)sse.y);
   // pass 3, pairs: g = s - (m - Z_k) (f'/eps in log2, the operand; f' = eps ln2 g), |q_k - mean q|
   {
     PairWalk w(cnt);

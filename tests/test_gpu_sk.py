@@ -60,6 +60,24 @@ def test_shared_kernel_iterates_match_oracle(T, steps):
         assert marginal_gap(probs[i], f, ref) <= 1e-5
 
 
+def test_shared_kernel_ragged_support(T):
+    """Six 11x11 stars (121 points: neither the four-point vectors of the
+    envelope and operand builds nor the 64-point reduction padding divide it)
+    follow the oracle for five half-steps in the phase."""
+    probs = stars(6, side=11, eps=0.01, seed=7_050_000)
+    with T.Solver(probs, T.options(apply_mode="bf16", lowp_start=0, refine_tol=0.0)) as s:
+        s.half_steps(5)
+        got = {i: s.potentials(i) for i in (0, 5)}
+    with T.Solver(probs, T.options()) as s:  # the FP32 path, for contrast
+        s.half_steps(5)
+        fp32 = s.potentials(0)
+    assert any(not np.array_equal(got[0][k], fp32[k]) for k in fp32)  # the phase ran
+    for i, f in got.items():
+        ref = O.run_half_steps(probs[i], 5)
+        assert rel_err(f, ref, probs[i].eps) <= 1e-4
+        assert marginal_gap(probs[i], f, ref) <= 1e-5
+
+
 def test_shared_kernel_solve_is_certified(T):
     """Twelve 16x16 stars at eps 0.005: the phase runs until the stopping
     quantity is below refine_tol, FP32 sweeps finish, the FP64-grade check
