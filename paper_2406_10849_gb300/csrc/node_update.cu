@@ -35,9 +35,10 @@ namespace {
 
 // Two paths.  FP64 handles merge FP64 partials and work in double throughout
 // (chunk_update64).  FP32 handles (chunk_update32) work in log2 units on
-// two-float values and use FP64 arithmetic only to form the stored potential:
-// GB300 executes FP64 arithmetic and float <-> double conversions at a small
-// fraction of its FP32 rate.
+// two-float values with no FP64 arithmetic per pair or per block reduction
+// (the stored potential is formed from the operand when it is read, by
+// materialise_f_kernel): GB300 executes FP64 arithmetic and float <-> double
+// conversions at a small fraction of its FP32 rate.
 
 __device__ __forceinline__ float quant(float v) { return rintf(v * 1024.f) * (1.f / 1024.f); }
 
