@@ -162,7 +162,7 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(p, budget_s: float = 12.0, max_applies: int = 16):
+def cpu_baseline(p, budget_s: float = 20.0, max_applies: int = 64):
     """FP64 oracle on a bounded sample: edge applies (messages) of half-step 1,
     timed on the host cores, as it stands."""
     from oracle import tree_ot as O
