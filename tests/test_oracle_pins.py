@@ -75,6 +75,29 @@ def test_golden_single_edge_two_points():
     assert abs(fc["transport_cost"] - g["transport_cost"][0]) < 1e-15
 
 
+def _star3_problem(g):
+    """Centre 0 free, leaves 1..3 fixed, two points each; C_(0,k) = [[0, c_k], [c_k, 0]]."""
+    mus = {k + 1: np.array([g["p"][k], 1.0 - g["p"][k]]) for k in range(3)}
+    costs = [np.array([[0.0, ck], [ck, 0.0]]) for ck in g["c"]]
+    return dense_problem([[0, 1], [0, 2], [0, 3]], [2, 2, 2, 2], [False, True, True, True], mus, costs,
+                         float(g["eps"][0]))
+
+
+def test_golden_stopping_quantity_away_from_convergence():
+    """The stopping quantity at u = 1 and after one and two half-steps, against the hand-worked
+    values of a 3-leaf star (arithmetic mean qbar in the free-node terms; the update's geometric
+    mean gives other values at degree 3)."""
+    g = _read_golden("star3_residual_2pt.txt")
+    p = _star3_problem(g)
+    order = [(1, 0), (2, 0), (3, 0), (0, 1), (0, 2), (0, 3)]
+    for t in range(3):
+        f = O.run_half_steps(p, t)
+        r, rmax, terms = O.residual(p, f)
+        np.testing.assert_allclose([terms[k] for k in order], g[f"terms_t{t}"], rtol=0, atol=1e-14)
+        assert abs(r - g[f"sum_t{t}"][0]) < 1e-14
+        assert abs(rmax - g[f"max_t{t}"][0]) < 1e-15
+
+
 @pytest.mark.parametrize("fixed_first", [True, False])
 def test_single_edge_closed_form(fixed_first):
     """Fixed-free edge: B = diag(mu ./ (K 1)) K after one update of each node."""
@@ -335,6 +358,7 @@ def _pins_pass():
     """A quick subset of the pins above; True when all hold."""
     try:
         test_golden_single_edge_two_points()
+        test_golden_stopping_quantity_away_from_convergence()
         test_chain_with_identity_edge_is_two_marginal_sinkhorn()
         test_star_is_ibp_barycenter()
         p = random_small_tree(41, 5, nmin=3, nmax=4, eps=0.1)
@@ -399,3 +423,40 @@ def test_planted_mistakes_are_caught(monkeypatch):
         return {key: v * 1.5 for key, v in upd.items()}, rho
     monkeypatch.setattr(O, "update_node", bad_update)
     assert not _pins_pass(), "scaled free update"
+
+
+def test_planted_stopping_rule_mistakes_are_caught(monkeypatch):
+    """Plausible mistakes in the stopping quantity: the geometric mean (the update's eq. q) in
+    place of the arithmetic qbar, the sum of the terms reported as the largest term, and the
+    free-node terms measured against the first neighbour's q instead of the mean."""
+    assert _pins_pass()
+    real_residual = O.residual
+
+    def planted(kind):
+        def residual(p, f):
+            nb = O.neighbours(p.num_nodes, p.edges)
+            terms = {}
+            for j in range(p.num_nodes):
+                if p.fixed[j]:
+                    (k,) = nb[j]
+                    terms[(j, k)] = float(np.abs(O.edge_marginal(p, f, j, k) - p.marginals[j]).sum())
+                    continue
+                qs = {k: O.edge_marginal(p, f, j, k) for k in nb[j]}
+                if kind == "geometric":
+                    qbar = np.exp(sum(np.log(q) for q in qs.values()) / len(qs))
+                elif kind == "first":
+                    qbar = qs[nb[j][0]]
+                else:
+                    qbar = sum(qs.values()) / len(qs)
+                for k in nb[j]:
+                    terms[(j, k)] = float(np.abs(qs[k] - qbar).sum())
+            r = float(sum(terms.values()))
+            return r, (r if kind == "max_is_sum" else float(max(terms.values()))), terms
+        return residual
+
+    for kind in ["geometric", "max_is_sum", "first"]:
+        monkeypatch.setattr(O, "residual", planted(kind))
+        assert not _pins_pass(), kind
+    monkeypatch.setattr(O, "residual", planted("none"))
+    assert _pins_pass()
+    monkeypatch.setattr(O, "residual", real_residual)
