@@ -252,6 +252,24 @@ int tree_ot_check(tree_ot_handle *h, void *cuda_stream, tree_ot_result *results)
  * out: host, n_j doubles. */
 int tree_ot_marginals(tree_ot_handle *h, int32_t prob, int32_t node, double *out);
 
+/* History of the stopping quantity (the while-condition of the Bipartite
+ * Iterative Scaling algorithm, Sec. 3.1, and its largest term) as the half-step
+ * kernels accumulate it in FP32 -- the value problems retire on.  The terms of
+ * iterate t (the potentials after t half-steps) are non-zero only on the side
+ * the next half-step updates, and that half-step (number t + 1) forms them from
+ * the messages it computes anyway; the other side's terms vanish up to
+ * rounding (lemma cor:tree_mass and the block updates of thm:tree_dual_var),
+ * except at t = 0 (u = 1), where that side is not measured.
+ * sum_out[i] / max_out[i] (host, count doubles each; either may be NULL) get
+ * the values of iterate first + i.  The last 256 iterates are kept; iterates
+ * must satisfy 0 <= first, first + count <= half-steps done, and
+ * first >= half-steps done - 256 (else TREE_OT_ERR_ARG).  A problem retired by
+ * tree_ot_solve skips later half-steps; its later entries read 0, and a
+ * problem resumed by the certification restarts its history.  Synchronises
+ * cuda_stream. */
+int tree_ot_residual_history(tree_ot_handle *h, void *cuda_stream, int32_t prob, int64_t first, int64_t count,
+                             double *sum_out, double *max_out);
+
 /* Copy the potential vector of directed edge `dedge` (0 <= dedge < 2(J-1), see
  * the numbering above) of problem p to / from host memory (FP64, n_owner values).
  * set_potentials is how warm starts and checkpoint resumes enter; the free-node
@@ -292,12 +310,17 @@ int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
 /* Allocation-free apply of one stored cost matrix (the paper has no
  * counterpart: this is a packaging of the edge-apply kernel for callers that
- * cannot allocate device memory -- code running while a CUDA graph is being
- * captured, serving runtimes that own every byte of device memory through a
- * pre-sized pool, or real-time loops that forbid the device-wide
- * synchronisation cudaMalloc/cudaFree can cause).
+ * cannot allocate device memory -- serving runtimes that own every byte of
+ * device memory through a pre-sized pool, plug-ins hosted by such a runtime,
+ * or real-time loops that forbid the device-wide synchronisation
+ * cudaMalloc/cudaFree can cause).
  *
  *   m_out[x] = log sum_{y < n_cols} exp( g[y] - cost[x * ld + y] / eps ),  x < n_rows
+ *
+ * Accuracy: every term is formed and summed in FP32 (the argument exact up to
+ * its final rounding, as in the solver's apply); the pieces of a row are merged
+ * and the logarithm taken in FP64, so m_out carries the FP32 sums' relative
+ * error (about 1e-7 of the row's sum, i.e. ~1e-7 absolute in m) and no more.
  *
  * cost: device, n_rows x ld FP32 row-major (ld >= n_cols, ld % 4 == 0, base
  *       16-byte aligned); entries past n_cols in a row are ignored; +inf entries

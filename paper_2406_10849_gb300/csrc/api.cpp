@@ -1830,6 +1830,34 @@ int tree_ot_marginals(tree_ot_handle* h, int32_t prob, int32_t node, double* out
   return TREE_OT_OK;
 }
 
+int tree_ot_residual_history(tree_ot_handle* h, void* cuda_stream, int32_t prob, int64_t first, int64_t count,
+                             double* sum_out, double* max_out) {
+  g_err.clear();
+  if (!h || prob < 0 || prob >= h->nprob || count < 0 || (count > 0 && !sum_out && !max_out))
+    return fail(TREE_OT_ERR_ARG, "bad handle, problem, count or output pointers");
+  // the terms of iterate t are recorded by half-step t + 1 in ring slot t % kResidRing
+  if (first < 0 || first + count > h->hs_host || first < h->hs_host - kResidRing)
+    return fail(TREE_OT_ERR_ARG, "iterates " + std::to_string(first) + " .. " + std::to_string(first + count - 1) +
+                                     " are not in the history (half-steps done: " + std::to_string(h->hs_host) +
+                                     ", kept: " + std::to_string(kResidRing) + ")");
+  if (count == 0) return TREE_OT_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<double> ring_sum(kResidRing);
+  std::vector<unsigned long long> ring_max(kResidRing);
+  CUDA_TRY(cudaMemcpy2DAsync(ring_sum.data(), sizeof(double), h->d_res_sum + prob, sizeof(double) * h->nprob,
+                             sizeof(double), kResidRing, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpy2DAsync(ring_max.data(), sizeof(double), h->d_res_max + prob,
+                             sizeof(unsigned long long) * h->nprob, sizeof(double), kResidRing,
+                             cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < count; ++i) {
+    const size_t slot = (size_t)((first + i) % kResidRing);
+    if (sum_out) sum_out[i] = ring_sum[slot];
+    if (max_out) std::memcpy(&max_out[i], &ring_max[slot], sizeof(double));
+  }
+  return TREE_OT_OK;
+}
+
 int tree_ot_get_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, int32_t dedge, double* out) {
   g_err.clear();
   if (!h || !out || prob < 0 || prob >= h->nprob || dedge < 0 || dedge >= 2 * (h->prob_nodes[prob] - 1))

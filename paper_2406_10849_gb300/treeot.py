@@ -104,6 +104,8 @@ SIGNATURES = {
     "tree_ot_node_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "tree_ot_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Result)]),
     "tree_ot_marginals": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_residual_history": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tree_ot_get_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "tree_ot_set_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "tree_ot_set_potentials_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
@@ -362,6 +364,16 @@ class Solver:
         _check(_lib.tree_ot_marginals(self.h, prob, node, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
+    def residual_history(self, prob: int, first: int, count: int):
+        """(sums, maxima) of the stopping quantity of iterates first .. first+count-1,
+        as the half-step kernels accumulated it (tree_ot_residual_history)."""
+        sums = np.zeros(int(count), np.float64)
+        maxs = np.zeros(int(count), np.float64)
+        _check(_lib.tree_ot_residual_history(self.h, self._s(), int(prob), int(first), int(count),
+                                             sums.ctypes.data_as(C.POINTER(C.c_double)),
+                                             maxs.ctypes.data_as(C.POINTER(C.c_double))))
+        return sums, maxs
+
     def potential(self, prob: int, dedge: int) -> np.ndarray:
         p = self.problems[prob]
         e = dedge // 2
@@ -436,9 +448,27 @@ def edge_apply_noalloc(cost, g, eps: float, m_out, ld: int = None, stream=None):
     g: CUDA float64 (n_cols,), m_out: CUDA float64 (n_rows,).  Marshalling only.
     """
     load()
+    import torch
+    if cost.dim() != 2 or g.dim() != 1 or m_out.dim() != 1:
+        raise ValueError("cost must be a matrix, g and m_out vectors")
+    if cost.dtype != torch.float32 or g.dtype != torch.float64 or m_out.dtype != torch.float64:
+        raise ValueError("cost must be float32, g and m_out float64")
+    if not (cost.is_cuda and g.is_cuda and m_out.is_cuda):
+        raise ValueError("cost, g and m_out must be CUDA tensors")
+    cur = torch.cuda.current_device()
+    if cost.device.index != cur or g.device.index != cur or m_out.device.index != cur:
+        raise ValueError("cost, g and m_out must live on the current CUDA device")
+    if cost.stride(1) != 1 or g.stride(0) != 1 or m_out.stride(0) != 1:
+        raise ValueError("cost rows, g and m_out must be contiguous")
     n_rows = int(cost.shape[0])
     n_cols = int(g.shape[0])
     ld = int(cost.stride(0)) if ld is None else int(ld)
+    # every row the kernel reads (x * ld .. x * ld + n_cols) must lie inside the tensor's storage
+    reach = (n_rows - 1) * ld + n_cols
+    avail = cost.untyped_storage().nbytes() // 4 - cost.storage_offset()
+    if n_cols > int(cost.shape[1]) or ld < n_cols or reach > avail or int(m_out.shape[0]) < n_rows:
+        raise ValueError("need len(g) <= cost columns, ld >= len(g), rows of stride ld inside the cost's "
+                         "storage and len(m_out) >= cost rows")
     _check(_lib.tree_ot_edge_apply_noalloc(C.c_void_p(cost.data_ptr()), ld, n_rows, n_cols,
                                            C.c_void_p(g.data_ptr()), float(eps), C.c_void_p(m_out.data_ptr()),
                                            C.c_void_p(_stream_ptr(stream))))

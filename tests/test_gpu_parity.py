@@ -213,6 +213,29 @@ def test_full_prufer_dense_sampled(T):
     torch.cuda.empty_cache()
 
 
+def test_full_prufer_bf16_solve_certified_by_oracle(T):
+    """The 64-node tree at full size (n = 4096, 4.2 GB of stored costs): the BF16
+    absorbed phase + FP32 refinement solved to max marginal L1 <= 1e-6 (the timed
+    time-to-1e-6 form), then every directed edge's marginal of the returned
+    potentials evaluated by the FP64 oracle: the largest stopping term is within
+    1e-6 and equals the GPU check's."""
+    p = gen.prufer_problem(seed=3000)
+    dev = torch.device("cuda")
+    costs = [gen.sqeuclid_cost_f32_torch(p.coords[a], p.coords[b], 1.0, dev) for a, b in p.edges]
+    with T.Solver([p], T.options(precision="fp32", apply_mode="bf16", tol=1e-6, tol_kind="max",
+                                 max_half_steps=20000), device_costs=[costs]) as s:
+        rc, res = s.solve()
+        got = s.potentials(0)
+    del costs
+    torch.cuda.empty_cache()
+    assert rc == 0, res
+    assert res[0]["lowp_half_steps"] > 0
+    r, m, _ = O.residual(p, got)
+    assert m <= 1e-6, m
+    assert abs(res[0]["max_marginal_l1"] - m) <= 5e-8, (res[0]["max_marginal_l1"], m)
+    assert abs(res[0]["residual_sum_l1"] - r) <= 1e-7 * max(1.0, r), (res[0]["residual_sum_l1"], r)
+
+
 def test_batched_forest(T):
     """A forest of uneven trees solved in one handle: iterate parity per tree, then
     each tree converges and retires on its own."""
@@ -240,15 +263,108 @@ def test_batched_forest(T):
 
 def test_full_batched_512_sampled(T):
     """The 512-tree batch (4..32 nodes, n in 128..2048, eps log-uniform): two
-    half-steps on the GPU, three trees re-run by the oracle."""
+    half-steps on the GPU; the largest tree, the tree holding the largest
+    support, the tree with the smallest eps and a median tree re-run by the
+    oracle (the kernels' multi-split reductions and 2048-point tasks)."""
     probs = gen.batched_problems(seed=4000)
+    sizes = np.array([pp.elements_per_half_step() for pp in probs])
+    pick = {int(np.argmax(sizes)), int(np.argmax([int(np.max(pp.n)) for pp in probs])),
+            int(np.argmin([pp.eps for pp in probs])), int(np.argsort(sizes)[len(probs) // 2])}
     with T.Solver(probs, T.options(precision="fp32")) as s:
         s.half_steps(2)
-        sizes = [pp.elements_per_half_step() for pp in probs]
-        for i in np.argsort(sizes)[:3]:
+        for i in sorted(pick):
             ref = O.run_half_steps(probs[i], 2)
-            got = s.potentials(int(i))
-            assert rel_err(got, ref, probs[i].eps) <= 1e-4
+            got = s.potentials(i)
+            assert rel_err(got, ref, probs[i].eps) <= 1e-4, i
+            assert marginal_gap(probs[i], got, ref) <= 1e-6, i
+
+
+def _geometric_mean_residual(p, f):
+    """The stopping sum with the update's geometric mean in place of the arithmetic qbar
+    (a plausible mistake; used only to show the comparison below can tell them apart)."""
+    nb = O.neighbours(p.num_nodes, p.edges)
+    tot = 0.0
+    for j in range(p.num_nodes):
+        if p.fixed[j]:
+            (k,) = nb[j]
+            tot += float(np.abs(O.edge_marginal(p, f, j, k) - p.marginals[j]).sum())
+            continue
+        qs = [O.edge_marginal(p, f, j, k) for k in nb[j]]
+        g = np.exp(sum(np.log(q) for q in qs) / len(qs))
+        tot += sum(float(np.abs(q - g).sum()) for q in qs)
+    return tot
+
+
+def test_stopping_quantity_away_from_convergence(T):
+    """The stopping sum and its largest term (the while-condition of the Bipartite Iterative
+    Scaling algorithm) at non-converged iterates of a 12-node tree with free nodes of degree
+    3 and 4.  (a) The FP32 quantity the half-step kernels accumulate -- the one problems
+    retire on -- for iterates 1..4 against the oracle's on the oracle's iterates; (b) the
+    FP64-grade check of iterate 5 against the oracle's evaluation of the same potentials."""
+    rng = np.random.default_rng(11)
+    p = gen.random_tree_problem(rng, 12, n_range=(40, 300), eps_range=(0.03, 0.03), D=2, name="stop")
+    with T.Solver([p], T.options(precision="fp32")) as s:
+        s.half_steps(5)
+        sums, maxs = s.residual_history(0, 1, 4)
+        res = s.check()[0]
+        got = s.potentials(0)
+    tol_fp32 = 1e-5   # FP32 q (~1e-7 relative per entry) summed over 22 directed edges, plus the iterates' gap
+    discriminating = 0
+    for i, t in enumerate(range(1, 5)):
+        f_ref = O.run_half_steps(p, t)
+        r, m, _ = O.residual(p, f_ref)
+        assert abs(sums[i] - r) <= tol_fp32, (t, sums[i], r)
+        assert abs(maxs[i] - m) <= tol_fp32, (t, maxs[i], m)
+        if abs(_geometric_mean_residual(p, f_ref) - r) > 10 * tol_fp32:
+            discriminating += 1
+    assert discriminating >= 2   # a geometric-mean stopping sum would fail (a)
+    r, m, _ = O.residual(p, got)
+    # double-float check: each marginal within a few 1e-8 (L1) of the FP64 evaluation
+    assert abs(res["residual_sum_l1"] - r) <= 1e-7, (res["residual_sum_l1"], r)
+    assert abs(res["max_marginal_l1"] - m) <= 5e-8, (res["max_marginal_l1"], m)
+
+
+def test_iteration_cap_reports_not_converged(T):
+    """A cap far below what tol needs: TREE_OT_NOT_CONVERGED, every result finite, the
+    reported stopping sum above tol and equal to the oracle's on the returned potentials."""
+    p = gen.star_problem(seed=2005, leaves=4, side=12, eps=0.01)
+    with T.Solver([p], T.options(precision="fp32", tol=1e-9, tol_kind="sum", max_half_steps=10,
+                                 check_every=2)) as s:
+        rc, res = s.solve()
+        got = s.potentials(0)
+    assert rc == T.NOT_CONVERGED and res[0]["status"] == T.NOT_CONVERGED
+    for k in ("residual_sum_l1", "max_marginal_l1", "primal", "dual", "transport_cost"):
+        assert np.isfinite(res[0][k]), k
+    assert res[0]["half_steps"] == 10
+    r, _, _ = O.residual(p, got)
+    assert res[0]["residual_sum_l1"] > 1e-9 and abs(res[0]["residual_sum_l1"] - r) <= 1e-7
+
+
+def test_infeasible_row_reports_nonfinite(T):
+    """A fixed leaf point with mu > 0 whose cost row is all +inf has no admissible plan
+    (K = 0 on its whole row): the solve stops with TREE_OT_ERR_NONFINITE (the node
+    update's non-finite flag, read between chunks; no device fault), and a new handle
+    on the same device then solves normally."""
+    rng = np.random.default_rng(29)
+    n = 24
+    mu0 = gen.dirichlet_marginal(n, rng)
+    mu2 = gen.dirichlet_marginal(n, rng)
+    C01 = rng.random((n, n)).astype(np.float32)
+    C01[5, :] = np.inf
+    C12 = rng.random((n, n)).astype(np.float32)
+    mk = lambda c: TreeProblem(name="inf", edges=np.array([[0, 1], [1, 2]], np.int32), n=np.full(3, n, np.int32),
+                               fixed=np.array([True, False, True]), marginals={0: mu0, 2: mu2}, eps=0.1,
+                               coords=[np.zeros((n, 1), np.float32)] * 3, cost_scale=1.0, cost_kind="dense",
+                               dense_costs=[c, C12])
+    assert mu0[5] > 0
+    with T.Solver([mk(C01)], T.options(precision="fp32", tol=1e-7, check_every=2)) as s:
+        with pytest.raises(T.TreeOTError) as ei:
+            s.solve()
+    assert ei.value.kind == "NONFINITE"
+    C01[5, :] = 0.5
+    with T.Solver([mk(C01)], T.options(precision="fp32", tol=1e-7, tol_kind="max")) as s:
+        rc, res = s.solve()
+    assert rc == 0 and res[0]["max_marginal_l1"] <= 1e-7
 
 
 def test_identity_edge_chain_is_sinkhorn_on_gpu(T):
