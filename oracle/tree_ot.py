@@ -35,7 +35,7 @@ Stopping quantity (the while-condition of that algorithm):
       + sum_{j free} sum_{k in N(j)} ||q_(j,k) - qbar_j||_1,
 with q_(j,k) = B_(j,k) 1 and qbar_j their arithmetic mean (lemma lem:f_upper_bound_tree).
 
-Readings of the paper taken here (also listed in the design notes):
+Readings of the paper taken here:
 * "iteration" t counts half-steps; S_1 (node 0's colour) goes first;
 * the closed form of thm:tree_dual_var is used (it equals the multiplicative
   listing from u = 1, proposition cor:equi; ``multiplicative_half_step`` implements the
@@ -407,3 +407,79 @@ def multiplicative_half_step(problem, u: Dict[Tuple[int, int], np.ndarray], colo
             for k in nb[j]:
                 new[(j, k)] = u[(j, k)] * (qj / qj.sum()) / qs[k]
     return new
+
+
+# ---------------------------------------------------------------------------
+# rounding to feasible plans (Algorithm "Rounding for transport plan on a
+# bipartite graph", Sec. 3.1; lemmas lem:round and lem:round_applied, Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def round_matrix(F: np.ndarray, r: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Algorithm 2 of Altschuler, Weed and Rigollet (2017), the routine the paper's
+    rounding calls: a nonnegative G with row sums r and column sums c (||r||_1 = ||c||_1).
+
+    1. scale every row of F down to at most r:     x_i = min(r_i / r_i(F), 1),  F' = diag(x) F;
+    2. scale every column down to at most c:       y_j = min(c_j / c_j(F'), 1), F'' = F' diag(y);
+    3. add what is missing as a rank-one term:     G = F'' + err_r err_c^T / ||err_r||_1,
+       err_r = r - F'' 1,  err_c = c - F''^T 1  (both nonnegative).
+    A row or column of F with zero sum is left unscaled (x or y = 1).
+    """
+    F = np.asarray(F, dtype=np.float64)
+    rF = F.sum(axis=1)
+    x = np.ones_like(rF)
+    pos = rF > 0
+    x[pos] = np.minimum(r[pos] / rF[pos], 1.0)
+    F1 = x[:, None] * F
+    cF1 = F1.sum(axis=0)
+    y = np.ones_like(cF1)
+    pos = cF1 > 0
+    y[pos] = np.minimum(c[pos] / cF1[pos], 1.0)
+    F2 = F1 * y[None, :]
+    # nonnegative in exact arithmetic; a last-bit negative difference is taken as 0
+    err_r = np.maximum(r - F2.sum(axis=1), 0.0)
+    err_c = np.maximum(c - F2.sum(axis=0), 0.0)
+    mass = float(err_r.sum())
+    if mass > 0:
+        F2 = F2 + np.outer(err_r, err_c) / mass
+    return F2
+
+
+def mismatched_side(T: int) -> int:
+    """The colour class whose projections miss their marginals after half-step T >= 1:
+    half-step T updated colour (T+1) % 2, so it is colour T % 2 (the set S of the rounding)."""
+    return T % 2
+
+
+def round_plans(problem, f: Potentials, side: int) -> Dict[Tuple[int, int], np.ndarray]:
+    """The rounding algorithm of Sec. 3.1 applied to the plans of the potentials f.
+
+    For every node j of colour class ``side`` (the set S) and every neighbour k, B_(j,k)
+    (rows on j) is rounded by ``round_matrix`` so that its row sums become mu_j (j fixed) or
+    qbar_j(B) = mean_k B_(j,k) 1 (j free) and its column sums stay B_(j,k)^T 1.  Every edge
+    has exactly one endpoint in S, so every plan is rounded once.  Returns {(j, k): B^_(j,k)}
+    keyed with j in S.
+    """
+    colour = bipartition(problem.num_nodes, problem.edges)
+    nb = neighbours(problem.num_nodes, problem.edges)
+    out = {}
+    for j in range(problem.num_nodes):
+        if colour[j] != side:
+            continue
+        Bs = {k: plan(problem, f, j, k) for k in nb[j]}
+        if problem.fixed[j]:
+            target = np.asarray(problem.marginals[j], dtype=np.float64)
+        else:
+            target = sum(B.sum(axis=1) for B in Bs.values()) / len(nb[j])
+        for k in nb[j]:
+            out[(j, k)] = round_matrix(Bs[k], target, Bs[k].sum(axis=0))
+    return out
+
+
+def rounded_transport_cost(problem, rounded: Dict[Tuple[int, int], np.ndarray]) -> float:
+    """sum_e <C_e, B^_e> of rounded plans (entries with B^ = 0 contribute nothing, also where C = +inf)."""
+    tc = 0.0
+    for (j, k), B in rounded.items():
+        C = cost(problem, j, k)
+        pos = B > 0
+        tc += float(np.sum(B[pos] * C[pos]))
+    return tc
