@@ -748,7 +748,9 @@ __global__ void __launch_bounds__(kApplyThreads) noalloc_row_kernel(const float*
   }
 }
 
-// m_out[x] = ln 2 * log2 sum_s S_s 2^(R_s) over the non-empty pieces (natural log)
+// m_out[x] = ln 2 * (R + log2 sum_s S_s 2^(R_s - R)) over the non-empty pieces
+// (natural log).  The pieces are merged and the logarithm taken in FP64 (one
+// double log per row), so the output adds no rounding beyond the pieces' own.
 __global__ void noalloc_merge_kernel(const float2* part, int32_t n_rows, int32_t nsplit, double* m_out) {
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n_rows; x += gridDim.x * blockDim.x) {
     float Rm = -kInf;
@@ -760,14 +762,12 @@ __global__ void noalloc_merge_kernel(const float2* part, int32_t n_rows, int32_t
       m_out[x] = -INFINITY;
       continue;
     }
-    float S = 0.f;
+    double S = 0.0;
     for (int s = 0; s < nsplit; ++s) {
       const float2 v = part[(int64_t)s * n_rows + x];
-      if (v.y > 0.f) S += (v.x == Rm) ? v.y : v.y * ex2(v.x - Rm);
+      if (v.y > 0.f) S += (double)v.y * exp2((double)v.x - (double)Rm);  // frames on the 2^-10 grid: exact
     }
-    int e;
-    const float mant = frexpf(S, &e);
-    m_out[x] = ((double)Rm + (double)e) * 0.69314718055994530942 + (double)logf(mant);
+    m_out[x] = (double)Rm * 0.69314718055994530942 + log(S);
   }
 }
 
