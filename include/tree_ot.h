@@ -270,6 +270,56 @@ int tree_ot_marginals(tree_ot_handle *h, int32_t prob, int32_t node, double *out
 int tree_ot_residual_history(tree_ot_handle *h, void *cuda_stream, int32_t prob, int64_t first, int64_t count,
                              double *sum_out, double *max_out);
 
+/* ---- rounding to feasible plans -------------------------------------------
+ * The rounding algorithm of Sec. 3.1 ("Rounding for transport plan on a
+ * bipartite graph") with the error bounds of lemmas lem:round and
+ * lem:round_applied (Sec. 3.2).  After a half-step the colour class it did not
+ * update (S) misses its marginals; every plan B_(j,k) with j in S is rounded by
+ * Algorithm 2 of Altschuler, Weed and Rigollet (2017) to row sums t_j and column
+ * sums c_k:
+ *     x = min(t / B 1, 1),  B' = diag(x) B,  y = min(c / B'^T 1, 1),  B'' = B' diag(y),
+ *     B^ = B'' + err_r err_c^T / ||err_r||_1,  err_r = t - B'' 1,  err_c = c - B''^T 1,
+ * with t_j = mu_j (j fixed) or qbar_j = mean_k B_(j,k) 1 (j free).  The paper
+ * keeps c = B_(j,k)^T 1, which the last half-step made equal to k's marginal;
+ * an FP32 iterate matches that only to its own accuracy, so c_k is k's
+ * marginal itself (mu_k, or the mean of k's plan marginals), and t and c are
+ * taken at unit mass (exactly 1 by lemma cor:tree_mass).  In exact arithmetic
+ * y = 1 and this is the paper's rounding; in floating point the rounded plans
+ * meet every constraint of the unregularised problem (eq. ot_graph_pairwise:
+ * fixed marginals mu_j / sum mu_j, one marginal per free node) to FP64 rounding.
+ * Plan entries are the FP64-grade check's (double-float exponent, ~1e-7
+ * relative each; FP64 handles: FP64); every sum over them is FP64. */
+typedef struct tree_ot_round_result {
+    int32_t side;                   /* colour class S that was rounded                    */
+    int64_t half_steps;             /* iterate rounded (half-steps applied to the problem) */
+    double residual_sum_l1;         /* stopping sum r of the input plans (their FP64 sums) */
+    double transport_cost;          /* sum_e <C_e, B_e> of the input plans                 */
+    double rounded_transport_cost;  /* sum_e <C_e, B^_e> (+inf if a correction lands on a
+                                       +inf cost entry)                                   */
+    double c_inf;                   /* max_e max |C_e| over finite entries                 */
+    double bound;                   /* 2 eps |E| log(d) + 4 C_inf r, d = max_j n_j: the
+                                       bound of lem:round_applied on rounded_transport_cost
+                                       minus the unregularised optimum                     */
+} tree_ot_round_result;
+
+/* Round the plans of the current potentials of every problem.  side = -1: per
+ * problem, the colour its last half-step did not update (a retired problem's
+ * last half-step is the one it retired at; a problem with no half-step yet
+ * returns TREE_OT_ERR_STATE); side = 0 or 1: that colour class for every
+ * problem.  results: host [num_probs] (may be NULL).  The rounded plans are kept
+ * implicitly (row scales and rank-one factors, a few vectors per edge) until the
+ * potentials next change; buffers are allocated on the first call.
+ * Synchronises cuda_stream. */
+int tree_ot_round(tree_ot_handle *h, void *cuda_stream, int32_t side, tree_ot_round_result *results);
+
+/* Write the rounded plan of edge `edge` (0 <= edge < J-1) of problem `prob` from
+ * the last tree_ot_round into plan_out: DEVICE memory, caller-owned, n_a x ld
+ * FP64 row-major with rows on node a = edges[edge][0] (ld >= n_b; entries past
+ * n_b are left alone).  TREE_OT_ERR_STATE if the potentials changed since the
+ * last tree_ot_round.  Enqueued on cuda_stream; does not synchronise. */
+int tree_ot_round_plan(tree_ot_handle *h, void *cuda_stream, int32_t prob, int32_t edge, double *plan_out,
+                       int64_t ld);
+
 /* Copy the potential vector of directed edge `dedge` (0 <= dedge < 2(J-1), see
  * the numbering above) of problem p to / from host memory (FP64, n_owner values).
  * set_potentials is how warm starts and checkpoint resumes enter; the free-node

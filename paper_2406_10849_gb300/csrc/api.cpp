@@ -256,6 +256,16 @@ struct tree_ot_handle {
   int64_t* d_deadline = nullptr;           // per-problem latest retirement half-step
   std::vector<int64_t> h_deadline;
   std::vector<void*> owned;
+  // rounding (tree_ot_round): buffers allocated on first use, the last rounding's tasks
+  double *d_rsum = nullptr, *d_rtgt = nullptr, *d_rxy = nullptr, *d_rs2 = nullptr, *d_rer = nullptr;
+  double *d_racc = nullptr, *d_rnmass = nullptr;
+  int32_t* d_rside = nullptr;
+  RoundTask* d_rtasks = nullptr;
+  int64_t rtask_cap = 0;
+  std::vector<RoundTask> rtasks;
+  std::vector<int32_t> rt_begin, rt_count;  // per edge: its tasks in rtasks
+  int64_t pot_version = 0;                  // bumped by every call that changes potentials
+  int64_t round_version = -1;               // pot_version the last rounding saw
 
   int64_t hs_host = 0;
   cudaStream_t hstream = nullptr;
@@ -1123,6 +1133,37 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
 // exported entry points
 // ---------------------------------------------------------------------------
 
+namespace {
+// device tables of the last rounding (see tree_ot_round)
+RoundArgs round_args(const tree_ot_handle* h) {
+  RoundArgs a{};
+  a.tasks = h->d_rtasks;
+  a.ntasks = (int32_t)h->rtasks.size();
+  a.dedges = h->d_dedges;
+  a.ndedges = (int32_t)h->dedges.size();
+  a.edges = h->d_edges;
+  a.nodes = h->d_nodes;
+  a.probs = h->d_probs;
+  a.node_dedges = h->d_node_dedges;
+  a.side = h->d_rside;
+  a.nmass = h->d_rnmass;
+  a.ah = h->d_ah;
+  a.al = h->d_al;
+  a.f = h->d_f;
+  a.Z = h->d_Z;
+  a.logg = h->d_logg;
+  a.mu = h->d_mu;
+  a.coords = h->d_coords;
+  a.rsum = h->d_rsum;
+  a.tgt = h->d_rtgt;
+  a.xy = h->d_rxy;
+  a.s2 = h->d_rs2;
+  a.er = h->d_rer;
+  a.edge_acc = h->d_racc;
+  return a;
+}
+}  // namespace
+
 extern "C" {
 
 void tree_ot_default_options(tree_ot_options* opt) {
@@ -1616,6 +1657,7 @@ int tree_ot_destroy(tree_ot_handle* h) {
 int tree_ot_reset(tree_ot_handle* h, void* cuda_stream) {
   g_err.clear();
   if (!h) return fail(TREE_OT_ERR_ARG, "handle is NULL");
+  ++h->pot_version;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   RC_TRY(reset_state(h, s));
   h->h_done.clear();
@@ -1627,6 +1669,7 @@ int tree_ot_reset(tree_ot_handle* h, void* cuda_stream) {
 int tree_ot_half_steps(tree_ot_handle* h, void* cuda_stream, int64_t T) {
   g_err.clear();
   if (!h || T < 0) return fail(TREE_OT_ERR_ARG, "handle is NULL or T < 0");
+  ++h->pot_version;
   return queue_half_steps(h, T, false, (cudaStream_t)cuda_stream);
 }
 
@@ -1640,6 +1683,7 @@ int tree_ot_node_update(tree_ot_handle* h, void* cuda_stream, int32_t colour) {
   g_err.clear();
   if (!h || (colour != 0 && colour != 1)) return fail(TREE_OT_ERR_ARG, "handle is NULL or colour not 0/1");
   if ((h->hs_host % 2) != colour) return fail(TREE_OT_ERR_STATE, "node_update colour does not follow the schedule");
+  ++h->pot_version;
   RC_TRY(launch_update(h, colour, false, (cudaStream_t)cuda_stream));
   ++h->hs_host;
   return TREE_OT_OK;
@@ -1648,6 +1692,7 @@ int tree_ot_node_update(tree_ot_handle* h, void* cuda_stream, int32_t colour) {
 int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results) {
   g_err.clear();
   if (!h) return fail(TREE_OT_ERR_ARG, "handle is NULL");
+  ++h->pot_version;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const auto t0 = std::chrono::steady_clock::now();
   const int G = h->opt.check_every;
@@ -1858,6 +1903,144 @@ int tree_ot_residual_history(tree_ot_handle* h, void* cuda_stream, int32_t prob,
   return TREE_OT_OK;
 }
 
+int tree_ot_round(tree_ot_handle* h, void* cuda_stream, int32_t side, tree_ot_round_result* results) {
+  g_err.clear();
+  if (!h || side < -1 || side > 1) return fail(TREE_OT_ERR_ARG, "bad handle or side (-1, 0 or 1)");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the iterate of every problem: a retired problem's potentials stopped at its retirement
+  std::vector<int32_t> done(h->nprob, 0);
+  std::vector<int64_t> done_at(h->nprob, 0);
+  CUDA_TRY(cudaMemcpyAsync(done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(done_at.data(), h->d_done_at, sizeof(int64_t) * h->nprob, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int32_t> pside(h->nprob);
+  std::vector<int64_t> piter(h->nprob);
+  for (int p = 0; p < h->nprob; ++p) {
+    piter[p] = done[p] ? done_at[p] : h->hs_host;
+    if (side < 0 && piter[p] < 1)
+      return fail(TREE_OT_ERR_STATE, "problem " + std::to_string(p) +
+                                         " has had no half-step: no colour class is known to be matched");
+    // half-step t updated colour (t + 1) % 2, so colour t % 2 missed its marginals
+    pside[p] = side >= 0 ? side : (int32_t)(piter[p] % 2);
+  }
+  // buffers on first use
+  if (!h->d_rsum) {
+    int rc = 0;
+    if ((rc = h->alloc(&h->d_rsum, h->vec_len)) || (rc = h->alloc(&h->d_rtgt, h->vec_len)) ||
+        (rc = h->alloc(&h->d_rxy, h->vec_len)) || (rc = h->alloc(&h->d_rs2, h->vec_len)) ||
+        (rc = h->alloc(&h->d_rer, h->vec_len)) || (rc = h->alloc(&h->d_racc, (int64_t)kRoundAcc * h->edges.size())) ||
+        (rc = h->alloc(&h->d_rnmass, (int64_t)h->nodes.size())) || (rc = h->alloc(&h->d_rside, h->nprob)))
+      return rc;
+    // mass of every fixed node's mu (targets are taken at unit mass)
+    std::vector<double> nm(h->nodes.size(), 1.0);
+    for (size_t j = 0; j < h->nodes.size(); ++j)
+      if (h->nodes[j].fixed) {
+        double m = 0.0;
+        for (double v : h->mu[j]) m += v;
+        nm[j] = m;
+      }
+    CUDA_TRY(cudaMemcpyAsync(h->d_rnmass, nm.data(), sizeof(double) * nm.size(), cudaMemcpyHostToDevice, s));
+  }
+  // tasks: 64 rows of every plan with its rows on the rounded side
+  h->rtasks.clear();
+  h->rt_begin.assign(h->edges.size(), 0);
+  h->rt_count.assign(h->edges.size(), 0);
+  for (int32_t e = 0; e < (int32_t)h->edges.size(); ++e) {
+    for (int k = 0; k < 2; ++k) {
+      const int32_t di = 2 * e + k;
+      const DEdgeD& d = h->dedges[di];
+      if (h->nodes[d.owner].colour != pside[d.prob]) continue;
+      h->rt_begin[e] = (int32_t)h->rtasks.size();
+      const int32_t n = h->nodes[d.owner].n;
+      for (int32_t o = 0; o < n; o += 64) h->rtasks.push_back({di, o, std::min(64, n - o), 0});
+      h->rt_count[e] = (int32_t)h->rtasks.size() - h->rt_begin[e];
+    }
+  }
+  if ((int64_t)h->rtasks.size() > h->rtask_cap) {
+    int rc = h->alloc(&h->d_rtasks, (int64_t)h->rtasks.size());
+    if (rc) return rc;
+    h->rtask_cap = (int64_t)h->rtasks.size();
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_rtasks, h->rtasks.data(), sizeof(RoundTask) * h->rtasks.size(),
+                           cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(h->d_rside, pside.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+  // the plans' operands, as for the check
+  RC_TRY(sync_potentials(h, s));
+  if (!h->fp64)
+    CUDA_TRY(launch_operand(h->d_f, h->d_Z, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs,
+                            (int32_t)h->dedges.size(), 1.0, false, h->d_ah, h->d_al, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_rsum, 0, sizeof(double) * h->vec_len, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_rs2, 0, sizeof(double) * h->vec_len, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_racc, 0, sizeof(double) * kRoundAcc * h->edges.size(), s));
+  const RoundArgs a = round_args(h);
+  CUDA_TRY(launch_round(a, h->fp64, s));
+  std::vector<double> acc((size_t)kRoundAcc * h->edges.size()), q(h->vec_len);
+  CUDA_TRY(cudaMemcpyAsync(acc.data(), h->d_racc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(q.data(), h->d_rsum, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->round_version = h->pot_version;
+  if (!results) return TREE_OT_OK;
+  for (int p = 0; p < h->nprob; ++p) {
+    tree_ot_round_result r{};
+    r.side = pside[p];
+    r.half_steps = piter[p];
+    // stopping sum of the input plans from their own FP64 marginals (q of every directed edge)
+    double rsum = 0.0;
+    int32_t dmax = 1;
+    const int32_t nb = h->prob_node_base[p], J = h->prob_nodes[p];
+    for (int32_t j = nb; j < nb + J; ++j) {
+      const NodeD& nd = h->nodes[j];
+      dmax = std::max(dmax, nd.n);
+      if (nd.fixed) {
+        const DEdgeD& d = h->dedges[h->node_dedges[nd.dedge_begin]];
+        for (int32_t x = 0; x < nd.n; ++x) rsum += std::fabs(q[d.off + x] - h->mu[j][x]);
+      } else {
+        for (int32_t x = 0; x < nd.n; ++x) {
+          double qb = 0.0;
+          for (int32_t i = 0; i < nd.deg; ++i) qb += q[h->dedges[h->node_dedges[nd.dedge_begin + i]].off + x];
+          qb /= nd.deg;
+          for (int32_t i = 0; i < nd.deg; ++i)
+            rsum += std::fabs(q[h->dedges[h->node_dedges[nd.dedge_begin + i]].off + x] - qb);
+        }
+      }
+    }
+    double tc = 0.0, trc = 0.0, cinf = 0.0;
+    for (int32_t e = h->prob_edge_base[p]; e < h->prob_edge_base[p] + J - 1; ++e) {
+      const double* v = &acc[(size_t)kRoundAcc * e];
+      tc += v[0];
+      trc += v[1] + (v[3] > 0.0 ? v[2] / v[3] : 0.0);
+      double cm;
+      std::memcpy(&cm, &v[4], sizeof(double));
+      cinf = std::max(cinf, cm);
+    }
+    r.residual_sum_l1 = rsum;
+    r.transport_cost = tc;
+    r.rounded_transport_cost = trc;
+    r.c_inf = cinf;
+    r.bound = 2.0 * h->probs[p].eps * (J - 1) * std::log((double)dmax) + 4.0 * cinf * rsum;
+    results[p] = r;
+  }
+  return TREE_OT_OK;
+}
+
+int tree_ot_round_plan(tree_ot_handle* h, void* cuda_stream, int32_t prob, int32_t edge, double* plan_out,
+                       int64_t ld) {
+  g_err.clear();
+  if (!h || !plan_out || prob < 0 || prob >= h->nprob || edge < 0 || edge >= h->prob_nodes[prob] - 1)
+    return fail(TREE_OT_ERR_ARG, "bad handle, problem, edge or output pointer");
+  const int32_t e = h->prob_edge_base[prob] + edge;
+  if (ld < h->edges[e].nb) return fail(TREE_OT_ERR_ARG, "ld must be at least the column count n_b");
+  if (h->round_version != h->pot_version || h->rt_count.empty())
+    return fail(TREE_OT_ERR_STATE, "call tree_ot_round after the potentials last changed");
+  RoundArgs a = round_args(h);
+  a.tasks = h->d_rtasks + h->rt_begin[e];
+  a.ntasks = h->rt_count[e];
+  a.plan_out = plan_out;
+  a.plan_ld = ld;
+  CUDA_TRY(launch_round_plan(a, h->fp64, (cudaStream_t)cuda_stream));
+  return TREE_OT_OK;
+}
+
 int tree_ot_get_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, int32_t dedge, double* out) {
   g_err.clear();
   if (!h || !out || prob < 0 || prob >= h->nprob || dedge < 0 || dedge >= 2 * (h->prob_nodes[prob] - 1))
@@ -1885,6 +2068,7 @@ int tree_ot_set_potentials(tree_ot_handle* h, void* cuda_stream, int32_t prob, i
   const int32_t n = h->nodes[d.owner].n;
   for (int32_t x = 0; x < n; ++x)
     if (!std::isfinite(in[x])) return fail(TREE_OT_ERR_NONFINITE, "potential entries must be finite");
+  ++h->pot_version;
   double z = 0.0;
   CUDA_TRY(cudaMemcpyAsync(&z, h->d_Z + d.owner, sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1955,6 +2139,7 @@ int tree_ot_set_potentials_batch(tree_ot_handle* h, void* cuda_stream, int32_t c
   if (!h || count < 0 || (count > 0 && (!probs || !dedges || !values)))
     return fail(TREE_OT_ERR_ARG, "bad handle, count or pointer");
   if (count == 0) return TREE_OT_OK;
+  ++h->pot_version;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int32_t* d_dlist = nullptr;
   DEdgeD* d_picked = nullptr;

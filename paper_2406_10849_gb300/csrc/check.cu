@@ -12,60 +12,11 @@
 #include <cmath>
 
 #include "internal.h"
+#include "plan_entry.cuh"
 #include "ptx.cuh"
 
 namespace treeot {
 namespace {
-
-struct DF {
-  float hi, lo;
-};
-
-// The error-free transformations below use the _rn intrinsics, which the
-// compiler never contracts into FMAs: a product fused into a neighbouring
-// addition would no longer be the rounded value the error term was taken from.
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-
-// exact-ish square of (p - q) as a double-float
-__device__ __forceinline__ DF sq_diff(float p, float q) {
-  const DF d = two_sum(p, -q);
-  const float h = __fmul_rn(d.hi, d.hi);
-  const float e = fmaf(2.f * d.hi, d.lo, fmaf(d.hi, d.hi, -h));
-  return {h, e};
-}
-
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const DF s = two_sum(a.hi, b.hi);
-  return {s.hi, s.lo + a.lo + b.lo};
-}
-
-// C(x,y) as a double-float; dense costs are exact FP32 values
-__device__ __forceinline__ DF cost_df(const CheckArgs& A, const EdgeD& e, const ProbD& P, int x, int y,
-                                     const float* pa, const float* pb) {
-  if (P.cost_kind == 0) return {e.C[(int64_t)x * e.ld + y], 0.f};
-  DF c = sq_diff(pa[0], pb[0]);
-  if (P.dim > 1) c = df_add(c, sq_diff(pa[1], pb[1]));
-  if (P.dim > 2) c = df_add(c, sq_diff(pa[2], pb[2]));
-  return c;
-}
-
-// B = exp(a + b - C * k), k = scale / eps as (kh, kl); returns B and adds C*B to tc
-__device__ __forceinline__ float plan_entry(float ah, float al, float bh, float bl, DF c, float kh, float kl,
-                                            float& cost_out) {
-  const DF s = two_sum(ah, bh);
-  const float p = __fmul_rn(c.hi, kh);  // the rounded product; pe holds what it lost
-  const float pe = fmaf(c.hi, kl, fmaf(c.lo, kh, fmaf(c.hi, kh, -p)));
-  const DF d = two_sum(s.hi, -p);
-  const float lo = (s.lo + d.lo) + (al + bl) - pe;
-  cost_out = c.hi + c.lo;
-  const float E = expf(d.hi);
-  return E == 0.f ? 0.f : E * (1.f + lo);
-}
 
 // One pass over every plan entry.  A ROW task covers up to 64 rows of an edge
 // (8 warps x 8 rows); the warps walk the columns together, 32 at a time (a lane
@@ -123,7 +74,7 @@ __global__ void __launch_bounds__(256) check_kernel(CheckArgs A) {
           if (!(rah[r] > -INFINITY)) continue;
           const int x = t.o0 + warp * kChkRows + r;
           float cst;
-          const float B = plan_entry(rah[r], ral[r], bh, bl, cost_df(A, e, P, x, y, rp[r], pb), kh, kl, cst);
+          const float B = plan_entry(rah[r], ral[r], bh, bl, cost_df(e, P, x, y, rp[r], pb), kh, kl, cst);
           float y1 = B - rc[r];
           float t1 = rs[r] + y1;
           rc[r] = (t1 - rs[r]) - y1;

@@ -87,6 +87,21 @@ class Result(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class RoundResult(C.Structure):
+    _fields_ = [
+        ("side", C.c_int32),
+        ("half_steps", C.c_int64),
+        ("residual_sum_l1", C.c_double),
+        ("transport_cost", C.c_double),
+        ("rounded_transport_cost", C.c_double),
+        ("c_inf", C.c_double),
+        ("bound", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # every exported symbol of include/tree_ot.h with its ctypes signature
 SIGNATURES = {
     "tree_ot_default_options": (None, [C.POINTER(Options)]),
@@ -104,6 +119,8 @@ SIGNATURES = {
     "tree_ot_node_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "tree_ot_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Result)]),
     "tree_ot_marginals": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_round": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(RoundResult)]),
+    "tree_ot_round_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64]),
     "tree_ot_residual_history": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tree_ot_get_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
@@ -362,6 +379,28 @@ class Solver:
         n = int(self.problems[prob].n[node])
         out = np.zeros(n, np.float64)
         _check(_lib.tree_ot_marginals(self.h, prob, node, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def round(self, side: int = -1):
+        """tree_ot_round: round every problem's plans (the mismatched colour class by default);
+        returns one dict per problem (costs before / after rounding, r, C_inf, the bound)."""
+        res = (RoundResult * len(self._m))()
+        _check(_lib.tree_ot_round(self.h, self._s(), int(side), res))
+        return [r.as_dict() for r in res]
+
+    def round_plan(self, prob: int, edge: int, out=None):
+        """tree_ot_round_plan into a CUDA float64 (n_a, n_b) tensor (rows on edges[edge][0])."""
+        import torch
+        p = self.problems[prob]
+        a, b = (int(v) for v in p.edges[edge])
+        shape = (int(p.n[a]), int(p.n[b]))
+        if out is None:
+            out = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        if (tuple(out.shape) != shape or out.dtype != torch.float64 or not out.is_cuda or out.stride(1) != 1
+                or out.device.index != torch.cuda.current_device()):
+            raise ValueError(f"out must be a CUDA float64 {shape} matrix with unit column stride on the current device")
+        _check(_lib.tree_ot_round_plan(self.h, self._s(), int(prob), int(edge), C.c_void_p(out.data_ptr()),
+                                       int(out.stride(0))))
         return out
 
     def residual_history(self, prob: int, first: int, count: int):
