@@ -67,6 +67,16 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def read_bf16_peak():
+    """Dense BF16 tensor throughput (TFLOP/s): the measured burst figure, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "bf16_tflops (burst) of measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 KERNEL_SOURCES = {"apply_dense_kernel": "apply_f32.cu", "apply_dense_tma_kernel": "apply_tma.cu"}
 
 
@@ -234,13 +244,6 @@ def run_reference(args):
 # microbenchmark on this GPU (115 and 30 per clock per SM achieved).
 FP32_LANES_PER_CLK = 128.0
 EX2_PER_CLK = 32.0
-# FP32-pipe lane operations the recomputed-cost apply spends per element (2-D
-# points): difference, square, difference, FMA for |p - q|^2; operand minus
-# frame, two FMAs with s = s_hi + s_lo, low-part add for the argument; one add
-# into the sum.  The running maximum uses the ALU pipe and ex2 the MUFU.
-RECOMP_FP32_OPS_PER_ELEM = 9.0
-
-
 def fp32_peak(sms: int, mhz: float) -> float:
     return FP32_LANES_PER_CLK * sms * mhz * 1e6
 
@@ -249,15 +252,115 @@ def sfu_peak(sms: int, mhz: float) -> float:
     return EX2_PER_CLK * sms * mhz * 1e6
 
 
-def run_batched(args):
-    """Independent random trees (4..32 nodes, n_j in 128..2048, 2-D points,
-    eps log-uniform in [0.002, 0.05], squared-Euclidean cost recomputed in the
-    kernel) in one handle; one step = one half-step over all trees."""
+# FP32-pipe lane operations per element the recomputed-cost apply needs by the
+# survey's algorithmic count (2-D points): the squared distance (two differences,
+# a square and an FMA), the argument (operand minus frame, scale), the sum --
+# about 8 -- beside one ex2 on the MUFU.
+RECOMP_ALG_OPS_PER_ELEM = 8.0
+
+
+def bench_batched(dev, stream, steps: int, warmup: int, converge: bool, num_trees: int = 512, rank: int = 0,
+                  world: int = 1, dist=None):
+    """Independent random trees (4..32 nodes, n_j in 128..2048, 2-D points, eps
+    log-uniform in [0.002, 0.05], squared-Euclidean cost recomputed in the kernel)
+    in one handle; this rank's share of the batch when world > 1.  One step = one
+    half-step over the rank's trees.  Returns a dict (timed with CUDA events on the
+    launching stream, per-kernel times from the library's launch timing)."""
     import torch
 
     import gen
     import paper_2406_10849_gb300 as T
     from paper_2406_10849_gb300 import shard
+
+    allp = gen.batched_problems(seed=4000, num_trees=num_trees)
+    probs, mine = shard.shard_problems(allp, rank, world) if world > 1 else (allp, list(range(len(allp))))
+    t0 = time.perf_counter()
+    solver = T.Solver(probs, T.options(precision="fp32"), stream=stream)
+    create_s = time.perf_counter() - t0
+    stats = solver.plan_stats()
+    elems = stats["elements_per_half_step"]
+    n_apply = stats["edges"]
+    for i in range(warmup):
+        solver.apply(i % 2)
+        solver.node_update(i % 2)
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    c0 = warmup % 2
+    solver.profile(True)
+    with ClockSampler(dev.index or 0) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for i in range(steps):
+            solver.apply((c0 + i) % 2)
+            solver.node_update((c0 + i) % 2)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+    prof = solver.profile_read()
+    solver.profile(False)
+    clocks = clk.summary()
+    t_ms = start.elapsed_time(stop)
+    t_max = shard.max_over_ranks(t_ms, dist, dev)
+    total_apply = shard.sum_over_ranks(n_apply, dist, dev)
+    apply_ms = prof["apply_recompute"][0] / steps   # every launch of a half-step (one per dimension)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks["sm_mhz"] or 2070.0
+    elem_rate = elems / (apply_ms / 1e3)
+    peak = fp32_peak(sms, mhz)
+    out = {
+        "workload": f"batched{num_trees}_trees_2d_sqeuclid", "trees": len(probs), "edges": n_apply,
+        "elements_per_step": elems, "create_s": create_s,
+        "edge_applies_per_s": total_apply * steps / (t_max / 1e3), "ms_per_step": t_max / steps,
+        "apply_ms": apply_ms, "node_update_ms": prof["node_update"][0] / steps,
+        "elements_per_s": elem_rate,
+        "roofline": {"bound": "alu", "kernel": "apply_recomp_kernel<2>",
+                     "achieved": RECOMP_ALG_OPS_PER_ELEM * elem_rate / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                     "frac": RECOMP_ALG_OPS_PER_ELEM * elem_rate / peak,
+                     "ops_per_element": RECOMP_ALG_OPS_PER_ELEM,
+                     "peak_kind": f"FP32 lanes: 128/clk/SM x {sms} SMs x {mhz:.0f} MHz (median SM clock under load)",
+                     "sfu_frac": elem_rate / sfu_peak(sms, mhz), "traffic": None},
+        "autotuned_tile": {"output_block": stats["recompute_output_block"],
+                           "ctas_per_sm": stats["recompute_ctas_per_sm"],
+                           "register_variant": stats["recompute_variant"]},
+        "clocks": clocks, "gpu_launches": 2 * steps,
+    }
+    if converge and rank == 0 and world == 1:
+        solver.close()
+        s2 = T.Solver(probs, T.options(precision="fp32", tol=1e-6, tol_kind="max", max_half_steps=20000),
+                      stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, res = s2.solve()
+        dt = time.perf_counter() - t0
+        hs = [r["half_steps"] for r in res]
+        s2.profile(True)
+        t0 = time.perf_counter()
+        rr = s2.round()
+        dt_round = time.perf_counter() - t0
+        pr = s2.profile_read()
+        s2.close()
+        out["solve_to_1e-6"] = {"seconds": dt, "certified": sum(1 for r in res if r["status"] == 0),
+                                "trees": len(res), "half_steps_median": int(np.median(hs)),
+                                "half_steps_max": int(max(hs)),
+                                "worst_max_marginal_l1": max(r["max_marginal_l1"] for r in res)}
+        out["rounding"] = {"seconds": dt_round, "kernel_ms": pr.get("round", (0.0, 0))[0],
+                           "max_abs_cost_change": max(abs(r["rounded_transport_cost"] - r["transport_cost"])
+                                                      for r in rr),
+                           "worst_bound": max(r["bound"] for r in rr)}
+    else:
+        solver.close()
+    return out
+
+
+def run_batched(args):
+    """--workload batched: the batched trees as the JSON line's own workload.  Under
+    torchrun the ranks split the 512 trees (disjoint subsets balanced by cost; no
+    data-path collective) and value is the whole job's edge applies per second."""
+    import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,85 +372,170 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    probs = gen.batched_problems(seed=4000, num_trees=args.trees)
-    solver = T.Solver(probs, T.options(precision="fp32"), stream=stream)
-    stats = solver.plan_stats()
-    elems = stats["elements_per_half_step"]
-    n_apply = stats["edges"]
-    for i in range(args.warmup):
-        solver.apply(i % 2)
-        solver.node_update(i % 2)
-    torch.cuda.synchronize(dev)
-    K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
-    c0 = args.warmup % 2
-    with ClockSampler(local) as clk:
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        start.record(stream)
-        for i in range(K):
-            ev[i][0].record(stream)
-            solver.apply((c0 + i) % 2)
-            ev[i][1].record(stream)
-            solver.node_update((c0 + i) % 2)
-        stop.record(stream)
-        torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-    clocks = clk.summary()
-    t_ms = start.elapsed_time(stop)
-    t_max = shard.max_over_ranks(t_ms, dist, dev)
-    apply_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = clocks["sm_mhz"] or 2070.0
-    elem_rate = elems / (apply_ms / 1e3)
-    achieved = RECOMP_FP32_OPS_PER_ELEM * elem_rate
-    peak = fp32_peak(sms, mhz)
-    extra = {}
-    if rank == 0 and not args.no_converge:
-        solver.reset()
-        s2 = T.Solver(probs, T.options(precision="fp32", tol=1e-6, tol_kind="max", max_half_steps=20000),
-                      stream=stream)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        rc, res = s2.solve()
-        dt = time.perf_counter() - t0
-        s2.close()
-        hs = [r["half_steps"] for r in res]
-        extra["solve_to_1e-6"] = {"seconds": dt, "converged": sum(1 for r in res if r["status"] == 0),
-                                  "trees": len(res), "half_steps_median": int(np.median(hs)),
-                                  "half_steps_max": int(max(hs)),
-                                  "worst_max_marginal_l1": max(r["max_marginal_l1"] for r in res)}
-    solver.close()
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
-    line = {
-        "metric": METRIC, "value": world * n_apply * K / (t_max / 1e3), "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched{args.trees}_trees_2d_sqeuclid", "trees": args.trees, "edges": n_apply,
-                   "elements_per_step": elems, "step": "one half-step over every tree (apply + node update)",
-                   "l2": "no stored costs; per-step vectors exceed L2",
-                   "autotuned_tile": {"output_block": stats["recompute_output_block"],
-                                      "ctas_per_sm": stats["recompute_ctas_per_sm"],
-                                      "register_variant": stats["recompute_variant"]}},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "apply_recomp_kernel<2>",
-                     "apply_ms_avg": apply_ms, "elements_per_s": elem_rate,
-                     "ops_per_element": RECOMP_FP32_OPS_PER_ELEM,
-                     "peak_kind": f"FP32 lanes: 128/clk/SM x {sms} SMs x {mhz:.0f} MHz (median SM clock under load)",
-                     "sfu_frac": elem_rate / sfu_peak(sms, mhz)},
-        "clocks": clocks, "gpu_launches": 2 * K,
-    }
-    line.update(extra)
-    print(json.dumps(line), flush=True)
+    b = bench_batched(dev, stream, args.steps, args.warmup, not args.no_converge, args.trees, rank, world, dist)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": b["edge_applies_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "trees": args.trees, "edges_rank0": b["edges"],
+                       "elements_per_step_rank0": b["elements_per_step"],
+                       "step": "one half-step over every tree (apply + node update); ranks split the trees",
+                       "l2": "no stored costs; per-step vectors exceed L2",
+                       "autotuned_tile": b["autotuned_tile"]},
+            "roofline": b["roofline"], "clocks": b["clocks"], "gpu_launches": b["gpu_launches"],
+        }
+        for k in ("solve_to_1e-6", "rounding"):
+            if k in b:
+                line[k] = b[k]
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_stars(dev, stream, stars: int, side: int, steps: int, warmup: int, converge: bool,
+                refine_tol: float = 1.5e-6):
+    """The shared-kernel BF16 phase on a batch of barycenter stars (8 fixed leaves on
+    a side x side grid, free centre, eps 0.005: every directed edge of every star
+    shares one Gibbs kernel) against the FP32 recomputed-cost path: a half-step of
+    each (CUDA events on the launching stream, per-kernel times from the library's
+    launch timing) and, when converge, the batch to a certified max marginal
+    L1 <= 1e-6 in each form."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+
+    probs = gen.warmstart_stars(9_000_000, stars, side=side, eps=0.005)
+    n = side * side
+    cols = 8 * stars  # directed edges applied per half-step
+    forms = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0, refine_tol=0.0)}
+    res = {}
+    clocks = None
+    for name, kw in forms.items():
+        s = T.Solver(probs, T.options(**kw), stream=stream)
+        s.half_steps(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s.profile(True)
+        with ClockSampler(dev.index or 0) as clk:
+            e0.record(stream)
+            s.half_steps(steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        prof = s.profile_read()
+        s.profile(False)
+        res[name] = {"ms_per_half_step": e0.elapsed_time(e1) / steps,
+                     "kernel_ms_per_half_step": {k: v[0] / steps for k, v in prof.items()}}
+        if name == "bf16_shared_kernel":
+            clocks = clk.summary()
+        s.close()
+    if converge:
+        solve = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0,
+                                                               refine_tol=refine_tol)}
+        for name, kw in solve.items():
+            s = T.Solver(probs, T.options(tol=1e-6, tol_kind="max", max_half_steps=20000, **kw), stream=stream)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc, out = s.solve()
+            dt = time.perf_counter() - t0
+            s.close()
+            hs = np.array([r["half_steps"] for r in out], dtype=np.float64)
+            res[name]["time_to_1e-6_s"] = dt
+            res[name]["half_steps_mean"] = float(hs.mean())
+            res[name]["bf16_half_steps_mean"] = float(np.mean([r["lowp_half_steps"] for r in out]))
+            res[name]["certified"] = int(sum(r["status"] == 0 for r in out))
+            res[name]["worst_max_marginal_l1"] = max(r["max_marginal_l1"] for r in out)
+    ph = res["bf16_shared_kernel"]
+    prod_ms = ph["kernel_ms_per_half_step"].get("sk_product", float("nan"))
+    flops3 = 3 * 2 * n * n * cols       # the three split products
+    flops1 = 2 * n * n * cols           # the method's one product
+    bf16_peak, kind = read_bf16_peak()
+    out = {
+        "workload": f"stars{stars}_grid{n}_eps0.005", "stars": stars, "n": n,
+        "edge_applies_per_s": cols / (ph["ms_per_half_step"] / 1e3),
+        "plain_fp32_edge_applies_per_s": cols / (res["plain_fp32"]["ms_per_half_step"] / 1e3),
+        "speedup_per_half_step": res["plain_fp32"]["ms_per_half_step"] / ph["ms_per_half_step"],
+        "product": {"kernel": "sk_gemm_tc_kernel", "ms_per_launch": prod_ms,
+                    "pflops_3_products": flops3 / (prod_ms / 1e3) / 1e15,
+                    "pflops_method_1_product": flops1 / (prod_ms / 1e3) / 1e15,
+                    "peak_pflops": bf16_peak / 1e3, "peak_kind": kind,
+                    "frac_3_products": flops3 / (prod_ms / 1e3) / 1e12 / bf16_peak,
+                    "frac_method": flops1 / (prod_ms / 1e3) / 1e12 / bf16_peak},
+        "forms": res, "clocks": clocks,
+    }
+    if converge:
+        out["speedup_time_to_1e-6"] = (res["plain_fp32"]["time_to_1e-6_s"]
+                                       / res["bf16_shared_kernel"]["time_to_1e-6_s"])
+    return out
+
+
+def bench_chain(dev, stream, steps: int):
+    """The 5-node chain (n = 64 grid, eps = 0.01, FP64 handle): microseconds per
+    half-step (CUDA events) and the solve to a stopping sum below 1e-9."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+
+    p = gen.chain_problem(seed=1000)
+    s = T.Solver([p], T.options(precision="fp64"), stream=stream)
+    s.half_steps(10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    s.half_steps(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    us = 1e3 * e0.elapsed_time(e1) / steps
+    s.close()
+    s = T.Solver([p], T.options(precision="fp64", tol=1e-9, tol_kind="sum", check_every=2), stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc, res = s.solve()
+    dt = time.perf_counter() - t0
+    rr = s.round()[0]
+    s.close()
+    return {"workload": "chain5_n64_fp64_eps0.01", "us_per_half_step": us,
+            "edge_applies_per_s": p.num_edges / (us / 1e6),
+            "solve_to_1e-9": {"seconds": dt, "half_steps": res[0]["half_steps"], "status": rc,
+                              "residual_sum_l1": res[0]["residual_sum_l1"]},
+            "rounded_transport_cost": rr["rounded_transport_cost"], "transport_cost": rr["transport_cost"]}
+
+
+def bench_star(dev, stream, steps: int):
+    """One barycenter star (8 fixed leaves on a 32 x 32 grid, free centre, eps
+    0.005, squared-Euclidean cost recomputed in the kernel, FP32): microseconds
+    per half-step and the solve to a certified max marginal L1 <= 1e-6."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+
+    p = gen.star_problem(seed=2000)
+    s = T.Solver([p], T.options(precision="fp32"), stream=stream)
+    s.half_steps(10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    s.profile(True)
+    e0.record(stream)
+    s.half_steps(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = s.profile_read()
+    us = 1e3 * e0.elapsed_time(e1) / steps
+    s.close()
+    s = T.Solver([p], T.options(precision="fp32", tol=1e-6, tol_kind="max"), stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc, res = s.solve()
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"workload": "star8_grid1024_sqeuclid_fp32_eps0.005", "us_per_half_step": us,
+            "edge_applies_per_s": p.num_edges / (us / 1e6),
+            "kernel_us_per_half_step": {k: 1e3 * v[0] / steps for k, v in prof.items()},
+            "solve_to_1e-6": {"seconds": dt, "half_steps": res[0]["half_steps"], "status": rc,
+                              "max_marginal_l1": res[0]["max_marginal_l1"]}}
 
 
 def run_warmstart(args):
@@ -451,70 +639,28 @@ def run_warmstart(args):
 
 
 def run_stars(args):
-    """The shared-kernel BF16 phase on a batch of barycenter stars (8 fixed
-    leaves on a side x side grid, free centre, eps 0.005: every directed edge of
-    every star shares one Gibbs kernel).  Times a half-step of the phase and of
-    the FP32 recomputed-cost path with CUDA events on the launching stream, and
-    (unless --no-converge) the whole batch to a certified max marginal L1 <= 1e-6
-    in each form."""
+    """--workload stars: the shared-kernel BF16 phase on a batch of stars as the JSON
+    line's own workload (see bench_stars)."""
     import torch
 
-    import gen
     import paper_2406_10849_gb300 as T
 
     T.load()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    probs = gen.warmstart_stars(9_000_000, args.stars, side=args.side, eps=0.005)
-    n = args.side * args.side
-    cols = 8 * args.stars  # directed edges per half-step
-    forms = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0, refine_tol=0.0)}
-    res = {}
-    for name, kw in forms.items():
-        s = T.Solver(probs, T.options(**kw), stream=stream)
-        s.half_steps(args.warmup)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        with ClockSampler(0) as clk:
-            e0.record(stream)
-            s.half_steps(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-        res[name] = {"ms_per_half_step": e0.elapsed_time(e1) / args.steps, "clocks": clk.summary()}
-        s.close()
-    if not args.no_converge:
-        solve = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0,
-                                                               refine_tol=args.refine_tol)}
-        for name, kw in solve.items():
-            s = T.Solver(probs, T.options(tol=1e-6, tol_kind="max", max_half_steps=20000, **kw), stream=stream)
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            rc, out = s.solve()
-            dt = time.perf_counter() - t0
-            s.close()
-            hs = np.array([r["half_steps"] for r in out], dtype=np.float64)
-            res[name]["time_to_1e-6_s"] = dt
-            res[name]["half_steps_mean"] = float(hs.mean())
-            res[name]["bf16_half_steps_mean"] = float(np.mean([r["lowp_half_steps"] for r in out]))
-            res[name]["certified"] = int(sum(r["status"] == 0 for r in out))
-            res[name]["worst_max_marginal_l1"] = max(r["max_marginal_l1"] for r in out)
-    ms = res["bf16_shared_kernel"]["ms_per_half_step"]
+    b = bench_stars(dev, stream, args.stars, args.side, args.steps, args.warmup, not args.no_converge,
+                    args.refine_tol)
+    ms = b["forms"]["bf16_shared_kernel"]["ms_per_half_step"]
     line = {
         "metric": "edge-kernel applies/sec, shared-kernel BF16 phase (stars on one grid)",
-        "value": cols / (ms / 1e3), "unit": "edge_applies/s", "n_gpus": 1, "steps": args.steps,
+        "value": b["edge_applies_per_s"], "unit": "edge_applies/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 tensor-core product, f32 node update", "data": "synthetic",
-        "config": {"workload": f"stars{args.stars}_grid{n}_eps0.005", "stars": args.stars, "leaves": 8, "n": n,
+        "config": {"workload": b["workload"], "stars": args.stars, "leaves": 8, "n": b["n"],
                    "step": "one half-step over all stars", "refine_tol": args.refine_tol},
-        "plain_fp32_edge_applies_per_s": cols / (res["plain_fp32"]["ms_per_half_step"] / 1e3),
-        "speedup_per_half_step": res["plain_fp32"]["ms_per_half_step"] / ms,
-        "product_flops_per_half_step": 3 * 2 * n * n * cols,
-        "forms": res,
     }
-    if not args.no_converge:
-        line["speedup_time_to_1e-6"] = (res["plain_fp32"]["time_to_1e-6_s"]
-                                        / res["bf16_shared_kernel"]["time_to_1e-6_s"])
+    line.update({k: v for k, v in b.items() if k not in ("workload", "stars", "n")})
     print(json.dumps(line), flush=True)
 
 
@@ -538,6 +684,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-1e-6 solve")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: skip the batched, stars, star and chain measurements")
     ap.add_argument("--nodes", type=int, default=NODES, help="tree size (64 = the benchmark workload)")
     ap.add_argument("--workload", default="prufer", choices=["prufer", "batched", "warmstart", "stars"],
                     help="prufer: the 64-node stored-cost tree (default); batched: independent random trees "
@@ -662,13 +810,25 @@ def main():
         t0 = time.perf_counter()
         rc3, res3 = s3.solve()
         dt3 = time.perf_counter() - t0
+        # rounding of the certified iterate to feasible plans (the step after the sweep)
+        s3.profile(True)
+        t0 = time.perf_counter()
+        rr = s3.round()[0]
+        dt_round = time.perf_counter() - t0
+        pr = s3.profile_read()
         s3.close()
         ttt.update({"bf16_refined_s": dt3, "bf16_half_steps": res3[0]["half_steps"],
+                    "bf16_lowp_half_steps": res3[0]["lowp_half_steps"], "bf16_absorptions": res3[0]["absorptions"],
                     "bf16_max_marginal_l1": res3[0]["max_marginal_l1"], "bf16_status": rc3,
                     "speedup": dt / dt3 if dt3 > 0 else None,
                     "note": "wall time of tree_ot_solve from u = 1 to max marginal L1 < 1e-6 (GPU check), "
                             "setup excluded"})
         extra["time_to_1e-6"] = ttt
+        extra["rounding"] = {"seconds": dt_round, "kernel_ms": pr.get("round", (0.0, 0))[0],
+                             "transport_cost": rr["transport_cost"],
+                             "rounded_transport_cost": rr["rounded_transport_cost"],
+                             "residual_sum_l1": rr["residual_sum_l1"], "bound_lem_round_applied": rr["bound"],
+                             "c_inf": rr["c_inf"]}
     solver.close()
 
     e2e = None
@@ -703,11 +863,23 @@ def main():
         e2e = {"value": world * n_apply * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                "d2h_bytes_per_step": d2h // K,
                "note": f"one public-API solve of {K} half-steps from pinned host buffers per run"}
+        host_costs = None
+        hp = None
 
+    costs = None
+    torch.cuda.empty_cache()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
+    # the other workloads, each with its own numbers (N = 1 only)
+    if world == 1 and not args.no_extra:
+        ks = max(10, min(K, 100))
+        extra["batched"] = bench_batched(dev, stream, ks, args.warmup, not args.no_converge)
+        extra["stars"] = bench_stars(dev, stream, args.stars, args.side, ks, args.warmup, not args.no_converge,
+                                     args.refine_tol)
+        extra["star"] = bench_star(dev, stream, max(ks, 50))
+        extra["chain_fp64"] = bench_chain(dev, stream, max(ks, 200))
     cpu = None if (args.no_cpu or world > 1) else cpu_baseline(p)  # the host baseline: N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,

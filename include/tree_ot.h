@@ -358,6 +358,30 @@ int tree_ot_get_potentials_batch(tree_ot_handle *h, void *cuda_stream, int32_t c
  * bulk-copy staged kernel (TREE_OT_OPT_DENSE_TMA or the autotuner's choice). */
 int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
+/* Launch timing (no paper counterpart: measurement support).  While enabled,
+ * every launch group the handle queues outside CUDA-graph capture (so not the
+ * graph chunks of tree_ot_solve) is bracketed by CUDA events on its stream,
+ * by category; tree_ot_profile_read waits for the last event, returns per
+ * category the summed milliseconds and the number of launch groups, and starts
+ * a new record.  Enabling or disabling also clears the record.  Events are
+ * created on demand and released by tree_ot_destroy. */
+#define TREE_OT_PROF_APPLY_STORED    0  /* stored-cost edge apply (plain-load or staged kernel)   */
+#define TREE_OT_PROF_APPLY_RECOMPUTE 1  /* recomputed-cost edge apply (one launch per dimension)  */
+#define TREE_OT_PROF_APPLY_BF16      2  /* absorbed BF16 apply                                    */
+#define TREE_OT_PROF_SK_BUILD        3  /* shared-kernel phase: envelope, K' and V' builds        */
+#define TREE_OT_PROF_SK_PRODUCT      4  /* shared-kernel phase: the tensor-core product           */
+#define TREE_OT_PROF_SK_FIXUP        5  /* shared-kernel phase: exact recomputation of underflows */
+#define TREE_OT_PROF_NODE_UPDATE     6  /* node update (block updates + stopping terms)          */
+#define TREE_OT_PROF_ABSORB          7  /* absorption step                                        */
+#define TREE_OT_PROF_CHECK           8  /* FP64-grade check                                       */
+#define TREE_OT_PROF_ROUND           9  /* rounding passes                                        */
+#define TREE_OT_PROF_APPLY_FP64     10  /* FP64 edge apply                                        */
+#define TREE_OT_PROF_CATEGORIES     11
+int tree_ot_profile(tree_ot_handle *h, int32_t enable);
+/* ms, launches: host arrays of ncat entries (either may be NULL); synchronises
+ * with the recorded work. */
+int tree_ot_profile_read(tree_ot_handle *h, double *ms, int64_t *launches, int32_t ncat);
+
 /* Allocation-free apply of one stored cost matrix (the paper has no
  * counterpart: this is a packaging of the edge-apply kernel for callers that
  * cannot allocate device memory -- serving runtimes that own every byte of

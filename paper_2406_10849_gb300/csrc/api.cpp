@@ -264,6 +264,14 @@ struct tree_ot_handle {
   int64_t rtask_cap = 0;
   std::vector<RoundTask> rtasks;
   std::vector<int32_t> rt_begin, rt_count;  // per edge: its tasks in rtasks
+  // launch timing (tree_ot_profile): CUDA events around launches queued outside graph capture
+  bool prof_on = false, prof_capturing = false;
+  std::vector<cudaEvent_t> prof_ev;
+  size_t prof_used = 0;
+  struct Span {
+    int32_t cat, i0, i1;
+  };
+  std::vector<Span> prof_spans;
   int64_t pot_version = 0;                  // bumped by every call that changes potentials
   int64_t round_version = -1;               // pot_version the last rounding saw
 
@@ -302,6 +310,27 @@ namespace {
     int rc_ = (call);     \
     if (rc_) return rc_;  \
   } while (0)
+
+// ---- launch timing ----------------------------------------------------------
+// an event of the pool (created on demand); -1 when timing is off or capturing
+int prof_take(tree_ot_handle* h) {
+  if (!h->prof_on || h->prof_capturing) return -1;
+  if (h->prof_used == h->prof_ev.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->prof_ev.push_back(e);
+  }
+  return (int)h->prof_used++;
+}
+int prof_mark(tree_ot_handle* h, cudaStream_t s) {
+  const int i = prof_take(h);
+  if (i >= 0 && cudaEventRecord(h->prof_ev[i], s) != cudaSuccess) return -1;
+  return i;
+}
+void prof_span(tree_ot_handle* h, int cat, int i0, int i1) {
+  if (i0 >= 0 && i1 >= 0) h->prof_spans.push_back({cat, i0, i1});
+}
+cudaEvent_t prof_event(tree_ot_handle* h, int i) { return i >= 0 ? h->prof_ev[i] : nullptr; }
 
 // Apply tasks of both colours, grouped by kernel slot.  rec_ob: largest output
 // block of a recomputed-cost task (256, 512 or 1024 outputs); a task with fewer
@@ -473,8 +502,10 @@ int launch_absorb_step(tree_ot_handle* h, cudaStream_t s) {
   if (!h->lowp) return TREE_OT_OK;
   AbsorbArgs a = absorb_args(h);
   const int grid = std::max(1, std::min<int>(a.ntasks, h->bf16_grid));
+  const int p0 = prof_mark(h, s);
   cudaError_t e = launch_absorb(a, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "absorption launch");
+  prof_span(h, TREE_OT_PROF_ABSORB, p0, prof_mark(h, s));
   return TREE_OT_OK;
 }
 
@@ -483,8 +514,10 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
   ApplyArgs a = apply_args(h, colour);
   if (h->fp64) {
     const int grid = std::max(1, std::min<int>(a.ntasks, h->apply_grid[0]));
+    const int p0 = prof_mark(h, s);
     cudaError_t e = launch_apply_f64(a, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+    prof_span(h, TREE_OT_PROF_APPLY_FP64, p0, prof_mark(h, s));
     return TREE_OT_OK;
   }
   for (int slot = 0; slot < (only_stored ? 1 : kApplySlots); ++slot) {
@@ -493,10 +526,12 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
     a.tasks = h->d_tasks[colour] + h->slot_begin[colour][slot];
     a.ntasks = cnt;
     a.queue = h->d_queue + 2 * (colour * kApplySlots + slot);
+    const int p0 = prof_mark(h, s);
     if (slot == 0 && h->dense_tma) {
       a.stasks = h->d_stasks[colour];
       cudaError_t e = launch_apply_tma(a, std::max(1, std::min<int>(cnt, h->sms)), s);
       if (e != cudaSuccess) return cuda_fail(e, "staged edge apply launch");
+      prof_span(h, TREE_OT_PROF_APPLY_STORED, p0, prof_mark(h, s));
       continue;
     }
     int cap = slot == 0 ? h->apply_grid[0] : h->rec_grid[h->rec_variant][slot];
@@ -504,25 +539,36 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
     const int grid = std::max(1, std::min<int>(cnt, cap));
     cudaError_t e = launch_apply_f32(a, slot, slot == 0 ? 0 : h->rec_variant, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "edge apply launch");
+    prof_span(h, slot == 0 ? TREE_OT_PROF_APPLY_STORED : TREE_OT_PROF_APPLY_RECOMPUTE, p0, prof_mark(h, s));
   }
   if (h->lowp && !only_stored && !h->btasks[colour].empty()) {
     a.tasks = h->d_btasks[colour];
     a.ntasks = (int32_t)h->btasks[colour].size();
     const int grid = std::max(1, std::min<int>(a.ntasks, h->bf16_grid));
+    const int p0 = prof_mark(h, s);
     cudaError_t e = launch_apply_bf16(a, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "absorbed apply launch");
+    prof_span(h, TREE_OT_PROF_APPLY_BF16, p0, prof_mark(h, s));
   }
   if (!only_stored)
     for (const auto& g : h->sk) {
-      cudaError_t e = launch_sk(g.args[colour], g.args[colour].use_tc ? &g.maps[colour] : nullptr, s);
+      const int p0 = prof_mark(h, s), m0 = prof_take(h), m1 = prof_take(h);
+      cudaError_t e = launch_sk(g.args[colour], g.args[colour].use_tc ? &g.maps[colour] : nullptr, s,
+                                prof_event(h, m0), prof_event(h, m1));
       if (e != cudaSuccess) return cuda_fail(e, "shared-kernel apply launch");
+      const int p1 = prof_mark(h, s);
+      prof_span(h, TREE_OT_PROF_SK_BUILD, p0, m0);
+      prof_span(h, TREE_OT_PROF_SK_PRODUCT, m0, m1);
+      prof_span(h, TREE_OT_PROF_SK_FIXUP, m1, p1);
     }
   return TREE_OT_OK;
 }
 
 int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
+  const int p0 = prof_mark(h, s);
   cudaError_t e = launch_node_update(node_args(h, colour, retire), h->fp64, s);
   if (e != cudaSuccess) return cuda_fail(e, "node update launch");
+  prof_span(h, TREE_OT_PROF_NODE_UPDATE, p0, prof_mark(h, s));
   if (!h->fp64) h->f_stale = true;
   return TREE_OT_OK;
 }
@@ -628,7 +674,9 @@ int build_graph(tree_ot_handle* h, int len) {
   CUDA_TRY(cudaStreamBeginCapture(h->hstream, cudaStreamCaptureModeThreadLocal));
   const int64_t saved = h->hs_host;
   h->hs_host = 0;
+  h->prof_capturing = true;
   int rc = queue_half_steps(h, len, true, h->hstream);
+  h->prof_capturing = false;
   h->hs_host = saved;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->hstream, &g);
@@ -679,7 +727,9 @@ int run_check(tree_ot_handle* h, cudaStream_t s, const std::vector<int32_t>* onl
   c.edge_tc = h->d_edge_tc;
   c.edge_mass = h->d_edge_mass;
   c.mask = partial ? h->d_chk_mask : nullptr;
+  const int p0 = prof_mark(h, s);
   CUDA_TRY(h->fp64 ? launch_check64(c, s) : launch_check(c, s));
+  prof_span(h, TREE_OT_PROF_CHECK, p0, prof_mark(h, s));
   h->h_marg.resize(h->vec_len);
   h->h_f.resize(h->vec_len);
   h->h_Z.resize(h->nodes.size());
@@ -1649,6 +1699,7 @@ int tree_ot_destroy(tree_ot_handle* h) {
   if (h->d_setbuf) cudaFree(h->d_setbuf);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->hstream) cudaStreamDestroy(h->hstream);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   for (void* p : h->owned) cudaFree(p);
   delete h;
   return TREE_OT_OK;
@@ -1973,7 +2024,9 @@ int tree_ot_round(tree_ot_handle* h, void* cuda_stream, int32_t side, tree_ot_ro
   CUDA_TRY(cudaMemsetAsync(h->d_rs2, 0, sizeof(double) * h->vec_len, s));
   CUDA_TRY(cudaMemsetAsync(h->d_racc, 0, sizeof(double) * kRoundAcc * h->edges.size(), s));
   const RoundArgs a = round_args(h);
+  const int p0 = prof_mark(h, s);
   CUDA_TRY(launch_round(a, h->fp64, s));
+  prof_span(h, TREE_OT_PROF_ROUND, p0, prof_mark(h, s));
   std::vector<double> acc((size_t)kRoundAcc * h->edges.size()), q(h->vec_len);
   CUDA_TRY(cudaMemcpyAsync(acc.data(), h->d_racc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(q.data(), h->d_rsum, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, s));
@@ -2158,6 +2211,36 @@ int tree_ot_set_potentials_batch(tree_ot_handle* h, void* cuda_stream, int32_t c
                           h->d_hl, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   h->have_check = false;
+  return TREE_OT_OK;
+}
+
+int tree_ot_profile(tree_ot_handle* h, int32_t enable) {
+  g_err.clear();
+  if (!h) return fail(TREE_OT_ERR_ARG, "handle is NULL");
+  h->prof_on = enable != 0;
+  h->prof_used = 0;
+  h->prof_spans.clear();
+  return TREE_OT_OK;
+}
+
+int tree_ot_profile_read(tree_ot_handle* h, double* ms, int64_t* launches, int32_t ncat) {
+  g_err.clear();
+  if (!h || ncat < 0 || (ncat > 0 && !ms && !launches)) return fail(TREE_OT_ERR_ARG, "bad handle or outputs");
+  std::vector<double> t(TREE_OT_PROF_CATEGORIES, 0.0);
+  std::vector<int64_t> n(TREE_OT_PROF_CATEGORIES, 0);
+  if (h->prof_used > 0) CUDA_TRY(cudaEventSynchronize(h->prof_ev[h->prof_used - 1]));
+  for (const auto& sp : h->prof_spans) {
+    float v = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&v, h->prof_ev[sp.i0], h->prof_ev[sp.i1]));
+    t[sp.cat] += v;
+    n[sp.cat] += 1;
+  }
+  for (int32_t c = 0; c < ncat && c < TREE_OT_PROF_CATEGORIES; ++c) {
+    if (ms) ms[c] = t[c];
+    if (launches) launches[c] = n[c];
+  }
+  h->prof_used = 0;
+  h->prof_spans.clear();
   return TREE_OT_OK;
 }
 

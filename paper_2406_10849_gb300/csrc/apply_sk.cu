@@ -700,18 +700,21 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
          make(&m->vlo, a.vlo, a.ncols);
 }
 
-cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s) {
+cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaEvent_t before_product,
+                      cudaEvent_t after_product) {
   if (a.ncols <= 0) return cudaSuccess;
   if (a.use_tc && !maps) return cudaErrorInvalidValue;
   if (!(a.use_tc ? sk_tc_ready() : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
   sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
   sk_kbuild_kernel<<<a.mp, 256, 0, s>>>(a);
   sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
+  if (before_product) cudaEventRecord(before_product, s);
   const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
   if (a.use_tc)
     sk_gemm_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo);
   else
     sk_gemm_kernel<<<grid, kSkThreads, kSkSmem, s>>>(a);
+  if (after_product) cudaEventRecord(after_product, s);
   sk_fixup_kernel<<<152 * 8, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -81,7 +81,9 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m);
 bool sk_tc_available();
 
 // the five launches of one group and colour (nothing to do when ncols == 0)
-cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s);
+// before_product / after_product (may be null): events recorded around the product launch
+cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaEvent_t before_product = nullptr,
+                      cudaEvent_t after_product = nullptr);
 // b := -inf (once at create; afterwards each product resets it)
 cudaError_t launch_sk_reset(float* b, int32_t kd, cudaStream_t s);
 

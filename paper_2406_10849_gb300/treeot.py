@@ -28,6 +28,10 @@ TOL_KIND = {"sum": 0, "max": 1}
 APPLY = {"auto": 0, "lse": 1, "bf16": 2}
 
 
+PROFILE_CATEGORIES = ["apply_stored", "apply_recompute", "apply_bf16", "sk_build", "sk_product", "sk_fixup",
+                      "node_update", "absorb", "check", "round", "apply_fp64"]
+
+
 class TreeOTError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"tree_ot error {code} ({ERR.get(code, '?')}): {msg}")
@@ -119,6 +123,8 @@ SIGNATURES = {
     "tree_ot_node_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "tree_ot_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Result)]),
     "tree_ot_marginals": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "tree_ot_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "tree_ot_round": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(RoundResult)]),
     "tree_ot_round_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64]),
     "tree_ot_residual_history": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
@@ -380,6 +386,18 @@ class Solver:
         out = np.zeros(n, np.float64)
         _check(_lib.tree_ot_marginals(self.h, prob, node, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
+
+    def profile(self, enable: bool = True):
+        """tree_ot_profile: time every launch group queued outside graph capture."""
+        _check(_lib.tree_ot_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{category: (milliseconds, launch groups)} since the last read (tree_ot_profile_read)."""
+        n = len(PROFILE_CATEGORIES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        _check(_lib.tree_ot_profile_read(self.h, ms, cnt, n))
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROFILE_CATEGORIES) if cnt[i]}
 
     def round(self, side: int = -1):
         """tree_ot_round: round every problem's plans (the mismatched colour class by default);
