@@ -19,6 +19,7 @@
 
 #include "../../include/tree_ot.h"
 #include "internal.h"
+#include "round.h"
 #include "sk.h"
 
 using namespace treeot;

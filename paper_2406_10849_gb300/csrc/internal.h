@@ -271,44 +271,6 @@ struct CheckArgs {
   const int32_t* mask; // per problem: 0 = skip its tasks (null: check every problem)
 };
 
-// Rounding (round.cu).  A task is 64 rows of one plan with its rows on the
-// colour class S being rounded (the directed edge's owner is in S).
-constexpr int kRoundAcc = 6;  // per edge: <C,F>, <C,F''>, err_r^T C err_c, E = ||err_r||_1, C_inf (bits), ||F||_1
-struct RoundTask {
-  int32_t dedge;        // directed edge j -> k, j in S
-  int32_t o0, ocount;   // rows (points of j)
-  int32_t pad;
-};
-struct RoundArgs {
-  const RoundTask* tasks;
-  int32_t ntasks;
-  const DEdgeD* dedges;
-  int32_t ndedges;
-  const EdgeD* edges;
-  const NodeD* nodes;
-  const ProbD* probs;
-  const int32_t* node_dedges;
-  const int32_t* side;    // per problem: the colour class S being rounded
-  const double* nmass;    // per node: sum of mu (fixed nodes)
-  const float* ah;        // FP32 handles: check operand f/eps - Z + log gamma as (hi, lo)
-  const float* al;
-  const double* f;        // FP64 handles: potentials f', Z and log gamma read directly
-  const double* Z;
-  const double* logg;
-  const double* mu;       // node-level mu (fixed nodes)
-  const float* coords;
-  // arenas (layout of the potentials): "S" = offsets of directed edges owned by S (rows),
-  // "K" = offsets of the other directed edges (columns)
-  double* rsum;           // S: F 1;  K: F^T 1
-  double* tgt;            // S: row target;  K: column target (the owner's marginal, unit mass)
-  double* xy;             // S: row scale x;  K: column scale y
-  double* s2;             // S: F'' 1;  K: F'^T 1
-  double* er;             // S: err_r
-  double* edge_acc;       // per edge: kRoundAcc doubles
-  double* plan_out;       // pass 5: the rounded plan of the tasks' edge, rows = node a, row stride plan_ld
-  int64_t plan_ld;
-};
-
 // ---- launchers (defined in the .cu files) --------------------------------
 // slot 0: stored-cost tasks (ROW/COL); slot D (1..3): recomputed squared-Euclidean tasks
 // variant (recomputed costs): 0 = 2 CTAs per SM register budget, 1 = 3 CTAs per SM
@@ -353,10 +315,6 @@ cudaError_t noalloc_scratch(float** out, int64_t* capacity_floats);
 int64_t noalloc_scratch_floats_needed(int32_t n_rows, int32_t n_cols);
 cudaError_t launch_edge_apply_noalloc(const float* C, int64_t ld, int32_t n_rows, int32_t n_cols, const double* g,
                                       float shi, float slo, double* m_out, float* scratch, cudaStream_t s);
-// the rounding's passes over the plans and the per-point steps between them
-cudaError_t launch_round(const RoundArgs& a, bool f64, cudaStream_t s);
-// write out the rounded plans of a.tasks (one edge)
-cudaError_t launch_round_plan(const RoundArgs& a, bool f64, cudaStream_t s);
 constexpr int kApplySlots = 4;
 
 }  // namespace treeot

@@ -33,6 +33,7 @@
 #include "internal.h"
 #include "plan_entry.cuh"
 #include "ptx.cuh"
+#include "round.h"
 
 namespace treeot {
 namespace {
