@@ -470,6 +470,65 @@ def bench_stars(dev, stream, stars: int, side: int, steps: int, warmup: int, con
     return out
 
 
+FIG4_D = (10, 20, 40, 80, 160, 320, 640, 1280)      # d at |E| = 3
+FIG4_E = (2, 3, 4, 6, 8, 12, 16, 24, 32)             # |E| at d = 10
+
+
+def bench_fig4(dev, stream, seeds: int = 5, delta: float = 0.2):
+    """The paper's experiment (Sec. 5, Fig. 4(a)) with this solver: half-steps of
+    the Bipartite Iterative Scaling algorithm until the stopping sum falls below
+    delta' = delta / (8 C_inf), with eps = delta / (4 |E| log d), on the
+    log-normal barycenter -- against d at |E| = 3 and against |E| at d = 10, each
+    point the mean over ``seeds`` seeds.  All instances run as one batch (each
+    problem retires on its own); the rounding then certifies every instance
+    delta-approximate by lemma lem:round_applied (bound <= delta)."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+
+    cases = [(3, d) for d in FIG4_D] + [(E, 10) for E in FIG4_E if E != 3]
+    probs, keys = [], []
+    for (E, d) in cases:
+        for sd in range(seeds):
+            probs.append(gen.lognormal_barycenter(6_000_000 + 1000 * E + 10 * d + sd, E, d, delta))
+            keys.append((E, d))
+    tol = probs[0].meta["tol"]
+    s = T.Solver(probs, T.options(precision="fp32", tol=tol, tol_kind="sum", max_half_steps=200000), stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc, res = s.solve()
+    dt = time.perf_counter() - t0
+    rr = s.round()
+    s.close()
+    by = {}
+    for k, r, q, pb in zip(keys, res, rr, probs):
+        b = by.setdefault(k, {"half_steps": [], "bound": [], "theorem": 2 + 88 * k[0] * 1.0 / (tol * pb.eps)})
+        b["half_steps"].append(r["half_steps"])
+        b["bound"].append(q["bound"])
+    def row(k):
+        b = by[k]
+        return {"E": k[0], "d": k[1], "eps": delta / (4 * k[0] * np.log(k[1])),
+                "half_steps_mean": float(np.mean(b["half_steps"])), "half_steps": b["half_steps"],
+                "thm_num_iter_bound": b["theorem"], "worst_round_bound": max(b["bound"])}
+    vs_d = [row((3, d)) for d in FIG4_D]
+    vs_E = [row((E, 10)) for E in FIG4_E]
+    # trends: iterations against log d (least-squares line) and against |E| (log-log slope)
+    ld = np.log(np.array(FIG4_D, dtype=np.float64))
+    yd = np.array([r["half_steps_mean"] for r in vs_d])
+    slope_d, icpt_d = np.polyfit(ld, yd, 1)
+    r2_d = 1.0 - float(np.sum((yd - (slope_d * ld + icpt_d)) ** 2) / np.sum((yd - yd.mean()) ** 2))
+    lE = np.log(np.array(FIG4_E, dtype=np.float64))
+    yE = np.log(np.array([r["half_steps_mean"] for r in vs_E]))
+    exp_E, _ = np.polyfit(lE, yE, 1)
+    return {"workload": f"fig4_lognormal_barycenter_delta{delta}", "delta": delta, "tol": tol, "seeds": seeds,
+            "instances": len(probs), "seconds": dt, "certified": int(sum(r["status"] == 0 for r in res)),
+            "all_delta_approximate": bool(max(q["bound"] for q in rr) <= delta),
+            "vs_d_at_E3": vs_d, "vs_E_at_d10": vs_E,
+            "trend": {"half_steps_per_log_d": float(slope_d), "r2_vs_log_d": r2_d,
+                      "loglog_exponent_vs_E": float(exp_E)}}
+
+
 def bench_chain(dev, stream, steps: int):
     """The 5-node chain (n = 64 grid, eps = 0.01, FP64 handle): microseconds per
     half-step (CUDA events) and the solve to a stopping sum below 1e-9."""
@@ -664,6 +723,22 @@ def run_stars(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fig4(args):
+    """--workload fig4: the iteration-count experiment as the JSON line's own workload."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    b = bench_fig4(dev, stream)
+    line = {"metric": "half-steps to the stopping threshold delta' (mean over seeds)", "value": b["seconds"],
+            "unit": "s for all instances", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * b["seconds"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "instances": b["instances"]}}
+    line.update({k: v for k, v in b.items() if k not in ("workload",)})
+    print(json.dumps(line), flush=True)
+
+
 def run_unit_rates():
     """Build and run the unit-rate microbenchmark (csrc/unit_rates.cu): FP32 FMA
     lanes, packed f32x2 lanes and MUFU ex2 per clock and SM, ex2.approx error."""
@@ -687,11 +762,12 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload only: skip the batched, stars, star and chain measurements")
     ap.add_argument("--nodes", type=int, default=NODES, help="tree size (64 = the benchmark workload)")
-    ap.add_argument("--workload", default="prufer", choices=["prufer", "batched", "warmstart", "stars"],
+    ap.add_argument("--workload", default="prufer", choices=["prufer", "batched", "warmstart", "stars", "fig4"],
                     help="prufer: the 64-node stored-cost tree (default); batched: independent random trees "
                          "with costs recomputed from 2-D points (measured against the MUFU ex2 roofline); "
                          "warmstart: learned warm start on barycenter stars, warm vs u = 1; "
-                         "stars: the shared-kernel BF16 phase on a batch of stars")
+                         "stars: the shared-kernel BF16 phase on a batch of stars; "
+                         "fig4: the paper's iteration-count experiment on log-normal barycenters")
     ap.add_argument("--stars", type=int, default=2000, help="stars workload: number of stars")
     ap.add_argument("--train-trees", type=int, default=20000, help="warmstart: training stars")
     ap.add_argument("--test-trees", type=int, default=2000, help="warmstart: held-out stars")
@@ -717,6 +793,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "stars":
         return run_stars(args)
+    if args.workload == "fig4":
+        return run_fig4(args)
 
     import torch
 
@@ -880,6 +958,7 @@ def main():
                                      args.refine_tol)
         extra["star"] = bench_star(dev, stream, max(ks, 50))
         extra["chain_fp64"] = bench_chain(dev, stream, max(ks, 200))
+        extra["fig4"] = bench_fig4(dev, stream)
     cpu = None if (args.no_cpu or world > 1) else cpu_baseline(p)  # the host baseline: N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,

@@ -20,6 +20,9 @@ shapes this project is measured on:
 * ``batched_problems`` -- 512 random trees with 4..32 nodes, n_j uniform in
   {128..2048}, 2-D uniform points, eps log-uniform in [0.002, 0.05].
 * ``star_problem`` with other seeds/eps -- the warm-start training/test sets.
+* ``lognormal_barycenter`` -- the paper's own experiment (Sec. 5, Fig. 4(a)):
+  |E| fixed leaves and a free centre on a uniform grid of d points in [0,1],
+  squared-Euclidean cost, log-normal marginals, eps = delta / (4 |E| log d).
 
 Every generator takes a ``seed``; by convention ``seed = 1000*workload + instance``.
 All randomness comes from ``numpy.random.default_rng(seed)`` (PCG64).
@@ -346,3 +349,38 @@ WORKLOADS = {
     "batched512_trees": "batched_problems",
     "star8_warmstart": "star_problem",
 }
+
+
+def lognormal_barycenter(seed: int, num_leaves: int, d: int, delta: float = 0.2,
+                         cost_kind: str = COST_SQEUCLID) -> TreeProblem:
+    """The barycenter of the paper's numerical section (Sec. 5): a star whose
+    ``num_leaves`` = |E| leaves carry fixed marginals and whose centre is free, all
+    on the uniform grid of d points between 0 and 1 (endpoints included), cost
+    |x - y|^2 (so C_inf = 1), and the parameter choice of Sec. 3.2 for a target
+    accuracy delta: eps = delta / (4 |E| log d); the stopping threshold is
+    delta' = delta / (8 C_inf), in ``meta["tol"]``.
+
+    Marginals: the density of a log-normal distribution evaluated on the grid
+    and normalised to sum to one, with log-mean m ~ U[-1.5, 0] and shape
+    s ~ U[0.3, 1] per leaf (mode e^(m - s^2) inside (0, 1]); the density is 0 at
+    x = 0.  The paper says only that the marginals are generated from the
+    log-normal distribution and normalised."""
+    rng = np.random.default_rng(seed)
+    edges = star_edges(num_leaves)
+    x = grid_1d(d)
+    xs = x[:, 0].astype(np.float64)
+    J = num_leaves + 1
+    fixed = np.ones(J, dtype=bool)
+    fixed[0] = False
+    marg = {}
+    for l in range(1, J):
+        m = rng.uniform(-1.5, 0.0)
+        sh = rng.uniform(0.3, 1.0)
+        w = np.zeros(d)
+        pos = xs > 0
+        w[pos] = np.exp(-(np.log(xs[pos]) - m) ** 2 / (2.0 * sh * sh)) / (xs[pos] * sh * np.sqrt(2.0 * np.pi))
+        marg[l] = w / w.sum()
+    eps = delta / (4.0 * num_leaves * np.log(d))
+    return TreeProblem(name=f"lognormal_bary_E{num_leaves}_d{d}", edges=edges, n=np.full(J, d, np.int32),
+                       fixed=fixed, marginals=marg, eps=float(eps), coords=[x] * J, cost_scale=1.0,
+                       cost_kind=cost_kind, meta={"seed": seed, "delta": delta, "tol": delta / 8.0})
