@@ -259,6 +259,18 @@ def sfu_peak(sms: int, mhz: float) -> float:
 RECOMP_ALG_OPS_PER_ELEM = 8.0
 
 
+def batched_share(num_trees: int, rank: int, world: int):
+    """This rank's trees of the batched workload (all of them at world = 1): disjoint
+    subsets balanced by plan elements per half-step, no data-path exchange."""
+    import gen
+    from paper_2406_10849_gb300 import shard
+
+    allp = gen.batched_problems(seed=4000, num_trees=num_trees)
+    if world == 1:
+        return allp, list(range(len(allp)))
+    return shard.shard_problems(allp, rank, world)
+
+
 def bench_batched(dev, stream, steps: int, warmup: int, converge: bool, num_trees: int = 512, rank: int = 0,
                   world: int = 1, dist=None):
     """Independent random trees (4..32 nodes, n_j in 128..2048, 2-D points, eps
@@ -272,8 +284,7 @@ def bench_batched(dev, stream, steps: int, warmup: int, converge: bool, num_tree
     import paper_2406_10849_gb300 as T
     from paper_2406_10849_gb300 import shard
 
-    allp = gen.batched_problems(seed=4000, num_trees=num_trees)
-    probs, mine = shard.shard_problems(allp, rank, world) if world > 1 else (allp, list(range(len(allp))))
+    probs, mine = batched_share(num_trees, rank, world)
     t0 = time.perf_counter()
     solver = T.Solver(probs, T.options(precision="fp32"), stream=stream)
     create_s = time.perf_counter() - t0

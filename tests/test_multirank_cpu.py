@@ -48,6 +48,42 @@ def test_sharding_world2_gloo():
     assert max(load0, load1) / min(load0, load1) < 1.3
 
 
+def _bench_share_worker(rank, world, port, out):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    from paper_2406_10849_gb300 import shard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    probs, idx = bench.batched_share(512, rank, world)
+    edges = sum(p.num_edges for p in probs)
+    elems = sum(p.elements_per_half_step() for p in probs)
+    out[rank] = (idx, edges, elems, shard.sum_over_ranks(edges, dist), shard.max_over_ranks(elems, dist))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_batched_split_world2_gloo():
+    """The batched benchmark's split at world size 2, as each rank builds it: the two
+    ranks' trees are disjoint and cover the 512, the summed edge count (the numerator
+    of the whole-job applies/s) equals the batch's, and the heavier rank carries
+    within 1 % of half the plan elements (the time of a step is the max over ranks)."""
+    import gen
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.start_processes(_bench_share_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    allp = gen.batched_problems(seed=4000, num_trees=512)
+    (i0, e0, m0, tot0, mx0), (i1, e1, m1, tot1, mx1) = out[0], out[1]
+    assert sorted(i0 + i1) == list(range(512)) and not set(i0) & set(i1)
+    assert tot0 == tot1 == e0 + e1 == sum(p.num_edges for p in allp)
+    total = sum(p.elements_per_half_step() for p in allp)
+    assert m0 + m1 == total and mx0 == mx1 == max(m0, m1)
+    assert max(m0, m1) <= 0.505 * total
+
+
 def test_shard_range_covers_all():
     from paper_2406_10849_gb300 import shard
     for n in (0, 1, 7, 512):
