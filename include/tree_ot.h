@@ -202,9 +202,15 @@ int tree_ot_validate(const tree_ot_problem *prob);
  * gets colour 0 (updated first).  edges: [num_nodes-1][2].  No CUDA call. */
 int tree_ot_bipartition(int32_t num_nodes, const int32_t *edges, uint8_t *colour_out);
 
-/* Validate all problems, build the device plan and upload the data.  Several
+/* Validate all problems, build the device plan and upload the data.  Each
+ * problem is the coupled bi-marginal problem of Sec. 3 (eq.
+ * ot_graph_pairwise_mass: tree, costs C_(j,k), fixed marginals mu_j on leaves,
+ * eps) with the inputs of the Bipartite Iterative Scaling algorithm; the
+ * stopping threshold delta' and the other controls come in *opt.  Several
  * problems form one batch ("forest"); each converges and retires on its own.
- * Potentials start at zero (u = 1).  opt may be NULL (defaults). */
+ * Potentials start at zero (u = 1, the algorithm's initialisation); warm starts
+ * and checkpoint resumes enter afterwards through tree_ot_set_potentials*.
+ * opt may be NULL (defaults).  On failure *out is NULL and nothing is leaked. */
 int tree_ot_create(const tree_ot_problem *probs, int32_t num_probs, const tree_ot_options *opt,
                    void *cuda_stream, tree_ot_handle **out);
 
@@ -248,8 +254,10 @@ int tree_ot_node_update(tree_ot_handle *h, void *cuda_stream, int32_t colour);
 int tree_ot_check(tree_ot_handle *h, void *cuda_stream, tree_ot_result *results);
 
 /* Marginal of node j of problem p from the last tree_ot_check / tree_ot_solve
- * (FP64): B_(j,k_j) 1 for fixed j, the mean of {B_(j,k) 1}_k for free j.
- * out: host, n_j doubles. */
+ * (FP64): B_(j,k_j) 1 for fixed j, the mean of {B_(j,k) 1}_k for free j (the
+ * arithmetic mean qbar_j of lemma lem:f_upper_bound_tree; for a star this is
+ * the barycenter).  out: host, n_j doubles.  The potentials of the same
+ * iterate come from tree_ot_get_potentials. */
 int tree_ot_marginals(tree_ot_handle *h, int32_t prob, int32_t node, double *out);
 
 /* History of the stopping quantity (the while-condition of the Bipartite
