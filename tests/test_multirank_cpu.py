@@ -36,7 +36,7 @@ def _worker(rank, world, port, out):
 def test_sharding_world2_gloo():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
     idx0, load0, tmax0, tot0 = out[0]
@@ -71,7 +71,7 @@ def test_bench_batched_split_world2_gloo():
     import gen
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_bench_share_worker, args=(world, port, out), nprocs=world, join=True,
                        start_method="spawn")
