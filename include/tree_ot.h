@@ -125,6 +125,23 @@ typedef struct tree_ot_problem {
  * kernel returns normally and tree_ot_solve reports TREE_OT_ERR_TIMEOUT.
  * Implies TREE_OT_OPT_DENSE_TMA.  No GPU fault is involved. */
 #define TREE_OT_OPT_TEST_STALL   16u
+/* Batches whose costs are all recomputed from points of one dimension (FP32,
+ * no BF16 phase): run chunks of half-steps as ONE persistent launch each
+ * (inside tree_ot_solve's captured CUDA graph, one graph node per chunk), the
+ * CTAs taking apply tasks and node-update chunks in schedule order from an
+ * atomic ticket and each waiting only for its own problem's previous phase
+ * (per-problem phase counters): trees advance on their own, a tree's node
+ * update overlaps other trees' applies, and retired trees cost nothing.  At
+ * create the per-half-step launches and the persistent kernel at 2 and 3 CTAs
+ * per SM are timed over 8 half-steps and the fastest is kept (plan_stats[13]:
+ * 0 = per-half-step launches, else the persistent kernel's CTAs per SM); with
+ * autotune = 0 the persistent kernel runs at 2 CTAs per SM.
+ * Every wait is bounded (1 s); one that runs out ends the launch and the
+ * solve reports TREE_OT_ERR_TIMEOUT.  With TREE_OT_OPT_TEST_STALL as well, the
+ * node-update items never report completion, so the next waits run out (tests
+ * the failure path without a GPU fault).  tree_ot_apply / tree_ot_node_update
+ * always launch their own kernels. */
+#define TREE_OT_OPT_PERSISTENT  64u
 #define TREE_OT_OPT_SK_MMA_SYNC 32u /* shared-kernel BF16 phase: multiply with the legacy
                                        mma.sync kernel instead of tcgen05 (tensor memory
                                        accumulators); for comparison and for devices
@@ -363,7 +380,9 @@ int tree_ot_get_potentials_batch(tree_ot_handle *h, void *cuda_stream, int32_t c
  * [9] output block of recomputed-cost tasks, [10] their CTAs per SM (0 = by
  * occupancy), [11] their kernel register budget (0: 2 CTAs per SM, 1: 3), all
  * as chosen by the autotuner, [12] 1 when stored costs stream through the
- * bulk-copy staged kernel (TREE_OT_OPT_DENSE_TMA or the autotuner's choice). */
+ * bulk-copy staged kernel (TREE_OT_OPT_DENSE_TMA or the autotuner's choice),
+ * [13] 0 when half-steps run as per-half-step launches, else the persistent
+ * forest kernel's CTAs per SM (TREE_OT_OPT_PERSISTENT). */
 int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
 /* Launch timing (no paper counterpart: measurement support).  While enabled,
@@ -384,7 +403,8 @@ int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 #define TREE_OT_PROF_CHECK           8  /* FP64-grade check                                       */
 #define TREE_OT_PROF_ROUND           9  /* rounding passes                                        */
 #define TREE_OT_PROF_APPLY_FP64     10  /* FP64 edge apply                                        */
-#define TREE_OT_PROF_CATEGORIES     11
+#define TREE_OT_PROF_FOREST         11  /* persistent forest launch (applies + node updates)      */
+#define TREE_OT_PROF_CATEGORIES     12
 int tree_ot_profile(tree_ot_handle *h, int32_t enable);
 /* ms, launches: host arrays of ncat entries (either may be NULL); synchronises
  * with the recorded work. */

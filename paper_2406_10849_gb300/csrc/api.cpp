@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tree_ot.h"
+#include "forest.h"
 #include "internal.h"
 #include "round.h"
 #include "sk.h"
@@ -273,6 +274,14 @@ struct tree_ot_handle {
     int32_t cat, i0, i1;
   };
   std::vector<Span> prof_spans;
+  // persistent forest launch (TREE_OT_OPT_PERSISTENT): 0 = off, else the register
+  // budget in CTAs per SM (2 or 3) the create-time timing chose
+  int persistent = 0;
+  int forest_D = 0;
+  uint32_t forest_smem = 0;
+  int forest_grid[2] = {0, 0};             // grids at 2 and 3 CTAs per SM
+  int forest_grid_exact = 0;
+  int32_t *d_fcnt = nullptr, *d_fdone = nullptr, *d_fctl = nullptr;
   int64_t pot_version = 0;                  // bumped by every call that changes potentials
   int64_t round_version = -1;               // pot_version the last rounding saw
 
@@ -584,7 +593,45 @@ int sync_potentials(tree_ot_handle* h, cudaStream_t s) {
   return TREE_OT_OK;
 }
 
+// one persistent launch of G half-steps (the forest kernel; see forest.cu)
+int launch_forest_chunk(tree_ot_handle* h, int G, bool retire, cudaStream_t s) {
+  ForestArgs f{};
+  for (int c = 0; c < 2; ++c) {
+    f.ap[c] = apply_args(h, c);
+    f.ap[c].tasks = h->d_tasks[c] + h->slot_begin[c][h->forest_D];
+    f.ap[c].ntasks = h->slot_count[c][h->forest_D];
+    f.nd[c] = node_args(h, c, retire);
+  }
+  f.cnt = h->d_fcnt;
+  f.app_done = h->d_fdone;
+  f.nod_done = h->d_fdone + h->nprob;
+  f.ctl = h->d_fctl;
+  f.err = h->d_err;
+  f.hs = h->d_hs;
+  f.nprob = h->nprob;
+  f.G = G;
+  f.c0 = (int32_t)(h->hs_host % 2);
+  f.test_stall = (h->opt.flags & TREE_OT_OPT_TEST_STALL) ? 1 : 0;
+  const bool exact = h->any_exact != 0;
+  const int grid = exact ? h->forest_grid_exact : h->forest_grid[h->persistent == 3 ? 1 : 0];
+  const int p0 = prof_mark(h, s);
+  cudaError_t e = launch_forest(f, h->forest_D, exact, exact ? 2 : h->persistent, h->forest_smem, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent forest launch");
+  prof_span(h, TREE_OT_PROF_FOREST, p0, prof_mark(h, s));
+  h->f_stale = true;  // the node updates advanced the operand past the stored potentials
+  return TREE_OT_OK;
+}
+
 int queue_half_steps(tree_ot_handle* h, int64_t T, bool retire, cudaStream_t s) {
+  if (h->persistent) {
+    while (T > 0) {
+      const int G = (int)std::min<int64_t>(T, 64);
+      RC_TRY(launch_forest_chunk(h, G, retire, s));
+      h->hs_host += G;
+      T -= G;
+    }
+    return TREE_OT_OK;
+  }
   for (int64_t i = 0; i < T; ++i) {
     const int colour = (int)(h->hs_host % 2);
     RC_TRY(launch_apply(h, colour, s));
@@ -632,6 +679,10 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(h->d_hs, 0, sizeof(int64_t), s));
   CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), s));
   CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t) * 2 * 2 * kApplySlots, s));
+  if (h->d_fdone) {  // the persistent launch's counters (its last CTA leaves them at zero)
+    CUDA_TRY(cudaMemsetAsync(h->d_fdone, 0, sizeof(int32_t) * 2 * h->nprob, s));
+    CUDA_TRY(cudaMemsetAsync(h->d_fctl, 0, sizeof(int32_t) * 2, s));
+  }
   // apply operand of u = 1: h = log gamma * log2(e)
   CUDA_TRY(launch_operand(h->d_f, nullptr, h->d_logg, h->d_dedges, h->d_nodes, h->d_probs, (int32_t)h->dedges.size(),
                           kLog2e, true, h->d_hh, h->d_hl, s));
@@ -1185,6 +1236,84 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 
 namespace {
+// The persistent forest launch: eligible when every problem's costs are
+// recomputed from points of one dimension in FP32 with no BF16 phase.  Builds
+// the per-problem item counts, then times G = 8 half-steps of the per-half-step
+// launches and of the persistent kernel at 2 and 3 CTAs per SM (after 2
+// warm-up half-steps each) and keeps the fastest; the state goes back to u = 1.
+int setup_forest(tree_ot_handle* h, cudaStream_t s) {
+  h->persistent = 0;
+  if (h->fp64 || h->lowp || !(h->opt.flags & TREE_OT_OPT_PERSISTENT)) return TREE_OT_OK;
+  int D = 0;
+  for (int c = 0; c < 2; ++c) {
+    if (h->slot_count[c][0] > 0) return TREE_OT_OK;
+    for (int slot = 1; slot < kApplySlots; ++slot) {
+      if (h->slot_count[c][slot] == 0) continue;
+      if (D && D != slot) return TREE_OT_OK;
+      D = slot;
+    }
+  }
+  if (D == 0) return TREE_OT_OK;
+  std::vector<int32_t> cnt(4 * (size_t)h->nprob, 0);
+  for (int c = 0; c < 2; ++c) {
+    for (int32_t i = 0; i < h->slot_count[c][D]; ++i)
+      ++cnt[4 * h->dedges[h->tasks[c][h->slot_begin[c][D] + i].dedge].prob + c];
+    for (const NodeChunk& ch : h->chunks[c]) ++cnt[4 * h->nodes[ch.node].prob + 2 + c];
+  }
+  if (!h->d_fcnt) {
+    int rc = 0;
+    if ((rc = h->alloc(&h->d_fcnt, 4 * (int64_t)h->nprob)) || (rc = h->alloc(&h->d_fdone, 2 * (int64_t)h->nprob)) ||
+        (rc = h->alloc(&h->d_fctl, 2)))
+      return rc;
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_fcnt, cnt.data(), sizeof(int32_t) * cnt.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_fdone, 0, sizeof(int32_t) * 2 * h->nprob, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_fctl, 0, sizeof(int32_t) * 2, s));
+  h->forest_D = D;
+  h->forest_smem = std::max(h->node_smem[0], h->node_smem[1]);
+  h->forest_grid[0] = h->sms * forest_ctas_per_sm(D, false, 2, h->forest_smem);
+  h->forest_grid[1] = h->sms * forest_ctas_per_sm(D, false, 3, h->forest_smem);
+  h->forest_grid_exact = h->sms * forest_ctas_per_sm(D, true, 2, h->forest_smem);
+  if (h->forest_grid[0] < 1 || h->forest_grid_exact < 1) return TREE_OT_OK;
+  if (!h->opt.autotune) {  // no timing: the persistent kernel at 2 CTAs per SM
+    h->persistent = 2;
+    return TREE_OT_OK;
+  }
+  // time the three forms from u = 1
+  constexpr int kWarm = 2, kTimed = 8;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = INFINITY;
+  int choice = 0;
+  for (int form : {0, 2, 3}) {
+    if (form == 3 && h->forest_grid[1] < 1) continue;
+    RC_TRY(reset_state(h, s));
+    h->persistent = form;
+    int rc = queue_half_steps(h, kWarm, false, s);
+    if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = TREE_OT_ERR_CUDA;
+    if (!rc) rc = queue_half_steps(h, kTimed, false, s);
+    if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = TREE_OT_ERR_CUDA;
+    float ms = INFINITY;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = TREE_OT_ERR_CUDA;
+    if (rc) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      h->persistent = 0;
+      return rc == TREE_OT_ERR_CUDA ? cuda_fail(cudaGetLastError(), "timing the persistent forest launch") : rc;
+    }
+    if (ms < best) {
+      best = ms;
+      choice = form;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->persistent = choice;
+  return reset_state(h, s);
+}
+
 // device tables of the last rounding (see tree_ot_round)
 RoundArgs round_args(const tree_ot_handle* h) {
   RoundArgs a{};
@@ -1687,6 +1816,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     }
   }
   if (h->lowp && (rc = reset_state(h, s))) return bail(rc);  // the BF16 phases back
+  if ((rc = setup_forest(h, s))) return bail(rc);
   {
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamSynchronize(create)"));
@@ -2248,7 +2378,7 @@ int tree_ot_profile_read(tree_ot_handle* h, double* ms, int64_t* launches, int32
 int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
   g_err.clear();
   if (!h || !stats || nstats < 0) return fail(TREE_OT_ERR_ARG, "bad handle or stats pointer");
-  const int64_t v[13] = {(int64_t)h->dedges.size(),
+  const int64_t v[14] = {(int64_t)h->dedges.size(),
                         (int64_t)h->edges.size(),
                         h->elems,
                         h->matrix_bytes,
@@ -2260,8 +2390,9 @@ int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
                         (int64_t)h->rec_ob,
                         (int64_t)h->grid_mult,
                         (int64_t)h->rec_variant,
-                        (int64_t)h->dense_tma};
-  for (int32_t i = 0; i < nstats && i < 13; ++i) stats[i] = v[i];
+                        (int64_t)h->dense_tma,
+                        (int64_t)h->persistent};
+  for (int32_t i = 0; i < nstats && i < 14; ++i) stats[i] = v[i];
   return TREE_OT_OK;
 }
 
