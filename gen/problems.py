@@ -384,3 +384,138 @@ def lognormal_barycenter(seed: int, num_leaves: int, d: int, delta: float = 0.2,
     return TreeProblem(name=f"lognormal_bary_E{num_leaves}_d{d}", edges=edges, n=np.full(J, d, np.int32),
                        fixed=fixed, marginals=marg, eps=float(eps), coords=[x] * J, cost_scale=1.0,
                        cost_kind=cost_kind, meta={"seed": seed, "delta": delta, "tol": delta / 8.0})
+
+
+# --------------------------------------------------------------------------
+# general graphs: modified junction trees (Sec. 4)
+# --------------------------------------------------------------------------
+
+@dataclass
+class JunctionTreeProblem:
+    """A coupled MOT problem on a modified junction tree (Sec. 4, eq. ot_graph_local_reg).
+
+    Attributes
+    ----------
+    d : int [V]; support size of every variable x_0 .. x_{V-1}.
+    clique_vars : per cost clique, the sorted tuple of its variables.
+    clique_costs : per cost clique, the FP64 cost tensor, axes in clique_vars order.
+    sep_vars : per separator, the sorted tuple of its variables.
+    sep_cliques : per separator, its neighbour cliques in the order of its
+        inclusion sequence (Assumption ass:inclusion: the intersections with the
+        separator are equal for the first two and nested after that).
+    sep_gamma : per separator, the constrained variable set (a sorted tuple) or None.
+    sep_mu : per separator, the FP64 marginal over sep_gamma (axes in that order) or None.
+    eps : local entropic regularisation.
+    coords : per variable float32 [d, 1] support points (the grid the costs were built on).
+    """
+
+    name: str
+    d: np.ndarray
+    clique_vars: List[tuple]
+    clique_costs: List[np.ndarray]
+    sep_vars: List[tuple]
+    sep_cliques: List[List[int]]
+    sep_gamma: List[Optional[tuple]]
+    sep_mu: List[Optional[np.ndarray]]
+    eps: float
+    coords: List[np.ndarray] = field(default_factory=list)
+    meta: Dict = field(default_factory=dict)
+
+
+def _lognormal_density_marginal(xs, rng):
+    m = rng.uniform(-1.5, 0.0)
+    sh = rng.uniform(0.3, 1.0)
+    w = np.zeros(xs.shape[0])
+    pos = xs > 0
+    w[pos] = np.exp(-(np.log(xs[pos]) - m) ** 2 / (2.0 * sh * sh)) / (xs[pos] * sh * np.sqrt(2.0 * np.pi))
+    return w / w.sum()
+
+
+def wls_junction_tree(seed: int, J: int, d: int, alpha: float = 10.0, delta: float = 0.2) -> JunctionTreeProblem:
+    """Wasserstein least squares (Sec. 2.3, eq. wls_cost) on its modified junction tree
+    (Sec. 4): variables x_0, x_1 .. x_J, x_{J+1} on the uniform grid of d points in
+    [0, 1]; cost cliques {x_0, x_j, x_{J+1}} with
+        C_j = |x_j - (1 - t_j) x_0 - t_j x_{J+1}|^2 + (alpha / J) |x_0 - x_{J+1}|^2,
+    t_j = j / (J + 1) (the alpha term of eq. wls_cost shared equally by the J cliques);
+    separators {x_0, x_{J+1}} (free, joined to every clique) and {x_j} (constrained to
+    the data marginal rho_{t_j}, a log-normal density on the grid).  eps and the
+    stopping threshold follow the parameter choice of Sec. 3.2 with |E| = J cliques:
+    eps = delta / (4 J log d), threshold delta / (8 C_inf) in meta["tol"]."""
+    rng = np.random.default_rng(seed)
+    x = grid_1d(d)
+    xs = x[:, 0].astype(np.float64)
+    V = J + 2
+    cv, cc = [], []
+    for j in range(1, J + 1):
+        t = j / (J + 1.0)
+        X0 = xs[:, None, None]
+        Xj = xs[None, :, None]
+        X1 = xs[None, None, :]
+        C = (Xj - (1.0 - t) * X0 - t * X1) ** 2 + (alpha / J) * (X0 - X1) ** 2   # axes (x_0, x_j, x_{J+1})
+        cv.append((0, j, J + 1))
+        cc.append(C)
+    sv = [(0, J + 1)] + [(j,) for j in range(1, J + 1)]
+    sc = [list(range(J))] + [[j - 1] for j in range(1, J + 1)]
+    sg = [None] + [(j,) for j in range(1, J + 1)]
+    smu = [None] + [_lognormal_density_marginal(xs, rng) for _ in range(J)]
+    cinf = max(float(np.max(np.abs(C))) for C in cc)
+    eps = delta / (4.0 * J * np.log(d))
+    return JunctionTreeProblem(name=f"wls_J{J}_d{d}", d=np.full(V, d, np.int32), clique_vars=cv, clique_costs=cc,
+                               sep_vars=sv, sep_cliques=sc, sep_gamma=sg, sep_mu=smu, eps=float(eps),
+                               coords=[x] * V, meta={"seed": seed, "alpha": alpha, "delta": delta,
+                                                     "tol": delta / (8.0 * cinf), "c_inf": cinf})
+
+
+def nested_junction_tree(seed: int, d: int = 2, eps: float = 0.5) -> JunctionTreeProblem:
+    """The nested example of Sec. 4 (Assumption ass:inclusion's figure) closed into a
+    modified junction tree: separator c = {x1, x3, x4} with cliques c1 = {x1, x2, x3, x4},
+    c2 = {x1, x3, x4}, c3 = {x0, x1, x3} (intersections {1,3,4} = {1,3,4} ⊇ {1,3}) and
+    the constraint gamma = {x3} embedded in c; each clique's second separator is a
+    constrained single variable: {x2} for c1, {x4} for c2, {x0} for c3.  Costs are
+    seeded uniform numbers in [0, 1); marginals Dirichlet(1)."""
+    rng = np.random.default_rng(seed)
+    V = 5
+    dd = np.full(V, d, np.int32)
+    cv = [(1, 2, 3, 4), (1, 3, 4), (0, 1, 3)]
+    cc = [rng.random(tuple(int(dd[v]) for v in c)) for c in cv]
+    sv = [(1, 3, 4), (2,), (4,), (0,)]
+    sc = [[0, 1, 2], [0], [1], [2]]
+    sg = [(3,), (2,), (4,), (0,)]
+    smu = [dirichlet_marginal(d, rng) for _ in range(4)]
+    x = grid_1d(d)
+    return JunctionTreeProblem(name=f"nested_d{d}", d=dd, clique_vars=cv, clique_costs=cc, sep_vars=sv,
+                               sep_cliques=sc, sep_gamma=sg, sep_mu=smu, eps=eps, coords=[x] * V,
+                               meta={"seed": seed})
+
+
+def tree_as_junction_tree(p: TreeProblem) -> JunctionTreeProblem:
+    """A tree problem of Sec. 3 written as a modified junction tree: variables = nodes,
+    cost cliques = edges {j, k}, separators = single nodes {j} (constrained to mu_j on
+    fixed nodes).  The cost tensors are the problem's FP32 costs in FP64."""
+    J = p.num_nodes
+    cv, cc = [], []
+    for e, (a, b) in enumerate(np.asarray(p.edges)):
+        a, b = int(a), int(b)
+        if p.cost_kind == COST_DENSE:
+            C = (p.dense_costs[e] if p.dense_costs is not None and p.dense_costs[e] is not None
+                 else p.dense_cost(e)).astype(np.float64)
+        else:
+            Xa = p.coords[a].astype(np.float64)
+            Xb = p.coords[b].astype(np.float64)
+            C = p.cost_scale * ((Xa[:, None, :] - Xb[None, :, :]) ** 2).sum(-1)
+        if a < b:
+            cv.append((a, b))
+            cc.append(C)
+        else:
+            cv.append((b, a))
+            cc.append(C.T.copy())
+    sv = [(j,) for j in range(J)]
+    sc = [[] for _ in range(J)]
+    for e, (a, b) in enumerate(np.asarray(p.edges)):
+        sc[int(a)].append(e)
+        sc[int(b)].append(e)
+    sg = [(j,) if p.fixed[j] else None for j in range(J)]
+    smu = [p.marginals[j] if p.fixed[j] else None for j in range(J)]
+    return JunctionTreeProblem(name=p.name + "_jt", d=np.asarray(p.n, np.int32), clique_vars=cv, clique_costs=cc,
+                               sep_vars=sv, sep_cliques=sc, sep_gamma=sg, sep_mu=smu, eps=p.eps,
+                               coords=list(p.coords), meta=dict(p.meta))

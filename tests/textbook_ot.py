@@ -151,3 +151,121 @@ def lp_optimum(J, edges, n, fixed, marginals, costs):
     res = linprog(c, A_eq=A, b_eq=rhs, bounds=(0, None), method="highs")
     assert res.status == 0, res.message
     return float(res.fun)
+
+
+# ---------------------------------------------------------------------------
+# coupled MOT on a modified junction tree (eq. ot_graph_local_reg), generic
+# ---------------------------------------------------------------------------
+
+def _projection(d, cvars, keep):
+    """Matrix mapping a clique tensor (axes cvars, row-major) to its marginal on keep."""
+    shape = tuple(int(d[v]) for v in cvars)
+    idx = np.indices(shape).reshape(len(cvars), -1)
+    kshape = tuple(int(d[v]) for v in keep)
+    rows = np.zeros(idx.shape[1], dtype=np.int64)
+    for v in keep:
+        rows = rows * int(d[v]) + idx[cvars.index(v)]
+    P = np.zeros((int(np.prod(kshape)) if keep else 1, idx.shape[1]))
+    P[rows if keep else np.zeros_like(rows), np.arange(idx.shape[1])] = 1.0
+    return P
+
+
+def _jt_constraints(jt):
+    offs = [0]
+    for C in jt.clique_costs:
+        offs.append(offs[-1] + C.size)
+    nvar = offs[-1]
+
+    def block(c, keep):
+        P = _projection(jt.d, tuple(jt.clique_vars[c]), tuple(keep))
+        out = np.zeros((P.shape[0], nvar))
+        out[:, offs[c]:offs[c + 1]] = P
+        return out
+
+    A, rhs = [], []
+    for s, cl in enumerate(jt.sep_cliques):
+        sv = jt.sep_vars[s]
+        sets = [tuple(v for v in sv if v in jt.clique_vars[c]) for c in cl]
+        for i in range(1, len(cl)):
+            A.append(block(cl[i], sets[i]) - block(cl[0], sets[i]))
+            rhs.append(np.zeros(A[-1].shape[0]))
+        if jt.sep_gamma[s] is None:
+            A.append(block(cl[0], ()))
+            rhs.append(np.ones(1))
+        else:
+            A.append(block(cl[0], tuple(jt.sep_gamma[s])))
+            rhs.append(np.asarray(jt.sep_mu[s], dtype=np.float64).reshape(-1))
+    return np.vstack(A), np.concatenate(rhs), offs
+
+
+def jt_primal_generic(jt, tol=1e-14, max_iter=500):
+    """Minimise sum_c <C_c,B_c> + eps H(B_c | M_c) under the constraints of eq.
+    ot_graph_local_reg (separator plans eliminated: each neighbour's marginal on the
+    intersection equals the first neighbour's; gamma marginal or unit mass), blind to
+    the junction-tree algorithm: Newton on the Lagrangian dual as in primal_generic.
+    M_c = m_{s_j} (x) m_{s_k} with m_s = mu_gamma (x) 1 (prop. local_reg_dual).
+    Returns (plans, primal value)."""
+    A, rhs, offs = _jt_constraints(jt)
+    lm = []
+    for c, cv in enumerate(jt.clique_vars):
+        shape = tuple(int(jt.d[v]) for v in cv)
+        a = np.zeros(shape)
+        for s, cl in enumerate(jt.sep_cliques):
+            if c in cl and jt.sep_gamma[s] is not None:
+                g = tuple(jt.sep_gamma[s])
+                with np.errstate(divide="ignore"):
+                    lmu = np.log(np.asarray(jt.sep_mu[s], dtype=np.float64))
+                sh = [int(jt.d[v]) if v in g else 1 for v in cv]
+                order = sorted(range(len(g)), key=lambda k: cv.index(g[k]))
+                a = a + np.transpose(lmu, order).reshape(sh)
+        lm.append(a.reshape(-1))
+    lm = np.concatenate(lm)
+    c = np.concatenate([np.asarray(C, dtype=np.float64).reshape(-1) for C in jt.clique_costs])
+    eps = jt.eps
+
+    def z_of(y):
+        with np.errstate(invalid="ignore"):
+            return np.nan_to_num(np.exp((A.T @ y - c) / eps + lm))
+
+    def dual(y):
+        return float(y @ rhs - eps * z_of(y).sum())
+
+    y = np.zeros(A.shape[0])
+    for _ in range(max_iter):
+        z = z_of(y)
+        g = rhs - A @ z
+        if np.abs(g).max() < tol:
+            break
+        H = (A * z[None, :]) @ A.T / eps
+        step = np.linalg.lstsq(H, g, rcond=None)[0]
+        t, d0 = 1.0, dual(y)
+        while dual(y + t * step) < d0 - 1e-15 * abs(d0) and t > 1e-12:
+            t *= 0.5
+        y = y + t * step
+    z = z_of(y)
+    pos = z > 0
+    val = float(c @ z + eps * np.sum(z[pos] * (np.log(z[pos]) - lm[pos] - 1.0)))
+    return [z[offs[k]:offs[k + 1]].reshape(np.asarray(C).shape) for k, C in enumerate(jt.clique_costs)], val
+
+
+def mot_lp_optimum(jt):
+    """The unregularised multi-marginal problem over the joint distribution of all
+    variables (eq. ot_graph): min sum_x (sum_c C_c(x_c)) pi(x) with the gamma marginals
+    fixed and unit mass, solved with HiGHS on the full joint tensor (tiny cases only)."""
+    V = len(jt.d)
+    shape = tuple(int(v) for v in jt.d)
+    idx = np.indices(shape).reshape(V, -1)
+    cost = np.zeros(idx.shape[1])
+    for cv, C in zip(jt.clique_vars, jt.clique_costs):
+        cost += np.asarray(C, dtype=np.float64)[tuple(idx[v] for v in cv)]
+    A, rhs = [np.ones((1, idx.shape[1]))], [np.ones(1)]
+    for s in range(len(jt.sep_vars)):
+        g = jt.sep_gamma[s]
+        if g is None:
+            continue
+        P = _projection(jt.d, tuple(range(V)), tuple(g))
+        A.append(P)
+        rhs.append(np.asarray(jt.sep_mu[s], dtype=np.float64).reshape(-1))
+    res = linprog(cost, A_eq=np.vstack(A), b_eq=np.concatenate(rhs), bounds=(0, None), method="highs")
+    assert res.status == 0, res.message
+    return float(res.fun)
