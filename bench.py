@@ -569,6 +569,58 @@ def bench_fig4(dev, stream, seeds: int = 5, delta: float = 0.2):
                       "loglog_exponent_vs_E": float(exp_E)}}
 
 
+FIG4_WLS_D = (5, 10, 20, 40, 80)       # d at |E| = 12 cliques
+FIG4_WLS_E = (2, 3, 4, 6, 8, 12, 16)   # cliques at d = 10
+
+
+def bench_fig4_wls(dev, stream, seeds: int = 5, delta: float = 0.2, alpha: float = 10.0):
+    """The Wasserstein least-squares half of the paper's experiment (Sec. 5, Fig. 4(b)):
+    each instance's modified junction tree reduced to its tree of separators
+    (x_0 x x_{J+1} centre of d^2 points, J constrained leaves) and solved by the same
+    kernels, eps = delta / (4 J log d), stopping sum below delta / (8 C_inf); mean
+    half-steps against d at J = 12 and against J at d = 10, all instances in one batch."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+    from paper_2406_10849_gb300 import junction as JR
+
+    cases = [(12, d) for d in FIG4_WLS_D] + [(J, 10) for J in FIG4_WLS_E if J != 12]
+    by_tol = {}
+    for (J, d) in cases:
+        for sd in range(seeds):
+            jt = gen.wls_junction_tree(6_500_000 + 1000 * J + 10 * d + sd, J, d, alpha, delta)
+            by_tol.setdefault(round(jt.meta["tol"], 12), []).append(((J, d), JR.reduce_junction_tree(jt)))
+    rows = {}
+    dt = 0.0
+    for tol, items in by_tol.items():   # one handle per stopping threshold (C_inf depends on J)
+        probs = [t for _, t in items]
+        s = T.Solver(probs, T.options(precision="fp32", tol=tol, tol_kind="sum", max_half_steps=400000),
+                     stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, res = s.solve()
+        dt += time.perf_counter() - t0
+        s.close()
+        for (k, _), r in zip(items, res):
+            rows.setdefault(k, []).append((r["half_steps"], r["status"]))
+    def row(k):
+        hs = [h for h, _ in rows[k]]
+        return {"J": k[0], "d": k[1], "half_steps_mean": float(np.mean(hs)), "half_steps": hs,
+                "certified": int(sum(1 for _, st in rows[k] if st == 0))}
+    vs_d = [row((12, d)) for d in FIG4_WLS_D]
+    vs_E = [row((J, 10)) for J in FIG4_WLS_E]
+    ld = np.log(np.array(FIG4_WLS_D, dtype=np.float64))
+    yd = np.array([r["half_steps_mean"] for r in vs_d])
+    slope_d, icpt_d = np.polyfit(ld, yd, 1)
+    r2_d = 1.0 - float(np.sum((yd - (slope_d * ld + icpt_d)) ** 2) / np.sum((yd - yd.mean()) ** 2))
+    exp_E = float(np.polyfit(np.log(np.array(FIG4_WLS_E, dtype=np.float64)),
+                             np.log(np.array([r["half_steps_mean"] for r in vs_E])), 1)[0])
+    return {"workload": f"fig4_wls_alpha{alpha}_delta{delta}", "instances": sum(len(v) for v in rows.values()),
+            "seconds": dt, "vs_d_at_E12": vs_d, "vs_E_at_d10": vs_E,
+            "trend": {"half_steps_per_log_d": float(slope_d), "r2_vs_log_d": r2_d, "loglog_exponent_vs_E": exp_E}}
+
+
 def bench_chain(dev, stream, steps: int):
     """The 5-node chain (n = 64 grid, eps = 0.01, FP64 handle): microseconds per
     half-step (CUDA events) and the solve to a stopping sum below 1e-9."""
@@ -771,6 +823,7 @@ def run_fig4(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     b = bench_fig4(dev, stream)
+    b["wls"] = bench_fig4_wls(dev, stream)
     line = {"metric": "half-steps to the stopping threshold delta' (mean over seeds)", "value": b["seconds"],
             "unit": "s for all instances", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * b["seconds"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -999,6 +1052,7 @@ def main():
         extra["star"] = bench_star(dev, stream, max(ks, 50))
         extra["chain_fp64"] = bench_chain(dev, stream, max(ks, 200))
         extra["fig4"] = bench_fig4(dev, stream)
+        extra["fig4_wls"] = bench_fig4_wls(dev, stream)
     cpu = None if (args.no_cpu or world > 1) else cpu_baseline(p)  # the host baseline: N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
