@@ -367,33 +367,51 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// tcgen05 variant of the product.  One CTA of 4 warps per 128 x 128 output
-// tile.  A stage holds 64 reduction points of K'hi, K'lo, V'hi and V'lo, each a
-// 128 x 64 BF16 box brought by one TMA copy (cp.async.bulk.tensor) in the
-// 128-byte-swizzled K-major layout the MMA descriptors describe (measured
-// faster than six stages of 64-byte-swizzled 128 x 32 boxes, 223 against 255 us
-// per product on 2000 stars, and than 128 x 256 tiles in two 96 KB stages, 253 us).  Thread 0
-// keeps kTcStages stages in flight: it waits for a stage's copies (full
-// barrier, transaction count), issues its 12 MMAs (kind::f16: BF16 operands
-// from shared memory, FP32 accumulators in tensor memory, 128 x 128 x 16
-// each), commits them to the stage's empty barrier, and refills the previous
-// stage's buffer once that stage's MMAs are done (one stage of MMAs always
-// queued behind the running one).  The accumulators
-// come back with tcgen05.ld, one output row per thread.  Every wait is
-// bounded; a wait that runs out sets bit 1 of the error word.
+// tcgen05 variant of the product: a persistent, warp-specialised kernel, one
+// CTA per SM walking 128 x 128 output tiles (row tiles fastest, so the CTAs
+// working on one column tile of V' at a time share it through L2).  A stage
+// holds 64 reduction points of K'hi, K'lo, V'hi and V'lo, each a 128 x 64 BF16
+// box brought by one TMA copy (cp.async.bulk.tensor) in the 128-byte-swizzled
+// K-major layout the MMA descriptors describe; three 64 KB stages.
+//   warp 0 (one lane): TMA producer -- waits for a stage to be free (empty
+//     barrier), posts its transaction count and the four copies (full barrier);
+//   warp 1 (one lane): MMA issuer -- per stage waits for the copies, issues 12
+//     tcgen05.mma (kind::f16: BF16 operands from shared memory, FP32
+//     accumulators in tensor memory, 128 x 128 x 16 each: the three split
+//     products), commits them to the stage's empty barrier; after a tile's
+//     last stage commits to that accumulator's full barrier;
+//   warps 2-5: epilogue -- read a finished accumulator with tcgen05.ld (each
+//     warp its 32-lane quarter of tensor memory, one output row per thread),
+//     write the partials, release the accumulator (empty barrier).
+// Two accumulators (2 x 128 tensor-memory columns) let the epilogue of one
+// tile run under the MMAs of the next, and the producer runs up to three
+// stages ahead across tile boundaries.  (Measured on 2000 stars: 115 us per
+// product against 165 us for one CTA per tile; 128 x 256 tiles in two 96 KB
+// stages also 115 us, an L2 prefetch of the next tile's V' 120 us; the tensor
+// pipe is active 40 % of the time, so the three stages of operands in flight
+// per SM, not the pipe, limit it.)  Tiles whose columns are all inactive
+// are skipped by every role alike (the same test on the same data).  Every
+// wait is bounded; a wait that runs out sets bit 1 of the error word and stops
+// every role; before tensor memory is released the MMA issuer waits (bounded)
+// for its last commit and the producer for every copy it issued.
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 192;                       // producer, MMA, four epilogue warps
 constexpr int kTcK = 64;                              // reduction points per stage (128-byte rows)
-constexpr int kTcTileBytes = kSkTileM * kTcK * 2;     // 16 KB
-constexpr int kTcStageBytes = 4 * kTcTileBytes;       // 64 KB
-constexpr int kTcStages = 3;
+constexpr int kTcN = 128;                             // output columns per tile (MMA N)
+constexpr int kTcTileBytes = kSkTileM * kTcK * 2;     // 16 KB: one K' part (128 rows)
+constexpr int kTcBBytes = kTcN * kTcK * 2;            // one V' part (kTcN columns)
+constexpr int kTcStageBytes = 2 * kTcTileBytes + 2 * kTcBBytes;
+constexpr int kTcStages = kTcN == 256 ? 2 : 3;
+constexpr int kTcAcc = 2;                             // accumulators in tensor memory
+constexpr int kTcMaxTiles = 512;                      // tiles one CTA may own (the grid grows beyond)
 constexpr size_t kTcSmem = kTcStages * kTcStageBytes + 1024;  // stages + alignment slack
-constexpr uint32_t kTcCols = kSkTileN;                        // tensor memory columns (N FP32 accumulators per row)
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSkTileN >> 3) << 17) |
+constexpr uint32_t kTcCols = kTcAcc * kTcN;                   // tensor memory columns
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = kTcN, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kSkTileM >> 4) << 24);
 constexpr uint64_t kTcWaitNs = 250ull * 1000 * 1000;  // a wait gives up after 250 ms
-static_assert(kSkTileM == 128 && kSkTileN == 128 && kSkPadK % kTcK == 0, "the tcgen05 tile is 128 x 128 x 64");
+static_assert(kSkTileM == 128 && (kTcN == 128 || kTcN == 256) && kSkPadK % kTcK == 0, "tcgen05 tile 128 x N x 64");
+static_assert(kTcStages * kTcStageBytes + 1024 <= 227 * 1024, "stages fit in shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -452,35 +470,57 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// whether any column of the column tile starting at n0 takes part in this product
+__device__ __forceinline__ bool tc_tile_active(const SkArgs& A, int n0) {
+  for (int c = 0; c < kTcN; ++c) {
+    const int j = n0 + c;
+    if (j >= A.ncols) break;
+    if (A.cmax[j] > -kInf && col_active(A, A.cols[j])) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 __global__ void __launch_bounds__(kTcThreads, 1)
     sk_gemm_tc_kernel(const __grid_constant__ SkArgs A, const __grid_constant__ CUtensorMap tkhi,
                       const __grid_constant__ CUtensorMap tklo, const __grid_constant__ CUtensorMap tvhi,
                       const __grid_constant__ CUtensorMap tvlo) {
   extern __shared__ __align__(16) unsigned char tc_raw[];
-  __shared__ SkCol s_cols[kSkTileN];
-  __shared__ int s_act[kSkTileN];
-  __shared__ float s_cm[kSkTileN];
-  __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages];
+  __shared__ SkCol s_cols[kTcN];
+  __shared__ int s_act[kTcN];
+  __shared__ float s_cm[kTcN];
+  __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages], s_afull[kTcAcc], s_aempty[kTcAcc];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_ok;
+  __shared__ int s_tiles[kTcMaxTiles];   // this CTA's active tiles, in order
+  __shared__ int s_ntiles;
+  __shared__ volatile int s_abort;
+  __shared__ int s_epi_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // row tiles vary fastest: the CTAs that share a column tile of V' run together (L2 reuse)
-  const int m0 = blockIdx.x * kSkTileM, n0 = blockIdx.y * kSkTileN;
-  if (blockIdx.x == 0 && blockIdx.y == 0)  // the envelope is consumed: reset it for the next product
+  const int mt = A.mp / kSkTileM;                              // row tiles
+  const int ntiles = mt * ((A.ncols + kTcN - 1) / kTcN);
+  if (blockIdx.x == 0)  // the envelope is consumed: reset it for the next product
     for (int y = tid; y < A.kd; y += kTcThreads) A.b[y] = -kInf;
-  bool any = false;
-  {
-    const int j = n0 + tid;  // one column per thread
-    int act = 0;
-    if (j < A.ncols) {
-      s_cols[tid] = A.cols[j];
-      s_cm[tid] = A.cmax[j];
-      act = col_active(A, s_cols[tid]) && s_cm[tid] > -kInf ? 1 : 0;
-    }
-    s_act[tid] = act;
-    any = act != 0;
+  // this CTA's tiles (t = blockIdx.x + i gridDim.x), the inactive ones left out
+  if (tid == 0) {
+    int n = 0;
+    for (int t = blockIdx.x; t < ntiles && n < kTcMaxTiles; t += gridDim.x)
+      if (tc_tile_active(A, (t / mt) * kTcN)) s_tiles[n++] = t;
+    s_ntiles = n;
+    s_abort = 0;
   }
-  if (!__syncthreads_or(any)) return;
+  __syncthreads();
+  const int nt = s_ntiles;
+  if (nt == 0) return;  // block-uniform
 
   // stages on a 1024-byte boundary (the swizzle pattern follows the address bits)
   const uint32_t raw = smem_u32(tc_raw);
@@ -490,10 +530,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[i])));
     }
+    for (int i = 0; i < kTcAcc; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_afull[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&s_aempty[i])));  // one per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_ok = 1;
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                  "r"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -504,96 +547,150 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = s_tmem;
   const int nk = A.kd / kTcK;
 
-  if (tid == 0) {
-    auto issue = [&](int kt) {
-      const int b = kt % kTcStages;
-      const uint32_t dst = stage0 + b * kTcStageBytes;
-      tc_expect(&s_full[b], kTcStageBytes);
-      tma_box(dst, &tkhi, kt * kTcK, m0, &s_full[b]);
-      tma_box(dst + kTcTileBytes, &tklo, kt * kTcK, m0, &s_full[b]);
-      tma_box(dst + 2 * kTcTileBytes, &tvhi, kt * kTcK, n0, &s_full[b]);
-      tma_box(dst + 3 * kTcTileBytes, &tvlo, kt * kTcK, n0, &s_full[b]);
-    };
-    int issued = 0;
-    for (; issued < kTcStages && issued < nk; ++issued) issue(issued);
-    bool ok = true;
-    int kt = 0;
-    for (; kt < nk; ++kt) {
-      const int b = kt % kTcStages;
-      const uint32_t par = (kt / kTcStages) & 1;
-      if (!tc_wait(&s_full[b], par)) {
-        ok = false;
-        break;
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      int g = 0;  // stage uses so far, across tiles
+      bool ok = true;
+      for (int i = 0; i < nt && ok; ++i) {
+        const int t = s_tiles[i];
+        const int m0 = (t % mt) * kSkTileM, n0 = (t / mt) * kTcN;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int b = g % kTcStages;
+          if (g >= kTcStages && !tc_wait(&s_empty[b], ((g / kTcStages) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          if (s_abort) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = stage0 + b * kTcStageBytes;
+          tc_expect(&s_full[b], kTcStageBytes);
+          tma_box(dst, &tkhi, kt * kTcK, m0, &s_full[b]);
+          tma_box(dst + kTcTileBytes, &tklo, kt * kTcK, m0, &s_full[b]);
+          tma_box(dst + 2 * kTcTileBytes, &tvhi, kt * kTcK, n0, &s_full[b]);
+          tma_box(dst + 2 * kTcTileBytes + kTcBBytes, &tvlo, kt * kTcK, n0, &s_full[b]);
+        }
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = stage0 + b * kTcStageBytes;
-      const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + kTcTileBytes);
-      const uint64_t bh = sw128_desc(sa + 2 * kTcTileBytes), bl = sw128_desc(sa + 3 * kTcTileBytes);
-      for (int k = 0; k < kTcK / 16; ++k) {
-        const uint64_t dk = (uint64_t)((k * 32) >> 4);  // 16 BF16 further along K
-        tc_mma(tmem, ah + dk, bh + dk, (kt | k) != 0 ? 1u : 0u);
-        tc_mma(tmem, ah + dk, bl + dk, 1u);
-        tc_mma(tmem, al + dk, bh + dk, 1u);
+      if (!ok) {
+        s_abort = 1;
+        atomicOr(A.err, 2);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&s_empty[b]))
-                   : "memory");
-      // refill the previous stage's buffer once its MMAs (queued ahead of this
-      // stage's, so the tensor pipe never runs dry) have read it
-      if (kt >= 1 && issued < nk) {
-        const int pb = (kt - 1) % kTcStages;
-        if (!tc_wait(&s_empty[pb], ((kt - 1) / kTcStages) & 1)) {
+      // every copy issued lands before the CTA may leave (bounded)
+      for (int q = (g > kTcStages ? g - kTcStages : 0); q < g; ++q)
+        (void)tc_wait(&s_full[q % kTcStages], (q / kTcStages) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      int last_acc = -1, last_use = 0;
+      for (int i = 0; i < nt && ok; ++i) {
+        const int a = i % kTcAcc;
+        if (i >= kTcAcc && !tc_wait(&s_aempty[a], ((i / kTcAcc) - 1) & 1)) {
           ok = false;
-          ++kt;
           break;
         }
-        issue(issued++);
-      }
-    }
-    if (!ok) {
-      // let every copy already issued land before the CTA may leave (bounded)
-      for (int q = kt; q < issued; ++q) (void)tc_wait(&s_full[q % kTcStages], (q / kTcStages) & 1);
-      s_ok = 0;
-    }
-  }
-  __syncthreads();
-  bool ok = s_ok != 0;
-  // the last commit covers every MMA issued before it
-  if (ok) ok = tc_wait(&s_empty[(nk - 1) % kTcStages], ((nk - 1) / kTcStages) & 1);
-  ok = __syncthreads_and(ok);
-  if (!ok) {
-    if (tid == 0) atomicOr(A.err, 2);
-  } else {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int x = m0 + warp * 32 + lane;  // tensor-memory lane = output row
-    for (int c0 = 0; c0 < kSkTileN; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (x >= A.nx) continue;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int cl = c0 + i;
-        if (!s_act[cl]) continue;
-        const SkCol& col = s_cols[cl];
-        const float S = __uint_as_float(v[i]);
-        if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
-          const int slot = atomicAdd(A.fix_count, 1);
-          A.fix_list[slot] = make_int2(x, n0 + cl);
-          continue;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(a * kTcN);
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int b = g % kTcStages;
+          if (!tc_wait(&s_full[b], (g / kTcStages) & 1) || s_abort) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = stage0 + b * kTcStageBytes;
+          const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + kTcTileBytes);
+          const uint64_t bh = sw128_desc(sa + 2 * kTcTileBytes), bl = sw128_desc(sa + 2 * kTcTileBytes + kTcBBytes);
+          for (int k = 0; k < kTcK / 16; ++k) {
+            const uint64_t dk = (uint64_t)((k * 32) >> 4);  // 16 BF16 further along K
+            tc_mma(d, ah + dk, bh + dk, (kt | k) != 0 ? 1u : 0u);
+            tc_mma(d, ah + dk, bl + dk, 1u);
+            tc_mma(d, al + dk, bh + dk, 1u);
+          }
+          tc_commit(&s_empty[b]);  // the stage's buffer is free once these MMAs have read it
         }
-        A.part32[col.part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
+        if (!ok) break;
+        tc_commit(&s_afull[a]);  // the tile's accumulator is complete once every MMA before it is
+        last_acc = a;
+        last_use = i / kTcAcc;
       }
+      if (!ok) {
+        s_abort = 1;
+        atomicOr(A.err, 2);
+      }
+      // the last commit covers every MMA issued before it: wait for it before tensor memory goes
+      if (last_acc >= 0) (void)tc_wait(&s_afull[last_acc], last_use & 1);
+      if (g > 0) (void)tc_wait(&s_empty[(g - 1) % kTcStages], ((g - 1) / kTcStages) & 1);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warps 2..5, tensor-memory lane quarter warp % 4 ----
+    const int et = tid - 64;                 // 0..127 within the epilogue group
+    const int quarter = warp & 3;
+    for (int i = 0; i < nt; ++i) {
+      const int a = i % kTcAcc;
+      const int t = s_tiles[i];
+      const int m0 = (t % mt) * kSkTileM, n0 = (t / mt) * kTcN;
+      epi_sync();  // the previous tile's column table is no longer read
+      for (int c = et; c < kTcN; c += 128) {  // the tile's column table
+        const int j = n0 + c;
+        int act = 0;
+        if (j < A.ncols) {
+          s_cols[c] = A.cols[j];
+          s_cm[c] = A.cmax[j];
+          act = col_active(A, s_cols[c]) && s_cm[c] > -kInf ? 1 : 0;
+        }
+        s_act[c] = act;
+      }
+      if (et == 0) s_epi_ok = tc_wait(&s_afull[a], (i / kTcAcc) & 1) && !s_abort ? 1 : 0;
+      epi_sync();
+      if (!s_epi_ok) {
+        if (et == 0) {
+          s_abort = 1;
+          atomicOr(A.err, 2);
+        }
+        break;  // uniform across the epilogue group
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int x = m0 + quarter * 32 + lane;  // tensor-memory lane = output row
+      for (int c0 = 0; c0 < kTcN; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kTcN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (x >= A.nx) continue;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int cl = c0 + q;
+          if (!s_act[cl]) continue;
+          const float S = __uint_as_float(v[q]);
+          if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
+            const int slot = atomicAdd(A.fix_count, 1);
+            A.fix_list[slot] = make_int2(x, n0 + cl);
+            continue;
+          }
+          A.part32[s_cols[cl].part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
+        }
+      }
+      // this warp's reads of the accumulator are done: release it to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) tc_arrive(&s_aempty[a]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
 // one warp per listed output: frame = the largest term on the 2^-10 grid, then
@@ -687,17 +784,17 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
     state.store(ok ? 1 : 2);
   }
   if (state.load() != 1 || a.ncols <= 0) return false;
-  auto make = [&](CUtensorMap* map, const void* base, int64_t rows) {
+  auto make = [&](CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
     const cuuint64_t dims[2] = {(cuuint64_t)a.kd, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)a.kd * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kSkTileM};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  return make(&m->khi, a.khi, a.mp) && make(&m->klo, a.klo, a.mp) && make(&m->vhi, a.vhi, a.ncols) &&
-         make(&m->vlo, a.vlo, a.ncols);
+  return make(&m->khi, a.khi, a.mp, kSkTileM) && make(&m->klo, a.klo, a.mp, kSkTileM) &&
+         make(&m->vhi, a.vhi, a.ncols, kTcN) && make(&m->vlo, a.vlo, a.ncols, kTcN);
 }
 
 cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaEvent_t before_product,
@@ -710,10 +807,18 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
   sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
   if (before_product) cudaEventRecord(before_product, s);
   const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
-  if (a.use_tc)
-    sk_gemm_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo);
-  else
+  if (a.use_tc) {
+    // persistent: one CTA per SM (shared memory allows no second), more only if a CTA
+    // would own more tiles than its table holds
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (int)grid.x * ((a.ncols + kTcN - 1) / kTcN);
+    const int ctas = std::max(std::min(ntiles, sms), (ntiles + kTcMaxTiles - 1) / kTcMaxTiles);
+    sk_gemm_tc_kernel<<<ctas, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo);
+  } else {
     sk_gemm_kernel<<<grid, kSkThreads, kSkSmem, s>>>(a);
+  }
   if (after_product) cudaEventRecord(after_product, s);
   sk_fixup_kernel<<<152 * 8, 256, 0, s>>>(a);
   return cudaGetLastError();
