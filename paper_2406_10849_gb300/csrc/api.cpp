@@ -276,6 +276,8 @@ struct tree_ot_handle {
   std::vector<Span> prof_spans;
   // persistent forest launch (TREE_OT_OPT_PERSISTENT): 0 = off, else the register
   // budget in CTAs per SM (2 or 3) the create-time timing chose
+  int32_t* d_live = nullptr;               // problems the FP32 applies process (see ApplyArgs::fp32_live)
+  int32_t nfixed_chunks[2] = {0, 0};       // per colour: its first chunks belong to fixed nodes
   int persistent = 0;
   int forest_D = 0;
   uint32_t forest_smem = 0;
@@ -433,6 +435,7 @@ ApplyArgs apply_args(tree_ot_handle* h, int colour) {
   a.arho = h->d_arho;
   a.err = h->d_err;
   a.test_stall = (h->opt.flags & TREE_OT_OPT_TEST_STALL) ? 1 : 0;
+  a.fp32_live = h->fp64 ? nullptr : h->d_live;
   return a;
 }
 
@@ -486,6 +489,8 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.lowp_span = h->d_lowp_span;
   a.lowp_best = h->d_lowp_best;
   a.lowp_best_t = h->d_lowp_best_t;
+  a.fp32_live = h->fp64 ? nullptr : h->d_live;
+  a.count_launch = 1;
   return a;
 }
 
@@ -576,7 +581,20 @@ int launch_apply(tree_ot_handle* h, int colour, cudaStream_t s, bool only_stored
 
 int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
   const int p0 = prof_mark(h, s);
-  cudaError_t e = launch_node_update(node_args(h, colour, retire), h->fp64, s);
+  NodeArgs a = node_args(h, colour, retire);
+  const int32_t nf = h->nfixed_chunks[colour], nall = a.nchunks;
+  cudaError_t e = cudaSuccess;
+  if (nf > 0) {  // fixed nodes' chunks first, with the kernel that has no free-node path
+    a.nchunks = nf;
+    a.count_launch = nf == nall ? 1 : 0;
+    e = launch_node_update(a, h->fp64, true, s);
+  }
+  if (e == cudaSuccess && nall > nf) {
+    a.chunks = h->d_chunks[colour] + nf;
+    a.nchunks = nall - nf;
+    a.count_launch = 1;
+    e = launch_node_update(a, h->fp64, false, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "node update launch");
   prof_span(h, TREE_OT_PROF_NODE_UPDATE, p0, prof_mark(h, s));
   if (!h->fp64) h->f_stale = true;
@@ -619,6 +637,14 @@ int launch_forest_chunk(tree_ot_handle* h, int G, bool retire, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "persistent forest launch");
   prof_span(h, TREE_OT_PROF_FOREST, p0, prof_mark(h, s));
   h->f_stale = true;  // the node updates advanced the operand past the stored potentials
+  return TREE_OT_OK;
+}
+
+// the count of problems the FP32 applies process, from the done and phase flags
+// (after the host changes either)
+int recount_live(tree_ot_handle* h, cudaStream_t s) {
+  if (h->fp64) return TREE_OT_OK;
+  CUDA_TRY(launch_count_live(h->d_done, h->lowp ? h->d_lowp : nullptr, h->nprob, h->d_live, s));
   return TREE_OT_OK;
 }
 
@@ -712,6 +738,7 @@ int reset_state(tree_ot_handle* h, cudaStream_t s) {
     CUDA_TRY(cudaStreamSynchronize(s));
     RC_TRY(launch_absorb_step(h, s));
   }
+  RC_TRY(recount_live(h, s));
   h->hs_host = 0;
   h->have_check = false;
   return TREE_OT_OK;
@@ -1595,14 +1622,17 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     if (!h->sk.empty()) h->lowp = true;
   }
   h->node_smem[0] = h->node_smem[1] = 0;
-  for (size_t j = 0; j < h->nodes.size(); ++j) {
-    const NodeD& nd = h->nodes[j];
-    const int32_t cp = node_chunk_points(nd.n, nd.deg);
-    for (int32_t c = 0; c < nd.nchunks; ++c)
-      h->chunks[nd.colour].push_back(NodeChunk{(int32_t)j, c, c * cp, std::min(cp, nd.n - c * cp)});
-    const uint32_t b = node_smem_layout(nd.deg, std::min(cp, nd.n), h->fp64).bytes;
-    h->node_smem[nd.colour] = std::max(h->node_smem[nd.colour], b);
-  }
+  for (int pass = 0; pass < 2; ++pass)  // per colour: the fixed nodes' chunks, then the free nodes'
+    for (size_t j = 0; j < h->nodes.size(); ++j) {
+      const NodeD& nd = h->nodes[j];
+      if ((pass == 0) != (nd.fixed != 0)) continue;
+      const int32_t cp = node_chunk_points(nd.n, nd.deg);
+      for (int32_t c = 0; c < nd.nchunks; ++c)
+        h->chunks[nd.colour].push_back(NodeChunk{(int32_t)j, c, c * cp, std::min(cp, nd.n - c * cp)});
+      if (pass == 0) h->nfixed_chunks[nd.colour] += nd.nchunks;
+      const uint32_t b = node_smem_layout(nd.deg, std::min(cp, nd.n), h->fp64).bytes;
+      h->node_smem[nd.colour] = std::max(h->node_smem[nd.colour], b);
+    }
   if (std::max(h->node_smem[0], h->node_smem[1]) > kNodeSmemMax)
     return bail(fail(TREE_OT_ERR_ARG, "a node's degree is too high for the node update"));
   for (size_t e = 0; e < h->edges.size(); ++e) {
@@ -1634,6 +1664,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       (rc = h->alloc(&h->d_zpart, h->nzchunks)) || (rc = h->alloc(&h->d_resid_acc, ND)) ||
       (rc = h->alloc(&h->d_resid_dedge, ND)) || (rc = h->alloc(&h->d_res_sum, (int64_t)kResidRing * num_probs)) ||
       (rc = h->alloc(&h->d_res_max, (int64_t)kResidRing * num_probs)) || (rc = h->alloc(&h->d_done, num_probs)) ||
+      (rc = h->alloc(&h->d_live, 1)) ||
       (rc = h->alloc(&h->d_done_at, num_probs)) || (rc = h->alloc(&h->d_node_arrive, NN)) ||
       (rc = h->alloc(&h->d_node_count, num_probs)) || (rc = h->alloc(&h->d_launch_count, 1)) ||
       (rc = h->alloc(&h->d_hs, 1)) || (rc = h->alloc(&h->d_ptol, num_probs)) ||
@@ -1805,6 +1836,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   if ((rc = reset_state(h, s))) return bail(rc);
   // the autotuners time the FP32 kernels: no problem in a BF16 phase meanwhile
   CUDA_TRY(cudaMemsetAsync(h->d_lowp, 0, sizeof(int32_t) * h->nprob, s));
+  if ((rc = recount_live(h, s))) return bail(rc);
   if (o.autotune && !h->fp64 && (rc = autotune_recompute(h, s))) return bail(rc);
   if (!h->fp64) {
     if ((rc = upload_stream_tasks(h, s))) return bail(rc);
@@ -2002,6 +2034,7 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
     CUDA_TRY(cudaMemcpyAsync(h->d_deadline, h->h_deadline.data(), sizeof(int64_t) * h->nprob, cudaMemcpyHostToDevice,
                              s));
     CUDA_TRY(cudaMemcpyAsync(h->d_done, h->h_done.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+    RC_TRY(recount_live(h, s));
     if (any_later) {
       RC_TRY(queue_half_steps(h, 1, true, s));
       CUDA_TRY(cudaMemcpyAsync(h->h_done.data(), h->d_done, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, s));
@@ -2009,6 +2042,7 @@ int tree_ot_solve(tree_ot_handle* h, void* cuda_stream, tree_ot_result* results)
       for (int p = 0; p < h->nprob; ++p)
         if (later[p]) h->h_done[p] = 0;
       CUDA_TRY(cudaMemcpyAsync(h->d_done, h->h_done.data(), sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, s));
+      RC_TRY(recount_live(h, s));
       RC_TRY(queue_half_steps(h, 1, true, s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));

@@ -226,6 +226,8 @@ __device__ void col_task(const ApplyArgs& A, const Task& t, float* sm) {
 
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_dense_kernel(ApplyArgs A) {
   __shared__ __align__(16) float sm[2 * kColRows + 2 * 8 * kColCols];  // 12 KB
+  // every problem retired or in a BF16 phase: nothing to apply (the same for every CTA)
+  if (A.fp32_live && *((volatile const int32_t*)A.fp32_live) <= 0) return;
   for (int ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
     const Task t = A.tasks[ti];
     const int prob = A.dedges[t.dedge].prob;
@@ -246,6 +248,9 @@ template <int D, int MINB, bool EXACT>
 __global__ void __launch_bounds__(kApplyThreads, MINB) apply_recomp_kernel(ApplyArgs A) {
   __shared__ __align__(16) float sm[16 * kApplyThreads + 2 * 4 * kApplyThreads];  // 24 KB
   __shared__ int s_ti;
+  // every problem retired or in a BF16 phase: nothing to apply (the same for every CTA; the
+  // work queue is then untouched and stays reset)
+  if (A.fp32_live && *((volatile const int32_t*)A.fp32_live) <= 0) return;
   for (;;) {
     if (threadIdx.x == 0) s_ti = atomicAdd(&A.queue[0], 1);
     __syncthreads();

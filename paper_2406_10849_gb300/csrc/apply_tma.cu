@@ -416,6 +416,8 @@ constexpr size_t kTmaSmem = (size_t)kStages * kStageBytes + 2 * (size_t)kTaskBuf
                             (size_t)kConsumers * kColCols * sizeof(float2);
 
 __global__ void __launch_bounds__(kTmaThreads, 1) apply_dense_tma_kernel(ApplyArgs A) {
+  // every problem retired or in a BF16 phase: nothing to apply (the same for every CTA)
+  if (A.fp32_live && *((volatile const int32_t*)A.fp32_live) <= 0) return;
   extern __shared__ __align__(128) char dyn[];
   char* stages = dyn;                                 // kStages x 32 KB
   char* tbufs = dyn + kStages * kStageBytes;          // 2 x (hh, hl, frames)

@@ -171,6 +171,8 @@ struct ApplyArgs {
   int32_t* err;              // error word: bit 1 = a bounded wait of a staged kernel ran out
   const StreamTask* stasks;  // staged kernel: resolved stored-cost tasks (ntasks of them)
   int32_t test_stall;        // staged kernel: the producer issues nothing (tests the timeout path)
+  const int32_t* fp32_live;  // problems the FP32 kernels still process (not retired, not in a BF16
+                             // phase); 0 = the launch has nothing to do (null: always run)
 };
 
 struct AbsorbArgs {
@@ -245,6 +247,9 @@ struct NodeArgs {
   int64_t* lowp_span;        // per problem: half-steps at which the BF16 phase began / ended (-1: not yet)
   double* lowp_best;         // per problem: smallest stopping quantity seen in the BF16 phase
   int64_t* lowp_best_t;      // per problem: the half-step of that last improvement
+  int32_t* fp32_live;        // count of problems the FP32 applies process (kept by the last node
+                             // of a problem as it retires or enters / leaves a BF16 phase; may be null)
+  int32_t count_launch;      // 1: the last CTA of the launch advances the half-step counter
 };
 
 // FP64-grade check of the current potentials.  Per element the exponent
@@ -279,7 +284,11 @@ cudaError_t launch_apply_f32(const ApplyArgs& a, int slot, int variant, int grid
 bool apply_tma_available();
 cudaError_t launch_apply_tma(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_apply_f64(const ApplyArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s);
+// fixed_only: every chunk of the launch belongs to a fixed node (a kernel without
+// the free-node path, so more CTAs fit on an SM)
+cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cudaStream_t s);
+// *out = number of problems with done == 0 and lowp != 1 (lowp may be null: all count)
+cudaError_t launch_count_live(const int32_t* done, const int32_t* lowp, int32_t nprob, int32_t* out, cudaStream_t s);
 // FP32 handles: the stored potentials f from the operand (hh, hl) and log2 mu
 cudaError_t launch_materialise_f(const DEdgeD* dedges, int32_t ndedges, const NodeD* nodes, const ProbD* probs,
                                  const float4* lgf, const float* hh, const float* hl, double* f, cudaStream_t s);

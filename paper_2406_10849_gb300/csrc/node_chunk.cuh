@@ -357,6 +357,7 @@ __device__ __forceinline__ float2 regrid(float hi, float lo) {
   return make_float2(hi + q, lo - q);
 }
 
+template <bool FIXED_ONLY>
 __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
                                unsigned char* sm, int node_id) {
   const int deg = nd.deg, cnt = c.cnt, np = deg * cnt;
@@ -391,19 +392,21 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   // kIt pairs per thread, as a chunk holds at most kNodePairs pairs)
   constexpr int kIt = kNodePairs / kNodeThreads;
 
-  if (nd.fixed) {  // a leaf: one edge, one pass
+  if (FIXED_ONLY || nd.fixed) {  // a leaf: one edge, one pass
+    // the fixed-leaf kernel batches two pairs per thread (fewer live registers, more CTAs per SM)
+    constexpr int kItF = FIXED_ONLY ? 2 : kIt;
     const DEdgeD& d = s_de[0];
     const float2 zk = s_zk[0];
     const int ns = one_piece ? 1 : d.nsplit;
     const double eps_ln2 = P.eps * kLn2;
     float r = 0.f;
     bool drift = false;
-    for (int xb = 0; xb < cnt; xb += kIt * kNodeThreads) {
-      Part2 pv[kIt];
-      float4 lg[kIt];
-      float oh[kIt], ol[kIt];
+    for (int xb = 0; xb < cnt; xb += kItF * kNodeThreads) {
+      Part2 pv[kItF];
+      float4 lg[kItF];
+      float oh[kItF], ol[kItF];
 #pragma unroll
-      for (int k = 0; k < kIt; ++k) {
+      for (int k = 0; k < kItF; ++k) {
         const int x = c.x0 + min(xb + tid + k * kNodeThreads, cnt - 1);  // past the end: reload the last point
         pv[k] = load_part2(A.part32 + d.part_off + x, ns, nd.n);
         lg[k] = A.lgf[nd.node_off + x];  // log2 mu (hi, lo), mu
@@ -411,7 +414,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
         ol[k] = A.hl[d.off + x];
       }
 #pragma unroll
-      for (int k = 0; k < kIt; ++k) {
+      for (int k = 0; k < kItF; ++k) {
         const int xi = xb + tid + k * kNodeThreads;
         if (xi >= cnt) break;
         const int x = c.x0 + xi;
@@ -544,7 +547,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
 // chunk's arrival bookkeeping: the last chunk of a node merges Z_j and the
 // node's stopping terms; the last node of a problem records the stopping
 // quantity of iterate t_now and (when asked) retires the problem.
-template <bool F64>
+template <bool F64, bool FIXED_ONLY = false>
 __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChunk c, int64_t t_now,
                                                 unsigned char* node_sm, double* red) {
   const NodeD nd = A.nodes[c.node];
@@ -556,7 +559,7 @@ __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChu
     if constexpr (F64)
       chunk_update64(A, nd, c, P, red, node_sm, c.node);
     else
-      chunk_update32(A, nd, c, P, red, node_sm, c.node);
+      chunk_update32<FIXED_ONLY>(A, nd, c, P, red, node_sm, c.node);
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -601,6 +604,7 @@ __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChu
       if (lp == 2 && t_now + 1 >= A.lowp_start) {
         // enter the low-precision phase: absorb every edge of the problem next
         A.lowp[p] = 1;
+        if (A.fp32_live) atomicSub(A.fp32_live, 1);  // the FP32 applies skip it from now on
         A.lowp_span[2 * p] = t_now + 1;
         A.lowp_best[p] = INFINITY;
         A.lowp_best_t[p] = t_now + 1;
@@ -612,16 +616,19 @@ __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChu
         if (crit < A.refine_tol || !(crit == crit)) {
           A.lowp[p] = 0;
           A.lowp_span[2 * p + 1] = t_now + 1;
+          if (A.fp32_live) atomicAdd(A.fp32_live, 1);  // back to the FP32 applies
         } else if (crit < 0.9 * A.lowp_best[p]) {
           A.lowp_best[p] = crit;
           A.lowp_best_t[p] = t_now;
         } else if (A.refine_tol > 0.0 && t_now - A.lowp_best_t[p] > kLowpStall) {
           A.lowp[p] = 0;
           A.lowp_span[2 * p + 1] = t_now + 1;
+          if (A.fp32_live) atomicAdd(A.fp32_live, 1);
         }
       } else if (A.retire && (crit < A.ptol[p] || t_now + 1 >= A.deadline[p])) {
         A.done[p] = 1;
         A.done_at[p] = t_now + 1;
+        if (A.fp32_live) atomicSub(A.fp32_live, 1);  // retired: no FP32 apply any more
       }
       A.node_count[p] = 0;
       const int nslot = (int)((t_now + 1) % kResidRing);

@@ -34,20 +34,37 @@
 namespace treeot {
 namespace {
 
-template <bool F64>
-__global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
-  extern __shared__ __align__(16) unsigned char node_sm[];
-  __shared__ double red[kNodeThreads / 32];
-  const NodeChunk c = A.chunks[blockIdx.x];
-  const int64_t t_now = *((volatile const int64_t*)A.hs);
-  node_chunk_item<F64>(A, c, t_now, node_sm, red);
-  if (threadIdx.x != 0) return;
+// the last CTA of a launch that counts (count_launch) advances the half-step counter
+__device__ __forceinline__ void node_launch_done(const NodeArgs& A) {
+  if (threadIdx.x != 0 || !A.count_launch) return;
   __threadfence();
   if (atomicAdd(A.launch_count, 1) == (int)gridDim.x - 1) {
     *A.launch_count = 0;
     __threadfence();
     atomicAdd((unsigned long long*)A.hs, 1ull);
   }
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
+  extern __shared__ __align__(16) unsigned char node_sm[];
+  __shared__ double red[kNodeThreads / 32];
+  const NodeChunk c = A.chunks[blockIdx.x];
+  const int64_t t_now = *((volatile const int64_t*)A.hs);
+  node_chunk_item<F64, false>(A, c, t_now, node_sm, red);
+  node_launch_done(A);
+}
+
+// chunks of fixed leaves only: no free-node path, so a smaller register budget and
+// more CTAs per SM
+template <bool F64>
+__global__ void __launch_bounds__(kNodeThreads, 4) node_update_fixed_kernel(NodeArgs A) {
+  extern __shared__ __align__(16) unsigned char node_sm[];
+  __shared__ double red[kNodeThreads / 32];
+  const NodeChunk c = A.chunks[blockIdx.x];
+  const int64_t t_now = *((volatile const int64_t*)A.hs);
+  node_chunk_item<F64, true>(A, c, t_now, node_sm, red);
+  node_launch_done(A);
 }
 
 // stored potentials of an FP32 handle from the operand the node update keeps:
@@ -74,24 +91,41 @@ __global__ void __launch_bounds__(256) materialise_f_kernel(const DEdgeD* dedges
   }
 }
 
+__global__ void count_live_kernel(const int32_t* done, const int32_t* lowp, int32_t nprob, int32_t* out) {
+  int n = 0;
+  for (int p = threadIdx.x; p < nprob; p += blockDim.x) n += (done[p] == 0 && (!lowp || lowp[p] != 1)) ? 1 : 0;
+  n = __reduce_add_sync(0xffffffffu, n);
+  __shared__ int part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    *out = t;
+  }
+}
+
 }  // namespace
 
-cudaError_t launch_node_update(const NodeArgs& a, bool fp64, cudaStream_t s) {
+cudaError_t launch_count_live(const int32_t* done, const int32_t* lowp, int32_t nprob, int32_t* out, cudaStream_t s) {
+  count_live_kernel<<<1, 256, 0, s>>>(done, lowp, nprob, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cudaStream_t s) {
   if (a.nchunks <= 0) return cudaSuccess;
+  const void* fn = fp64 ? (fixed_only ? reinterpret_cast<const void*>(node_update_fixed_kernel<true>)
+                                      : reinterpret_cast<const void*>(node_update_kernel<true>))
+                        : (fixed_only ? reinterpret_cast<const void*>(node_update_fixed_kernel<false>)
+                                      : reinterpret_cast<const void*>(node_update_kernel<false>));
   // more than the default 48 KB of dynamic shared memory only for nodes of very
   // high degree; the attribute is per device and cheap to set again
   if (a.smem > 48u * 1024) {
-    const cudaError_t e =
-        fp64 ? cudaFuncSetAttribute(node_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem)
-             : cudaFuncSetAttribute(node_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)a.smem);
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
     if (e != cudaSuccess) return e;
   }
-  if (fp64)
-    node_update_kernel<true><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
-  else
-    node_update_kernel<false><<<a.nchunks, kNodeThreads, a.smem, s>>>(a);
-  return cudaGetLastError();
+  void* args[] = {const_cast<NodeArgs*>(&a)};
+  return cudaLaunchKernel(fn, dim3(a.nchunks), dim3(kNodeThreads), args, a.smem, s);
 }
 
 cudaError_t launch_materialise_f(const DEdgeD* dedges, int32_t ndedges, const NodeD* nodes, const ProbD* probs,
