@@ -1060,7 +1060,9 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "nodes": p.num_nodes, "edges": p.num_edges, "n": 4096, "dim": 3,
                    "eps": 0.01, "cost": f"stored dense FP32, {stats['matrix_bytes_per_half_step'] / 1e9:.2f} GB", "step": "one half-step (apply + node update)",
-                   "l2": "inputs (4.2 GB) exceed L2", "elements_per_step": stats["elements_per_half_step"]},
+                   "l2": f"inputs ({stats['matrix_bytes_per_half_step'] / 1e9:.2f} GB of costs) "
+                         f"{'exceed' if stats['matrix_bytes_per_half_step'] > 129e6 else 'fit in'} L2 (129 MB)",
+                   "elements_per_step": stats["elements_per_half_step"]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * K,
     }
     line.update(extra)

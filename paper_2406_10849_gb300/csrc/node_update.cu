@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
   node_launch_done(A);
 }
 
-// chunks of fixed leaves only: no free-node path, so a smaller register budget and
-// more CTAs per SM
+// chunks of fixed leaves only: without the free-node path the FP32 form fits in
+// 64 registers, so four CTAs share an SM instead of three
 template <bool F64>
 __global__ void __launch_bounds__(kNodeThreads, 4) node_update_fixed_kernel(NodeArgs A) {
   extern __shared__ __align__(16) unsigned char node_sm[];
