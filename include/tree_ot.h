@@ -142,6 +142,17 @@ typedef struct tree_ot_problem {
  * the failure path without a GPU fault).  tree_ot_apply / tree_ot_node_update
  * always launch their own kernels. */
 #define TREE_OT_OPT_PERSISTENT  64u
+/* Node update bookkeeping.  Each CTA updates a chunk of one node's points;
+ * the node's normaliser Z_j, its stopping terms and the problem's stopping
+ * quantity (with phase control and retirement) are finished either by the
+ * last-arriving chunk (arrival counters: fences and serial atomics on a
+ * chunk's way out) or by one extra launch after the chunks (one warp per
+ * problem), chosen per colour: the extra launch when the colour has more than
+ * four chunks per SM, where the chunks' exit latency outweighs it
+ * (plan_stats[14], bit c for colour c).  Same arithmetic either way; these
+ * bits force one form for every colour (DEFER wins if both are set). */
+#define TREE_OT_OPT_NODE_DEFER  128u
+#define TREE_OT_OPT_NODE_ARRIVE 256u
 #define TREE_OT_OPT_SK_MMA_SYNC 32u /* shared-kernel BF16 phase: multiply with the legacy
                                        mma.sync kernel instead of tcgen05 (tensor memory
                                        accumulators); for comparison and for devices
@@ -382,7 +393,9 @@ int tree_ot_get_potentials_batch(tree_ot_handle *h, void *cuda_stream, int32_t c
  * as chosen by the autotuner, [12] 1 when stored costs stream through the
  * bulk-copy staged kernel (TREE_OT_OPT_DENSE_TMA or the autotuner's choice),
  * [13] 0 when half-steps run as per-half-step launches, else the persistent
- * forest kernel's CTAs per SM (TREE_OT_OPT_PERSISTENT). */
+ * forest kernel's CTAs per SM (TREE_OT_OPT_PERSISTENT), [14] bit c set when
+ * colour c's node update finishes its bookkeeping in an extra launch
+ * (TREE_OT_OPT_NODE_DEFER). */
 int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
 /* Launch timing (no paper counterpart: measurement support).  While enabled,

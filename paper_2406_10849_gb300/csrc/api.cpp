@@ -278,6 +278,10 @@ struct tree_ot_handle {
   // budget in CTAs per SM (2 or 3) the create-time timing chose
   int32_t* d_live = nullptr;               // problems the FP32 applies process (see ApplyArgs::fp32_live)
   int32_t nfixed_chunks[2] = {0, 0};       // per colour: its first chunks belong to fixed nodes
+  bool node_defer[2] = {false, false};     // per colour: bookkeeping in node_finish_kernel
+  SkRefD* d_skref = nullptr;               // per directed edge: its shared-kernel product's output
+  int32_t* d_fin[2] = {nullptr, nullptr};  // per colour: the FinishList arrays, one allocation
+  FinishList fin[2] = {};
   int persistent = 0;
   int forest_D = 0;
   uint32_t forest_smem = 0;
@@ -485,6 +489,7 @@ NodeArgs node_args(tree_ot_handle* h, int colour, bool retire) {
   a.drift = h->d_drift;
   a.refine_tol = h->opt.refine_tol;
   a.tau = (float)h->opt.absorb_tau;
+  a.sk_ref = h->d_skref;
   a.lowp_start = h->opt.lowp_start;
   a.lowp_span = h->d_lowp_span;
   a.lowp_best = h->d_lowp_best;
@@ -583,17 +588,23 @@ int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
   const int p0 = prof_mark(h, s);
   NodeArgs a = node_args(h, colour, retire);
   const int32_t nf = h->nfixed_chunks[colour], nall = a.nchunks;
+  const bool defer = h->node_defer[colour];
+  a.defer = defer ? 1 : 0;
   cudaError_t e = cudaSuccess;
   if (nf > 0) {  // fixed nodes' chunks first, with the kernel that has no free-node path
     a.nchunks = nf;
-    a.count_launch = nf == nall ? 1 : 0;
+    a.count_launch = (nf == nall && !defer) ? 1 : 0;
     e = launch_node_update(a, h->fp64, true, s);
   }
   if (e == cudaSuccess && nall > nf) {
     a.chunks = h->d_chunks[colour] + nf;
     a.nchunks = nall - nf;
-    a.count_launch = 1;
+    a.count_launch = defer ? 0 : 1;
     e = launch_node_update(a, h->fp64, false, s);
+  }
+  if (e == cudaSuccess && defer) {  // the bookkeeping; its last CTA advances the half-step counter
+    a.count_launch = 1;
+    e = launch_node_finish(a, h->fin[colour], s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "node update launch");
   prof_span(h, TREE_OT_PROF_NODE_UPDATE, p0, prof_mark(h, s));
@@ -1181,7 +1192,7 @@ int plan_shared_kernels(tree_ot_handle* h, const tree_ot_problem* probs, int32_t
   for (size_t di = 0; di < h->dedges.size(); ++di) {
     const DEdgeD& d = h->dedges[di];
     if (!ok[d.prob]) continue;
-    h->sk[dgroup[di]].cols[h->nodes[d.owner].colour].push_back(SkCol{d.rev_off, d.part_off, d.prob});
+    h->sk[dgroup[di]].cols[h->nodes[d.owner].colour].push_back(SkCol{d.rev_off, d.part_off, d.prob, (int32_t)di});
   }
   std::vector<tree_ot_handle::SkGroup> kept;
   for (auto& g : h->sk)
@@ -1200,7 +1211,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
     const ProbD& pd = h->probs[g.prob_rep];
     const int32_t mp = (int32_t)align_up(own.n, kSkTileM), kd = (int32_t)align_up(nbn.n, kSkPadK);
     const int64_t maxc = (int64_t)std::max(g.cols[0].size(), g.cols[1].size());
-    float *b = nullptr, *rf = nullptr, *cmax = nullptr;
+    float *b = nullptr, *rf = nullptr, *cmax = nullptr, *sout = nullptr;
     __nv_bfloat16 *khi = nullptr, *klo = nullptr, *vhi = nullptr, *vlo = nullptr;
     SkCol* dc[2] = {nullptr, nullptr};
     int32_t* fix_count = nullptr;
@@ -1208,7 +1219,8 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
     if ((rc = h->alloc(&b, kd)) || (rc = h->alloc(&rf, mp)) || (rc = h->alloc(&cmax, maxc)) ||
         (rc = h->alloc(&khi, (int64_t)mp * kd)) ||
         (rc = h->alloc(&klo, (int64_t)mp * kd)) || (rc = h->alloc(&vhi, maxc * kd)) ||
-        (rc = h->alloc(&vlo, maxc * kd)) || (rc = h->alloc(&dc[0], (int64_t)g.cols[0].size())) ||
+        (rc = h->alloc(&vlo, maxc * kd)) || (rc = h->alloc(&sout, maxc * own.n)) ||
+        (rc = h->alloc(&dc[0], (int64_t)g.cols[0].size())) ||
         (rc = h->alloc(&dc[1], (int64_t)g.cols[1].size())) || (rc = h->alloc(&fix_count, 1)) ||
         (rc = h->alloc(&fix_list, (int64_t)own.n * maxc)))
       return rc;
@@ -1241,6 +1253,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       a.vhi = vhi;
       a.vlo = vlo;
       a.part32 = h->d_part32;
+      a.sout = sout;
       a.fix_count = fix_count;
       a.fix_list = fix_list;
       a.err = h->d_err;
@@ -1252,6 +1265,16 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       if (g.args[c].ncols > 0 && !sk_encode_maps(g.args[c], &g.maps[c])) tc = false;
     for (int c = 0; c < 2; ++c) g.args[c].use_tc = tc ? 1 : 0;
     CUDA_TRY(launch_sk_reset(b, kd, s));
+  }
+  if (!h->sk.empty()) {  // per directed edge: where its colour's product leaves the message
+    std::vector<SkRefD> ref(h->dedges.size(), SkRefD{nullptr, nullptr, nullptr});
+    for (auto& g : h->sk)
+      for (int c = 0; c < 2; ++c)
+        for (size_t j = 0; j < g.cols[c].size(); ++j)
+          ref[g.cols[c][j].dedge] =
+              SkRefD{g.args[c].sout + (int64_t)j * g.args[c].nx, g.args[c].rf, g.args[c].cmax + j};
+    if ((rc = h->alloc(&h->d_skref, (int64_t)ref.size()))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(h->d_skref, ref.data(), sizeof(SkRefD) * ref.size(), cudaMemcpyHostToDevice, s));
   }
   return TREE_OT_OK;
 }
@@ -1635,6 +1658,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     }
   if (std::max(h->node_smem[0], h->node_smem[1]) > kNodeSmemMax)
     return bail(fail(TREE_OT_ERR_ARG, "a node's degree is too high for the node update"));
+
   for (size_t e = 0; e < h->edges.size(); ++e) {
     const EdgeD& ed = h->edges[e];
     for (int32_t o0 = 0; o0 < ed.na; o0 += 64)
@@ -1823,6 +1847,39 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     for (int v = 0; v < 2; ++v) h->rec_grid[v][slot] = sms * apply_ctas_per_sm(slot, v);
   }
   h->bf16_grid = sms * apply_bf16_ctas_per_sm();
+  for (int c = 0; c < 2; ++c) {  // deferred node bookkeeping: where, and what it reads
+    if (o.flags & TREE_OT_OPT_NODE_DEFER)
+      h->node_defer[c] = true;
+    else if (o.flags & TREE_OT_OPT_NODE_ARRIVE)
+      h->node_defer[c] = false;
+    else
+      h->node_defer[c] = (int64_t)h->chunks[c].size() > 4 * (int64_t)sms;
+    // per problem: the colour's owned directed edges, then its free nodes
+    const int32_t np = h->nprob;
+    std::vector<std::vector<int32_t>> dl(np), nl(np);
+    for (size_t j = 0; j < h->nodes.size(); ++j) {
+      const NodeD& nd = h->nodes[j];
+      if (nd.colour != c) continue;
+      for (int32_t i = 0; i < nd.deg; ++i) dl[nd.prob].push_back(h->node_dedges[nd.dedge_begin + i]);
+      if (!nd.fixed) nl[nd.prob].push_back((int32_t)j);
+    }
+    // one array: dbeg [np + 1], dedges, nbeg [np + 1], nodes
+    std::vector<int32_t> buf(np + 1, 0);
+    for (int32_t p = 0; p < np; ++p) {
+      buf[p + 1] = buf[p] + (int32_t)dl[p].size();
+      buf.insert(buf.end(), dl[p].begin(), dl[p].end());
+    }
+    const size_t nb = buf.size();
+    buf.resize(nb + np + 1, 0);
+    for (int32_t p = 0; p < np; ++p) {
+      buf[nb + p + 1] = buf[nb + p] + (int32_t)nl[p].size();
+      buf.insert(buf.end(), nl[p].begin(), nl[p].end());
+    }
+    if ((rc = h->alloc(&h->d_fin[c], (int64_t)buf.size())) ||
+        (rc = up(h->d_fin[c], buf.data(), sizeof(int32_t) * buf.size())))
+      return bail(rc);
+    h->fin[c] = FinishList{h->d_fin[c], h->d_fin[c] + (np + 1), h->d_fin[c] + nb, h->d_fin[c] + nb + (np + 1)};
+  }
   {
     cudaError_t ce = cudaStreamCreateWithFlags(&h->hstream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
@@ -2412,7 +2469,7 @@ int tree_ot_profile_read(tree_ot_handle* h, double* ms, int64_t* launches, int32
 int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
   g_err.clear();
   if (!h || !stats || nstats < 0) return fail(TREE_OT_ERR_ARG, "bad handle or stats pointer");
-  const int64_t v[14] = {(int64_t)h->dedges.size(),
+  const int64_t v[15] = {(int64_t)h->dedges.size(),
                         (int64_t)h->edges.size(),
                         h->elems,
                         h->matrix_bytes,
@@ -2425,8 +2482,9 @@ int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
                         (int64_t)h->grid_mult,
                         (int64_t)h->rec_variant,
                         (int64_t)h->dense_tma,
-                        (int64_t)h->persistent};
-  for (int32_t i = 0; i < nstats && i < 14; ++i) stats[i] = v[i];
+                        (int64_t)h->persistent,
+                        (int64_t)((h->node_defer[0] ? 1 : 0) | (h->node_defer[1] ? 2 : 0))};
+  for (int32_t i = 0; i < nstats && i < 15; ++i) stats[i] = v[i];
   return TREE_OT_OK;
 }
 

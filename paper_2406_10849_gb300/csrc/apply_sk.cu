@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
       const SkCol col = A.cols[c0 + k];
       off = col.h_off;
       if (col_active(A, col))
-        for (int y0 = 4 * lane; y0 < A.ny; y0 += 4 * 32) {
+#pragma unroll 4
+        for (int y0 = 4 * lane; y0 < A.ny; y0 += 4 * 32) {  // unrolled: several loads in flight
           float v[4];
           load_sum4(A.hh + off, A.hl + off, y0, A.ny, v);
           m = fmaxf(m, fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3])));
@@ -92,7 +93,8 @@ __global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
   __syncthreads();
   for (int y0 = 4 * (int)threadIdx.x; y0 < A.ny; y0 += 4 * 256) {
     float e[4] = {-kInf, -kInf, -kInf, -kInf};
-    for (int k = 0; k < nc; ++k) {
+#pragma unroll 8
+    for (int k = 0; k < nc; ++k) {  // unrolled: the columns' loads are independent
       if (!(s_m[k] > -kInf)) continue;
       const float* hh = A.hh + s_off[k];
       const float* hl = A.hl + s_off[k];
@@ -113,6 +115,69 @@ __global__ void __launch_bounds__(256) sk_envelope_kernel(SkArgs A) {
     for (int i = 0; i < 4; ++i)
       if (y0 + i < A.ny) atomic_max_float(&A.b[y0 + i], e[i]);
   }
+}
+
+// Supports of at most 1024 points: one pass over the operands.  Thread t owns
+// the points 4t .. 4t+3; columns come kEnvBatch at a time, their values are
+// loaded once into registers, the batch's maxima are reduced across the CTA and
+// the normalised values folded into the thread's envelope (the two-pass kernel
+// above reads every operand twice, the second time mostly from DRAM again).
+constexpr int kEnvBatch = 8;
+__global__ void __launch_bounds__(256) sk_envelope1_kernel(SkArgs A) {
+  __shared__ float s_part[8][kEnvBatch];
+  __shared__ float s_m[kEnvBatch];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * kEnvCols, nc = min(kEnvCols, A.ncols - c0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.fix_count = 0;  // the previous fix-up is done
+  const int y0 = 4 * (int)threadIdx.x;
+  float e[4] = {-kInf, -kInf, -kInf, -kInf};
+  for (int kb = 0; kb < nc; kb += kEnvBatch) {
+    float v[kEnvBatch][4];
+    float m[kEnvBatch];
+#pragma unroll
+    for (int i = 0; i < kEnvBatch; ++i) {
+      const int k = kb + i;
+      bool on = false;
+      int64_t off = 0;
+      if (k < nc) {
+        const SkCol col = A.cols[c0 + k];
+        on = col_active(A, col);
+        off = col.h_off;
+      }
+      if (on && y0 < A.ny) {
+        load_sum4(A.hh + off, A.hl + off, y0, A.ny, v[i]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[i][q] = -kInf;
+      }
+      m[i] = fmaxf(fmaxf(v[i][0], v[i][1]), fmaxf(v[i][2], v[i][3]));
+    }
+#pragma unroll
+    for (int i = 0; i < kEnvBatch; ++i) m[i] = warp_max(m[i]);
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < kEnvBatch; ++i) s_part[warp][i] = m[i];
+    __syncthreads();
+    if (threadIdx.x < kEnvBatch) {
+      float mm = s_part[0][threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) mm = fmaxf(mm, s_part[w][threadIdx.x]);
+      const float mq = mm > -kInf ? quant(mm) : -kInf;
+      s_m[threadIdx.x] = mq;
+      if (kb + (int)threadIdx.x < nc) A.cmax[c0 + kb + threadIdx.x] = mq;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kEnvBatch; ++i) {
+      const float M = s_m[i];
+      if (M > -kInf)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = fmaxf(e[q], v[i][q] - M);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (y0 + q < A.ny) atomic_max_float(&A.b[y0 + q], e[q]);
 }
 
 __device__ __forceinline__ float sqdist(const float* p, const float* q, int dim) {
@@ -286,7 +351,7 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
     if (j < A.ncols) {
       s_cols[tid] = A.cols[j];
       s_cm[tid] = A.cmax[j];
-      act = col_active(A, s_cols[tid]) && s_cm[tid] > -kInf ? 1 : 0;
+      act = col_active(A, s_cols[tid]) ? 1 : 0;  // (M = -inf: every term is zero)
     }
     s_act[tid] = act;
     any = act != 0;
@@ -344,7 +409,7 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
     __syncthreads();  // this stage is refilled by the next iteration's loads
   }
 
-  // epilogue: partial (R(x), S(x,j)) into piece 0, the other pieces emptied
+  // epilogue: the sum S(x,j) (the node update adds the frame R(x) + M_j)
   const int gid = lane >> 2, tig = lane & 3;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -355,14 +420,19 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
         const int x = m0 + wm + 16 * i + gid + (r >= 2 ? 8 : 0);
         const int cl = wn + 8 * j + 2 * tig + (r & 1);
         if (x >= A.nx || !s_act[cl]) continue;
-        const SkCol& col = s_cols[cl];
+        float* const so = A.sout + (int64_t)(n0 + cl) * A.nx;
+        if (!(s_cm[cl] > -kInf)) {  // an empty column (V' not built): no message
+          so[x] = 0.f;
+          continue;
+        }
         const float S = acc[i][j][r];
         if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
           const int slot = atomicAdd(A.fix_count, 1);
           A.fix_list[slot] = make_int2(x, n0 + cl);
+          so[x] = -1.f;
           continue;
         }
-        A.part32[col.part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
+        so[x] = fminf(S, FLT_MAX);
       }
 }
 
@@ -380,22 +450,26 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
 //     accumulators in tensor memory, 128 x 128 x 16 each: the three split
 //     products), commits them to the stage's empty barrier; after a tile's
 //     last stage commits to that accumulator's full barrier;
-//   warps 2-5: epilogue -- read a finished accumulator with tcgen05.ld (each
-//     warp its 32-lane quarter of tensor memory, one output row per thread),
-//     write the partials, release the accumulator (empty barrier).
+//   warps 2-9: epilogue -- read a finished accumulator with tcgen05.ld (each
+//     warp its 32-lane quarter of tensor memory, warp % 4, one output row per
+//     thread, and one half of the tile's columns), write the partials,
+//     release the accumulator (empty barrier, one arrival per warp).
 // Two accumulators (2 x 128 tensor-memory columns) let the epilogue of one
 // tile run under the MMAs of the next, and the producer runs up to three
-// stages ahead across tile boundaries.  (Measured on 2000 stars: 115 us per
-// product against 165 us for one CTA per tile; 128 x 256 tiles in two 96 KB
-// stages also 115 us, an L2 prefetch of the next tile's V' 120 us; the tensor
-// pipe is active 40 % of the time, so the three stages of operands in flight
-// per SM, not the pipe, limit it.)  Tiles whose columns are all inactive
+// stages ahead across tile boundaries.  The epilogue writes one float per
+// output, the sum S (the node update adds the frame R(x) + M_j): on 2000
+// stars the kernel took 117 us with four epilogue warps writing (frame, sum)
+// pairs and re-reading the row frame after every store, 94 us with eight
+// warps and the frame in a register, and 65.5 us with no stores at all;
+// writing half the bytes brings it to the latter (the operands' 1 GB of TMA
+// reads already keep L2 busy).  Tiles whose columns are all inactive
 // are skipped by every role alike (the same test on the same data).  Every
 // wait is bounded; a wait that runs out sets bit 1 of the error word and stops
 // every role; before tensor memory is released the MMA issuer waits (bounded)
 // for its last commit and the producer for every copy it issued.
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 192;                       // producer, MMA, four epilogue warps
+constexpr int kTcEpiWarps = 8;                        // two per tensor-memory lane quarter (4 or 8)
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;     // producer, MMA, epilogue warps
 constexpr int kTcK = 64;                              // reduction points per stage (128-byte rows)
 constexpr int kTcN = 128;                             // output columns per tile (MMA N)
 constexpr int kTcTileBytes = kSkTileM * kTcK * 2;     // 16 KB: one K' part (128 rows)
@@ -475,7 +549,7 @@ __device__ __forceinline__ bool tc_tile_active(const SkArgs& A, int n0) {
   for (int c = 0; c < kTcN; ++c) {
     const int j = n0 + c;
     if (j >= A.ncols) break;
-    if (A.cmax[j] > -kInf && col_active(A, A.cols[j])) return true;
+    if (col_active(A, A.cols[j])) return true;  // (an empty column still gets S = 0 written)
   }
   return false;
 }
@@ -489,16 +563,15 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kTcEpiWarps) : "memory"); }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     sk_gemm_tc_kernel(const __grid_constant__ SkArgs A, const __grid_constant__ CUtensorMap tkhi,
                       const __grid_constant__ CUtensorMap tklo, const __grid_constant__ CUtensorMap tvhi,
                       const __grid_constant__ CUtensorMap tvlo) {
   extern __shared__ __align__(16) unsigned char tc_raw[];
-  __shared__ SkCol s_cols[kTcN];
-  __shared__ int s_act[kTcN];
-  __shared__ float s_cm[kTcN];
+  __shared__ int64_t s_off[kTcN];  // the tile's columns: offset of their sums in sout (-1: inactive)
+  __shared__ float s_cm[kTcN];     // and column maximum (-inf: an empty column, S = 0)
   __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages], s_afull[kTcAcc], s_aempty[kTcAcc];
   __shared__ uint32_t s_tmem;
   __shared__ int s_tiles[kTcMaxTiles];   // this CTA's active tiles, in order
@@ -532,7 +605,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int i = 0; i < kTcAcc; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_afull[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&s_aempty[i])));  // one per epilogue warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_aempty[i])), "n"(kTcEpiWarps));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -629,23 +702,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     __syncwarp();
   } else {
-    // ---- epilogue: warps 2..5, tensor-memory lane quarter warp % 4 ----
-    const int et = tid - 64;                 // 0..127 within the epilogue group
+    // ---- epilogue: warps 2..9, tensor-memory lane quarter warp % 4, column half (warp - 2) / 4 ----
+    const int et = tid - 64;  // 0 .. 32 kTcEpiWarps - 1 within the epilogue group
     const int quarter = warp & 3;
+    constexpr int kSpan = kTcN * 4 / kTcEpiWarps;  // columns per warp
+    const int c_beg = ((warp - 2) >> 2) * kSpan;
     for (int i = 0; i < nt; ++i) {
       const int a = i % kTcAcc;
       const int t = s_tiles[i];
       const int m0 = (t % mt) * kSkTileM, n0 = (t / mt) * kTcN;
       epi_sync();  // the previous tile's column table is no longer read
-      for (int c = et; c < kTcN; c += 128) {  // the tile's column table
+      for (int c = et; c < kTcN; c += 32 * kTcEpiWarps) {  // the tile's column table
         const int j = n0 + c;
-        int act = 0;
-        if (j < A.ncols) {
-          s_cols[c] = A.cols[j];
-          s_cm[c] = A.cmax[j];
-          act = col_active(A, s_cols[c]) && s_cm[c] > -kInf ? 1 : 0;
+        float cm = -kInf;
+        int64_t off = -1;
+        if (j < A.ncols && col_active(A, A.cols[j])) {
+          cm = A.cmax[j];
+          off = (int64_t)j * A.nx;
         }
-        s_act[c] = act;
+        s_off[c] = off;
+        s_cm[c] = cm;
       }
       if (et == 0) s_epi_ok = tc_wait(&s_afull[a], (i / kTcAcc) & 1) && !s_abort ? 1 : 0;
       epi_sync();
@@ -658,27 +734,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int x = m0 + quarter * 32 + lane;  // tensor-memory lane = output row
-      for (int c0 = 0; c0 < kTcN; c0 += 16) {
-        uint32_t v[16];
+      const bool row_in = x < A.nx;
+      float* const sout = A.sout;
+      for (int c0 = c_beg; c0 < c_beg + kSpan; c0 += 32) {
+        uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kTcN + c0);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (x >= A.nx) continue;
+        if (!row_in) continue;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < 32; ++q) {
           const int cl = c0 + q;
-          if (!s_act[cl]) continue;
+          const int64_t off = s_off[cl];
+          if (off < 0) continue;
+          if (s_cm[cl] == -kInf) {  // an empty column (V' not built): no message
+            sout[off + x] = 0.f;
+            continue;
+          }
           const float S = __uint_as_float(v[q]);
           if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
             const int slot = atomicAdd(A.fix_count, 1);
             A.fix_list[slot] = make_int2(x, n0 + cl);
+            sout[off + x] = -1.f;
             continue;
           }
-          A.part32[s_cols[cl].part_off + x] = make_float2(A.rf[x] + s_cm[cl], fminf(S, FLT_MAX));
+          sout[off + x] = fminf(S, FLT_MAX);
         }
       }
       // this warp's reads of the accumulator are done: release it to the MMA issuer
@@ -707,12 +795,14 @@ __global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
     float p[3] = {0.f, 0.f, 0.f};
     for (int d = 0; d < A.dim; ++d) p[d] = A.xc[(int64_t)x * A.dim + d];
     float mx = -kInf;
+#pragma unroll 4
     for (int y = lane; y < A.ny; y += 32)
       mx = fmaxf(mx, fmaf(-sqdist(p, A.yc + (int64_t)y * A.dim, A.dim), A.s_hi, hh[y]));
     mx = warp_max(mx);
     float R = 0.f, S = 0.f;
     if (mx > -kInf) {
       R = quant(mx);
+#pragma unroll 4
       for (int y = lane; y < A.ny; y += 32) {
         if (!(hh[y] > -kInf)) continue;
         const float c = sqdist(p, A.yc + (int64_t)y * A.dim, A.dim);
@@ -802,7 +892,10 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
   if (a.ncols <= 0) return cudaSuccess;
   if (a.use_tc && !maps) return cudaErrorInvalidValue;
   if (!(a.use_tc ? sk_tc_ready() : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
-  sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
+  if (a.ny <= 4 * 256)
+    sk_envelope1_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
+  else
+    sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
   sk_kbuild_kernel<<<a.mp, 256, 0, s>>>(a);
   sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
   if (before_product) cudaEventRecord(before_product, s);

@@ -85,12 +85,30 @@ inline int32_t node_chunk_points(int32_t n, int32_t deg) {
   return c < n ? c : n;
 }
 
+// A directed edge of a shared-kernel group (BF16 phase): where the product of
+// its colour leaves the message's sum S(x) (one float per output; negative
+// where the output was listed for the exact fix-up, which writes (frame, sum)
+// to the partials instead), the group's row frames R(x) and the column's
+// maximum M_j; the message is R(x) + M_j + log2 S(x) (log2 units).
+struct SkRefD {
+  const float* s;
+  const float* rf;
+  const float* cm;
+};
+// the same, as a node-update CTA keeps it (the column maximum read once)
+struct SkEdgeS {
+  const float* s;
+  const float* rf;
+  float cm, pad;
+};
+
 // Node update: dynamic shared memory of one CTA (deg edges, cnt points), in
 // this order: edge records, neighbour normalisers, edge ids, drift flags,
-// per-edge stopping sums, per-pair messages and q, per-point s and mean q.
-// q and the sums are double for FP64 handles, float otherwise.
+// per-edge stopping sums, shared-kernel references, per-pair messages and q,
+// per-point s and mean q.  q and the sums are double for FP64 handles, float
+// otherwise.
 struct NodeSmem {
-  uint32_t de, zn, di, dr, r, mi, q, s, qb, bytes;
+  uint32_t de, zn, di, dr, r, sk, mi, q, s, qb, bytes;
 };
 __host__ __device__ inline uint32_t node_align16(uint32_t b) { return (b + 15u) & ~15u; }
 __host__ __device__ inline NodeSmem node_smem_layout(int32_t deg, int32_t cnt, bool f64) {
@@ -101,7 +119,8 @@ __host__ __device__ inline NodeSmem node_smem_layout(int32_t deg, int32_t cnt, b
   L.di = L.zn + node_align16((uint32_t)deg * 8u);
   L.dr = L.di + node_align16((uint32_t)deg * 4u);
   L.r = L.dr + node_align16((uint32_t)deg * 4u);
-  L.mi = L.r + node_align16((uint32_t)deg * qs);
+  L.sk = L.r + node_align16((uint32_t)deg * qs);
+  L.mi = L.sk + node_align16((uint32_t)deg * (uint32_t)sizeof(SkEdgeS));
   L.q = L.mi + node_align16(np * 8u);
   L.s = L.q + node_align16(np * qs);
   L.qb = L.s + node_align16((uint32_t)cnt * 8u);
@@ -250,6 +269,18 @@ struct NodeArgs {
   int32_t* fp32_live;        // count of problems the FP32 applies process (kept by the last node
                              // of a problem as it retires or enters / leaves a BF16 phase; may be null)
   int32_t count_launch;      // 1: the last CTA of the launch advances the half-step counter
+  int32_t defer;             // 1: chunks leave the arrival bookkeeping to node_finish_kernel
+  const SkRefD* sk_ref;      // per directed edge, for problems in the shared-kernel phase (or null)
+};
+
+// Per problem, what node_finish_kernel reads for one colour: the directed
+// edges owned by the colour's nodes (dedges[dbeg[p] .. dbeg[p+1])) and its
+// free nodes (nodes[nbeg[p] .. nbeg[p+1])).
+struct FinishList {
+  const int32_t* dbeg;
+  const int32_t* dedges;
+  const int32_t* nbeg;
+  const int32_t* nodes;
 };
 
 // FP64-grade check of the current potentials.  Per element the exponent
@@ -287,6 +318,8 @@ cudaError_t launch_apply_f64(const ApplyArgs& a, int grid, cudaStream_t s);
 // fixed_only: every chunk of the launch belongs to a fixed node (a kernel without
 // the free-node path, so more CTAs fit on an SM)
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cudaStream_t s);
+// the deferred bookkeeping of a node update of one colour (one warp per problem)
+cudaError_t launch_node_finish(const NodeArgs& a, const FinishList& l, cudaStream_t s);
 // *out = number of problems with done == 0 and lowp != 1 (lowp may be null: all count)
 cudaError_t launch_count_live(const int32_t* done, const int32_t* lowp, int32_t nprob, int32_t* out, cudaStream_t s);
 // FP32 handles: the stored potentials f from the operand (hh, hl) and log2 mu

@@ -318,6 +318,22 @@ __device__ __forceinline__ float2 split_l2(double v) {
 struct Part2 {
   float2 a, b;
 };
+// The one piece of a problem in the shared-kernel phase, in two steps so that a
+// thread's loads stay batched: load_sk_raw reads (R(x), S) -- the group's row
+// frame and the product's sum -- and resolve_sk makes the piece (R(x) + M_j, S),
+// or takes the exact fix-up's (frame, sum) where the product listed the output
+// (S < 0); S = 0 is an empty column (no message).
+__device__ __forceinline__ Part2 load_sk_raw(const SkEdgeS& e, int x) {
+  Part2 v;
+  v.a = make_float2(e.rf[x], e.s[x]);
+  v.b = make_float2(0.f, 0.f);
+  return v;
+}
+__device__ __forceinline__ void resolve_sk(Part2& v, float cm, const float2* part, int x) {
+  const float S = v.a.y;
+  v.a = S > 0.f ? make_float2(v.a.x + cm, S) : S == 0.f ? make_float2(0.f, 0.f) : part[x];
+}
+
 __device__ __forceinline__ Part2 load_part2(const float2* part, int nsplit, int64_t stride) {
   Part2 v;
   v.a = part[0];
@@ -371,7 +387,14 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   float* s_q = reinterpret_cast<float*>(sm + L.q);
   float2* s_s = reinterpret_cast<float2*>(sm + L.s);    // s log2(e)
   float* s_qb = reinterpret_cast<float*>(sm + L.qb);
+  SkEdgeS* s_sk = reinterpret_cast<SkEdgeS*>(sm + L.sk);
   const int tid = threadIdx.x, lane = tid & 31;
+  // the shared-kernel phase leaves one sum per output (its product's, or the
+  // fix-up's piece); drift from an absorbed base is tracked on stored-cost
+  // problems, the only ones absorbed
+  const int lp = A.absorbed ? A.lowp[nd.prob] : 0;
+  const bool track = lp == 1 && P.cost_kind == 0;
+  const bool one_piece = lp == 1 && P.cost_kind != 0 && A.sk_ref;
   for (int i = tid; i < deg; i += kNodeThreads) {
     const int di = A.node_dedges[nd.dedge_begin + i];
     const DEdgeD d = A.dedges[di];
@@ -380,13 +403,12 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
     s_di[i] = di;
     s_dr[i] = 0;
     s_r[i] = 0.f;
+    if (one_piece) {
+      const SkRefD r = A.sk_ref[di];
+      s_sk[i] = SkEdgeS{r.s, r.rf, *r.cm, 0.f};
+    }
   }
   __syncthreads();
-  // the shared-kernel phase leaves one partial per output; drift from an
-  // absorbed base is tracked on stored-cost problems, the only ones absorbed
-  const int lp = A.absorbed ? A.lowp[nd.prob] : 0;
-  const bool track = lp == 1 && P.cost_kind == 0;
-  const bool one_piece = lp == 1 && P.cost_kind != 0;
   bool bad = false;
   // a thread loads all its pairs of a pass before it stores anything (at most
   // kIt pairs per thread, as a chunk holds at most kNodePairs pairs)
@@ -408,7 +430,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
 #pragma unroll
       for (int k = 0; k < kItF; ++k) {
         const int x = c.x0 + min(xb + tid + k * kNodeThreads, cnt - 1);  // past the end: reload the last point
-        pv[k] = load_part2(A.part32 + d.part_off + x, ns, nd.n);
+        pv[k] = one_piece ? load_sk_raw(s_sk[0], x) : load_part2(A.part32 + d.part_off + x, ns, nd.n);
         lg[k] = A.lgf[nd.node_off + x];  // log2 mu (hi, lo), mu
         oh[k] = A.hh[d.off + x];
         ol[k] = A.hl[d.off + x];
@@ -418,6 +440,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
         const int xi = xb + tid + k * kNodeThreads;
         if (xi >= cnt) break;
         const int x = c.x0 + xi;
+        if (one_piece) resolve_sk(pv[k], s_sk[0].cm, A.part32 + d.part_off, x);
         const float2 mm = merge32_l2(pv[k], A.part32 + d.part_off + x, ns, nd.n);
         A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
         const float mh = mm.x - zk.x, ml = mm.y - zk.y;  // (m - Z_k) log2(e)
@@ -460,7 +483,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
         if (on) w.next(cnt);
         const DEdgeD& d = s_de[pi[k]];
         const int x = c.x0 + px[k];
-        pv[k] = load_part2(A.part32 + d.part_off + x, one_piece ? 1 : d.nsplit, nd.n);
+        pv[k] = one_piece ? load_sk_raw(s_sk[pi[k]], x) : load_part2(A.part32 + d.part_off + x, d.nsplit, nd.n);
         oh[k] = A.hh[d.off + x];  // f/eps log2(e) of the previous iterate
         ol[k] = A.hl[d.off + x];
       }
@@ -470,6 +493,7 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
         if (q >= np) break;
         const DEdgeD& d = s_de[pi[k]];
         const int x = c.x0 + px[k];
+        if (one_piece) resolve_sk(pv[k], s_sk[pi[k]].cm, A.part32 + d.part_off, x);
         const float2 mm = merge32_l2(pv[k], A.part32 + d.part_off + x, one_piece ? 1 : d.nsplit, nd.n);
         A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
         const float2 zk = s_zk[pi[k]];
@@ -542,11 +566,94 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
 }
 
+// Z_j of a free node from its chunks' (max, sum) pieces of s, and rho_j
+__device__ __forceinline__ void finish_free_node(const NodeArgs& A, int node, const NodeD& nd) {
+  double M = -INFINITY;
+  for (int k = 0; k < nd.nchunks; ++k) M = fmax(M, A.zpart[nd.chunk_base + k].x);
+  double S = 0.0;
+  for (int k = 0; k < nd.nchunks; ++k) {
+    const double2 z = A.zpart[nd.chunk_base + k];
+    S += z.y * exp(z.x - M);
+  }
+  const double Zn = M + log(S);
+  A.Z[node] = Zn;
+  A.rho[node] = -(double)nd.deg * Zn;
+}
+
+// The same, by a whole warp (every lane gets the result): the exponentials of
+// the chunks in parallel lanes, then the sum in chunk order by every lane, so
+// the result is bit-identical to finish_free_node's (FP64 transcendental work
+// by one lane at a time is slow on this GPU).
+__device__ __forceinline__ void finish_free_node_warp(const NodeArgs& A, int node, const NodeD& nd, int lane) {
+  double M = -INFINITY;
+  for (int k = lane; k < nd.nchunks; k += 32) M = fmax(M, A.zpart[nd.chunk_base + k].x);
+  M = warp_max_d(M);
+  double S = 0.0;
+  for (int k0 = 0; k0 < nd.nchunks; k0 += 32) {
+    double zy = 0.0, ex = 0.0;
+    if (k0 + lane < nd.nchunks) {
+      const double2 z = A.zpart[nd.chunk_base + k0 + lane];
+      zy = z.y;
+      ex = exp(z.x - M);
+    }
+    const int m = min(32, nd.nchunks - k0);
+    for (int i = 0; i < m; ++i) S += __shfl_sync(0xffffffffu, zy, i) * __shfl_sync(0xffffffffu, ex, i);
+  }
+  if (lane == 0) {
+    const double Zn = M + log(S);
+    A.Z[node] = Zn;
+    A.rho[node] = -(double)nd.deg * Zn;
+  }
+}
+
+// The stopping quantity of iterate t_now of problem p is complete (rs: the
+// sum of its terms, rm: the largest): phase control and retirement, then the
+// counters of the next launch.
+__device__ __forceinline__ void problem_after_update(const NodeArgs& A, int p, const ProbD& P, int64_t t_now,
+                                                     double rs, double rm) {
+  const double crit = A.tol_kind == 1 ? rm : rs;
+  const int lp = A.absorbed ? A.lowp[p] : 0;
+  if (lp == 2 && t_now + 1 >= A.lowp_start) {
+    // enter the low-precision phase: absorb every edge of the problem next
+    A.lowp[p] = 1;
+    if (A.fp32_live) atomicSub(A.fp32_live, 1);  // the FP32 applies skip it from now on
+    A.lowp_span[2 * p] = t_now + 1;
+    A.lowp_best[p] = INFINITY;
+    A.lowp_best_t[p] = t_now + 1;
+    for (int k = 0; k < P.edge_count; ++k) A.drift[P.edge_begin + k] = 1;
+  } else if (lp == 1) {
+    // the phase's accuracy is enough until the stopping quantity reaches
+    // refine_tol; from then on (or once the phase stops improving) the FP32
+    // kernel refines.  refine_tol = 0 keeps a problem in the phase.
+    if (crit < A.refine_tol || !(crit == crit)) {
+      A.lowp[p] = 0;
+      A.lowp_span[2 * p + 1] = t_now + 1;
+      if (A.fp32_live) atomicAdd(A.fp32_live, 1);  // back to the FP32 applies
+    } else if (crit < 0.9 * A.lowp_best[p]) {
+      A.lowp_best[p] = crit;
+      A.lowp_best_t[p] = t_now;
+    } else if (A.refine_tol > 0.0 && t_now - A.lowp_best_t[p] > kLowpStall) {
+      A.lowp[p] = 0;
+      A.lowp_span[2 * p + 1] = t_now + 1;
+      if (A.fp32_live) atomicAdd(A.fp32_live, 1);
+    }
+  } else if (A.retire && (crit < A.ptol[p] || t_now + 1 >= A.deadline[p])) {
+    A.done[p] = 1;
+    A.done_at[p] = t_now + 1;
+    if (A.fp32_live) atomicSub(A.fp32_live, 1);  // retired: no FP32 apply any more
+  }
+  A.node_count[p] = 0;
+  const int nslot = (int)((t_now + 1) % kResidRing);
+  A.res_sum[nslot * A.nprob + p] = 0.0;
+  A.res_max[nslot * A.nprob + p] = 0ull;
+}
+
 // One node-update item: chunk c of a node of the active colour at half-step
-// t_now (the number of half-steps done before it).  Thread 0 also does the
-// chunk's arrival bookkeeping: the last chunk of a node merges Z_j and the
-// node's stopping terms; the last node of a problem records the stopping
-// quantity of iterate t_now and (when asked) retires the problem.
+// t_now (the number of half-steps done before it).  Unless the launch defers
+// it to node_finish_kernel, thread 0 also does the chunk's arrival
+// bookkeeping: the last chunk of a node merges Z_j and the node's stopping
+// terms; the last node of a problem records the stopping quantity of iterate
+// t_now and (when asked) retires the problem.
 template <bool F64, bool FIXED_ONLY = false>
 __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChunk c, int64_t t_now,
                                                 unsigned char* node_sm, double* red) {
@@ -561,24 +668,14 @@ __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChu
     else
       chunk_update32<FIXED_ONLY>(A, nd, c, P, red, node_sm, c.node);
   }
+  if (A.defer) return;  // launch-uniform: the chunk's terms are in resid_acc and zpart
   __syncthreads();
   if (threadIdx.x != 0) return;
   __threadfence();
   if (!skip && atomicAdd(&A.node_arrive[c.node], 1) == nd.nchunks - 1) {
     // last chunk of this node: finish Z_j and the node's stopping terms
     __threadfence();
-    if (!nd.fixed) {
-      double M = -INFINITY;
-      for (int k = 0; k < nd.nchunks; ++k) M = fmax(M, A.zpart[nd.chunk_base + k].x);
-      double S = 0.0;
-      for (int k = 0; k < nd.nchunks; ++k) {
-        const double2 z = A.zpart[nd.chunk_base + k];
-        S += z.y * exp(z.x - M);
-      }
-      const double Zn = M + log(S);
-      A.Z[c.node] = Zn;
-      A.rho[c.node] = -(double)nd.deg * Zn;
-    }
+    if (!nd.fixed) finish_free_node(A, c.node, nd);
     double nsum = 0.0, nmax = 0.0;
     for (int i = 0; i < nd.deg; ++i) {
       const int di = A.node_dedges[nd.dedge_begin + i];
@@ -599,41 +696,7 @@ __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChu
       const double rs = *((volatile double*)&A.res_sum[slot * A.nprob + p]);
       const double rm = __longlong_as_double(
           (long long)*((volatile unsigned long long*)&A.res_max[slot * A.nprob + p]));
-      const double crit = A.tol_kind == 1 ? rm : rs;
-      const int lp = A.absorbed ? A.lowp[p] : 0;
-      if (lp == 2 && t_now + 1 >= A.lowp_start) {
-        // enter the low-precision phase: absorb every edge of the problem next
-        A.lowp[p] = 1;
-        if (A.fp32_live) atomicSub(A.fp32_live, 1);  // the FP32 applies skip it from now on
-        A.lowp_span[2 * p] = t_now + 1;
-        A.lowp_best[p] = INFINITY;
-        A.lowp_best_t[p] = t_now + 1;
-        for (int k = 0; k < P.edge_count; ++k) A.drift[P.edge_begin + k] = 1;
-      } else if (lp == 1) {
-        // the phase's accuracy is enough until the stopping quantity reaches
-        // refine_tol; from then on (or once the phase stops improving) the FP32
-        // kernel refines.  refine_tol = 0 keeps a problem in the phase.
-        if (crit < A.refine_tol || !(crit == crit)) {
-          A.lowp[p] = 0;
-          A.lowp_span[2 * p + 1] = t_now + 1;
-          if (A.fp32_live) atomicAdd(A.fp32_live, 1);  // back to the FP32 applies
-        } else if (crit < 0.9 * A.lowp_best[p]) {
-          A.lowp_best[p] = crit;
-          A.lowp_best_t[p] = t_now;
-        } else if (A.refine_tol > 0.0 && t_now - A.lowp_best_t[p] > kLowpStall) {
-          A.lowp[p] = 0;
-          A.lowp_span[2 * p + 1] = t_now + 1;
-          if (A.fp32_live) atomicAdd(A.fp32_live, 1);
-        }
-      } else if (A.retire && (crit < A.ptol[p] || t_now + 1 >= A.deadline[p])) {
-        A.done[p] = 1;
-        A.done_at[p] = t_now + 1;
-        if (A.fp32_live) atomicSub(A.fp32_live, 1);  // retired: no FP32 apply any more
-      }
-      A.node_count[p] = 0;
-      const int nslot = (int)((t_now + 1) % kResidRing);
-      A.res_sum[nslot * A.nprob + p] = 0.0;
-      A.res_max[nslot * A.nprob + p] = 0ull;
+      problem_after_update(A, p, P, t_now, rs, rm);
     }
   }
 }

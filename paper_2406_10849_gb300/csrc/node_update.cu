@@ -67,6 +67,48 @@ __global__ void __launch_bounds__(kNodeThreads, 4) node_update_fixed_kernel(Node
   node_launch_done(A);
 }
 
+// Deferred bookkeeping of one colour's node update, one warp per problem: each
+// owned directed edge's stopping term (summed into resid_acc by the chunks),
+// Z_j of the free nodes from their chunks' pieces, the problem's stopping
+// quantity of iterate t_now, phase control and retirement; the last CTA
+// advances the half-step counter.  The same arithmetic as the last-arrival
+// path of node_chunk_item, run after the chunks' launch instead of on their
+// way out: a chunk then leaves with no fence and no atomic it waits for.
+constexpr int kFinishWarps = 8;
+__global__ void __launch_bounds__(32 * kFinishWarps) node_finish_kernel(NodeArgs A, FinishList L) {
+  const int lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kFinishWarps + (threadIdx.x >> 5);
+  const int64_t t_now = *((volatile const int64_t*)A.hs);
+  if (p < A.nprob && A.done[p] == 0) {
+    const ProbD P = A.probs[p];
+    if (P.nodes_in_colour[A.colour] > 0) {
+      double nsum = 0.0, nmax = 0.0;
+      for (int i = L.dbeg[p] + lane; i < L.dbeg[p + 1]; i += 32) {
+        const int di = L.dedges[i];
+        const double r = A.resid_acc[di];
+        A.resid_acc[di] = 0.0;  // for the next launch
+        A.resid_dedge[di] = r;
+        nsum += r;
+        nmax = fmax(nmax, r);
+      }
+      for (int i = L.nbeg[p]; i < L.nbeg[p + 1]; ++i) {  // warp-uniform
+        const int node = L.nodes[i];
+        finish_free_node_warp(A, node, A.nodes[node], lane);
+      }
+      nsum = warp_sum_d(nsum);
+      nmax = warp_max_d(nmax);
+      if (lane == 0) {
+        const int slot = (int)(t_now % kResidRing);
+        A.res_sum[slot * A.nprob + p] = nsum;
+        A.res_max[slot * A.nprob + p] = (unsigned long long)__double_as_longlong(nmax);
+        problem_after_update(A, p, P, t_now, nsum, nmax);
+      }
+    }
+  }
+  __syncthreads();
+  node_launch_done(A);
+}
+
 // stored potentials of an FP32 handle from the operand the node update keeps:
 // f' = eps ln2 (hh + hl) on a free owner, eps ln2 ((hh + hl) - log2 mu) on a
 // fixed one (points with mu = 0 keep the f the update wrote).  One CTA per
@@ -126,6 +168,13 @@ cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cu
   }
   void* args[] = {const_cast<NodeArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(a.nchunks), dim3(kNodeThreads), args, a.smem, s);
+}
+
+cudaError_t launch_node_finish(const NodeArgs& a, const FinishList& l, cudaStream_t s) {
+  if (a.nprob <= 0) return cudaSuccess;
+  const int grid = (a.nprob + kFinishWarps - 1) / kFinishWarps;
+  node_finish_kernel<<<grid, 32 * kFinishWarps, 0, s>>>(a, l);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_materialise_f(const DEdgeD* dedges, int32_t ndedges, const NodeD* nodes, const ProbD* probs,

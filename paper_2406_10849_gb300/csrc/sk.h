@@ -39,9 +39,10 @@ constexpr float kSkFixBelow = 1.2621774e-29f;  // 2^-96
 // one column of a group: a directed edge of one colour
 struct SkCol {
   int64_t h_off;     // its operand (hh, hl of the reverse directed edge), length ny
-  int64_t part_off;  // its partial: part32[part_off + x] (piece 0; the node update
-                     // merges that piece alone for a problem in the phase)
+  int64_t part_off;  // its partial: part32[part_off + x] (piece 0), written by the
+                     // exact fix-up for the outputs it recomputes
   int32_t prob;
+  int32_t dedge;     // the directed edge whose message the column is
 };
 
 struct SkArgs {
@@ -65,6 +66,7 @@ struct SkArgs {
   __nv_bfloat16* vhi;     // [ncols][kd]
   __nv_bfloat16* vlo;
   float2* part32;
+  float* sout;            // [ncols][nx] sums S(x, j) (-1: listed for the fix-up, which writes part32)
   int32_t* fix_count;     // outputs listed for the exact fix-up (reset by the envelope launch)
   int2* fix_list;         // (x, column), capacity nx * ncols
   int32_t* err;           // error word: bit 1 = a bounded wait of the tcgen05 product ran out

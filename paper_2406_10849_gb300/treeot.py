@@ -272,7 +272,7 @@ class _Marshalled:
 def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, check_every=32, use_graph=True,
             apply_mode="auto", refine_tol=None, absorb_tau=None, lowp_start=None, autotune=None,
             dense_kernel="auto", exact_dist=False, transpose=True, test_stall=False, sk_product="auto",
-            persistent=False) -> Options:
+            persistent=False, node_finish="auto") -> Options:
     """tree_ot_options with the defaults of tree_ot_default_options; dense_kernel picks the
     stored-cost apply ("auto": the autotuner's choice, "tma": bulk-copy staged, "ldg": plain loads);
     exact_dist: recompute squared distances exactly from the first half-step;
@@ -281,7 +281,9 @@ def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, c
     persistent: allow the persistent forest launch (TREE_OT_OPT_PERSISTENT; kept only where the
     create-time timing finds it faster);
     sk_product: the shared-kernel BF16 phase's product ("auto": tcgen05 where available,
-    "mma": the legacy mma.sync kernel)."""
+    "mma": the legacy mma.sync kernel);
+    node_finish: where the node update's bookkeeping runs ("auto": by chunk count per colour,
+    "defer": an extra launch after the chunks, "arrive": the last-arriving chunk)."""
     load()
     o = Options()
     _lib.tree_ot_default_options(C.byref(o))
@@ -301,7 +303,8 @@ def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, c
     if autotune is not None:
         o.autotune = 1 if autotune else 0
     o.flags = ({"auto": 0, "tma": 1, "ldg": 2}[dense_kernel] | (4 if exact_dist else 0) | (0 if transpose else 8)
-               | (16 if test_stall else 0) | {"auto": 0, "mma": 32}[sk_product] | (64 if persistent else 0))
+               | (16 if test_stall else 0) | {"auto": 0, "mma": 32}[sk_product] | (64 if persistent else 0)
+               | {"auto": 0, "defer": 128, "arrive": 256}[node_finish])
     return o
 
 
@@ -493,12 +496,12 @@ class Solver:
             self.set_potential(prob, 2 * e + 1, f[(int(b), int(a))])
 
     def plan_stats(self) -> dict:
-        st = (C.c_int64 * 14)()
-        _check(_lib.tree_ot_plan_stats(self.h, st, 14))
+        st = (C.c_int64 * 15)()
+        _check(_lib.tree_ot_plan_stats(self.h, st, 15))
         keys = ["directed_edges", "edges", "elements_per_half_step", "matrix_bytes_per_half_step",
                 "apply_tasks_c0", "apply_tasks_c1", "device_bytes", "node_ctas_c0", "node_ctas_c1",
                 "recompute_output_block", "recompute_ctas_per_sm", "recompute_variant", "dense_tma",
-                "persistent"]
+                "persistent", "node_defer"]
         return dict(zip(keys, [int(x) for x in st]))
 
 

@@ -129,3 +129,17 @@ def test_tensor_memory_product_matches_mma_sync(T):
             got[prod] = [s.potentials(i) for i in (0, 17, 39)]
     for a, b, i in zip(got["auto"], got["mma"], (0, 17, 39)):
         assert rel_err(a, b, probs[i].eps) <= 1e-5
+
+
+def test_large_support_two_pass_envelope(T):
+    """Supports above 1024 points (33 x 33 = 1089) take the two-pass envelope
+    kernel (the one-pass kernel holds at most 1024 points per CTA in registers):
+    three stars follow the oracle for three half-steps in the phase."""
+    probs = stars(3, side=33, eps=0.01, seed=7_500_000)
+    with T.Solver(probs, T.options(apply_mode="bf16", lowp_start=0, refine_tol=0.0)) as s:
+        s.half_steps(3)
+        got = {i: s.potentials(i) for i in (0, 2)}
+    for i, f in got.items():
+        ref = O.run_half_steps(probs[i], 3)
+        assert rel_err(f, ref, probs[i].eps) <= 1e-4
+        assert marginal_gap(probs[i], f, ref) <= 1e-5
