@@ -279,6 +279,7 @@ struct tree_ot_handle {
   int32_t* d_live = nullptr;               // problems the FP32 applies process (see ApplyArgs::fp32_live)
   int32_t nfixed_chunks[2] = {0, 0};       // per colour: its first chunks belong to fixed nodes
   bool node_defer[2] = {false, false};     // per colour: bookkeeping in node_finish_kernel
+  int32_t chunk_pairs[2] = {0, 0};         // per colour: (edge, point) pairs per node-update chunk
   SkRefD* d_skref = nullptr;               // per directed edge: its shared-kernel product's output
   int32_t* d_fin[2] = {nullptr, nullptr};  // per colour: the FinishList arrays, one allocation
   FinishList fin[2] = {};
@@ -591,16 +592,23 @@ int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
   const bool defer = h->node_defer[colour];
   a.defer = defer ? 1 : 0;
   cudaError_t e = cudaSuccess;
-  if (nf > 0) {  // fixed nodes' chunks first, with the kernel that has no free-node path
+  // The kernel without the free-node path takes the fixed nodes' chunks (listed
+  // first) when they fill the GPU on their own, or when there is nothing else;
+  // otherwise one launch takes every chunk (two half-empty launches back to
+  // back cost more than the leaner kernel saves).
+  const bool all_fixed = nf > 0 && nf == nall;
+  const bool split = nf > 0 && nf < nall && nf >= 4 * h->sms;
+  if (split) {
     a.nchunks = nf;
-    a.count_launch = (nf == nall && !defer) ? 1 : 0;
+    a.count_launch = 0;
     e = launch_node_update(a, h->fp64, true, s);
   }
-  if (e == cudaSuccess && nall > nf) {
-    a.chunks = h->d_chunks[colour] + nf;
-    a.nchunks = nall - nf;
+  if (e == cudaSuccess && nall > 0) {
+    const int32_t first = split ? nf : 0;
+    a.chunks = h->d_chunks[colour] + first;
+    a.nchunks = nall - first;
     a.count_launch = defer ? 0 : 1;
-    e = launch_node_update(a, h->fp64, false, s);
+    e = launch_node_update(a, h->fp64, all_fixed, s);
   }
   if (e == cudaSuccess && defer) {  // the bookkeeping; its last CTA advances the half-step counter
     a.count_launch = 1;
@@ -1540,12 +1548,6 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       node_off += align_up(nd.n, 32);
       nd.coord_off = have_coords ? coord_off : -1;
       if (have_coords) coord_off += align_up((int64_t)nd.n * pd.dim, 4);
-      {
-        const int32_t cp = node_chunk_points(nd.n, nd.deg);
-        nd.nchunks = (nd.n + cp - 1) / cp;
-      }
-      nd.chunk_base = chunk_base;
-      chunk_base += nd.nchunks;
       pd.nodes_in_colour[nd.colour] += 1;
       h->nodes.push_back(nd);
       owned_by.emplace_back();
@@ -1601,6 +1603,24 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
   h->node_len = node_off;
   h->coord_len = coord_off;
   h->part_len = part_off;
+  // node-update chunks: kNodePairs (edge, point) pairs per CTA where a colour has
+  // many of them (fewer CTAs, each CTA's metadata loads amortised over more
+  // pairs), kNodePairsSmall where its pairs fill few waves of CTAs anyway
+  {
+    int64_t pairs[2] = {0, 0};
+    for (const NodeD& nd : h->nodes) pairs[nd.colour] += (int64_t)nd.n * std::max(nd.deg, 1);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (int c = 0; c < 2; ++c)
+      h->chunk_pairs[c] = pairs[c] > (int64_t)kNodePairsSmall * 8 * nsm ? kNodePairs : kNodePairsSmall;
+    for (NodeD& nd : h->nodes) {
+      const int32_t cp = node_chunk_points(nd.n, nd.deg, h->chunk_pairs[nd.colour]);
+      nd.nchunks = (nd.n + cp - 1) / cp;
+      nd.chunk_base = chunk_base;
+      chunk_base += nd.nchunks;
+    }
+  }
   h->nzchunks = chunk_base;
 
   // device task arrays are sized for the finest output blocking the autotuner may pick
@@ -1649,7 +1669,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     for (size_t j = 0; j < h->nodes.size(); ++j) {
       const NodeD& nd = h->nodes[j];
       if ((pass == 0) != (nd.fixed != 0)) continue;
-      const int32_t cp = node_chunk_points(nd.n, nd.deg);
+      const int32_t cp = node_chunk_points(nd.n, nd.deg, h->chunk_pairs[nd.colour]);
       for (int32_t c = 0; c < nd.nchunks; ++c)
         h->chunks[nd.colour].push_back(NodeChunk{(int32_t)j, c, c * cp, std::min(cp, nd.n - c * cp)});
       if (pass == 0) h->nfixed_chunks[nd.colour] += nd.nchunks;

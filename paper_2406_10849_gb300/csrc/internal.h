@@ -26,7 +26,14 @@ constexpr int kColRows = 512;          // COL task: rows per task (8 warps x 64)
 constexpr int kRecOut = 1024;          // RECOMP task: outputs per task (256 threads x 4)
 constexpr int kRecRed = 512;           // RECOMP task: reduction points per task
 constexpr int kNodeThreads = 256;
-constexpr int kNodePairs = 1024;       // node update: (owned edge, point) pairs per CTA
+// node update: (owned edge, point) pairs per CTA.  Larger chunks amortise a
+// CTA's dependent metadata loads over more pairs: on 2000 stars the node update
+// took 0.347 / 0.297 / 0.274 ms per half-step at 1024 / 2048 / 4096 pairs, on
+// the 512 batched trees 0.363 / 0.325 / 0.329 ms; but a colour with few pairs
+// (the 64-node tree: 32 leaves of 4096 points) needs the smaller chunks to
+// fill the GPU at all (its node update took 0.106 against 0.045 ms).
+constexpr int kNodePairs = 4096;
+constexpr int kNodePairsSmall = 1024;
 constexpr int kBfCols = 256;           // BF16 COL task: columns per task (32 lanes x 8)
 constexpr int kBfRowTask = 256;        // BF16 ROW task: rows per task
 constexpr double kGrid = 1024.0;       // apply operands and frames live on a 2^-10 grid
@@ -76,10 +83,10 @@ struct NodeChunk {
 };
 
 // Node update: points per CTA for a node of n points and degree deg, so that a
-// CTA holds at most kNodePairs (edge, point) pairs (a multiple of 32 points
-// when that is at least 32, and at least one point).
-inline int32_t node_chunk_points(int32_t n, int32_t deg) {
-  int32_t c = kNodePairs / (deg > 0 ? deg : 1);
+// CTA holds at most `pairs` (edge, point) pairs (a multiple of 32 points when
+// that is at least 32, and at least one point).
+inline int32_t node_chunk_points(int32_t n, int32_t deg, int32_t pairs) {
+  int32_t c = pairs / (deg > 0 ? deg : 1);
   if (c >= 32) c &= ~31;
   if (c < 1) c = 1;
   return c < n ? c : n;

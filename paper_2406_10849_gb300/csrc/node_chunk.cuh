@@ -410,9 +410,8 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   }
   __syncthreads();
   bool bad = false;
-  // a thread loads all its pairs of a pass before it stores anything (at most
-  // kIt pairs per thread, as a chunk holds at most kNodePairs pairs)
-  constexpr int kIt = kNodePairs / kNodeThreads;
+  // a thread loads a batch of kIt pairs before it stores anything
+  constexpr int kIt = 4;
 
   if (FIXED_ONLY || nd.fixed) {  // a leaf: one edge, one pass
     // the fixed-leaf kernel batches two pairs per thread (fewer live registers, more CTAs per SM)
