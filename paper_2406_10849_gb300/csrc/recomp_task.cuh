@@ -16,6 +16,10 @@ namespace {
 
 #define kInf (__int_as_float(0x7f800000))
 constexpr float kWindow = 12.f;   // a frame up to this far above the chunk maximum is kept
+// The plain recomputed-cost apply moves a frame (see recomp_task):
+constexpr float kWindowRec = 64.f;  //   down, for a fresh output, only when the chunk lies this far below it,
+constexpr float kRoomRec = 32.f;    //   and then to this far above the chunk's maximum;
+constexpr float kShiftRec = 2.f;    //   up by at most this much by shifting the chunk's terms
 constexpr int kRecPts = 4;        // RECOMP: reduction points per frame check (per thread: 4 outputs x 4)
 
 
@@ -171,16 +175,33 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
 #pragma unroll
         for (int jj = 2; jj < kRecPts; jj += 2) cmk[k] = max3f(cmk[k], tv[k][jj], tv[k][jj + 1]);
       }
-      // one test for the four outputs in the common case (frames fit, sums started)
+      // one test for the four outputs in the common case (frames fit, sums started).
+      // A frame moves up when a term exceeds it by more than 0.5, and down (before
+      // anything is summed) when the chunk's terms all lie more than kWindowRec
+      // below it; a term at t below its frame carries a rounding error of about
+      // |t| 2^-24 but weighs 2^t, so terms far below their frame cost no
+      // accuracy.  Moving down, the frame stops kRoomRec above the chunk's
+      // maximum (later, larger terms then rarely move it up again), and the terms
+      // shift with it: t - d is exact there (|t - d| < |t|, d on the 2^-10 grid).
+      // Moving up by at most kShiftRec the terms shift too: the largest, now near
+      // 0, keeps the rounding error of |t| <= 2 (at most 2^-23).  A larger move
+      // up recomputes the chunk's terms from the moved frame.
       const bool fresh = (acc[0] == 0.f) | (acc[1] == 0.f) | (acc[2] == 0.f) | (acc[3] == 0.f);
       if (fresh || fmaxf(max3f(cmk[0], cmk[1], cmk[2]), cmk[3]) > 0.5f) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float cm = cmk[k];
-          if ((cm > 0.5f || (acc[k] == 0.f && cm < -kWindow)) && cm > -kInf) {
-            const float Rn = R[k] + quant(cm);
+          const bool up = cm > 0.5f, down = acc[k] == 0.f && cm < -kWindowRec;
+          if ((up || down) && cm > -kInf) {
+            const float dlt = down ? quant(cm) + kRoomRec : quant(cm);
+            const float Rn = R[k] + dlt;
             acc[k] = acc[k] == 0.f ? 0.f : acc[k] * ex2(R[k] - Rn);
             R[k] = Rn;
+            if (!up || cm <= kShiftRec) {
+#pragma unroll
+              for (int jj = 0; jj < kRecPts; ++jj) tv[k][jj] -= dlt;
+              continue;
+            }
             const float pxk = k == 0 ? px01.x : k == 1 ? px01.y : k == 2 ? px23.x : px23.y;
             const float pyk = k == 0 ? py01.x : k == 1 ? py01.y : k == 2 ? py23.x : py23.y;
             const float pzk = k == 0 ? pz01.x : k == 1 ? pz01.y : k == 2 ? pz23.x : pz23.y;
