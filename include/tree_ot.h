@@ -492,6 +492,76 @@ int tree_ot_mlp_train_step(tree_ot_mlp *m, void *cuda_stream, const float *x, co
                            double lr, double *loss);
 const char *tree_ot_mlp_last_error(void);
 
+/* ---- General graphs: coupled MOT on a modified junction tree ------------
+ * Sec. 4 (def:jt_general, problem eq:ot_graph_local_reg, Assumption
+ * ass:inclusion, prop:local_reg_dual and the separator update of
+ * prop:general_algo).  Variables 0 .. num_vars-1 with support sizes
+ * var_size[v].  Cost clique c has the variables
+ * clique_vars[clique_var_begin[c] .. clique_var_begin[c+1]) (the axis order of
+ * its cost tensor) and a dense FP32 cost tensor clique_cost[c] (host memory,
+ * row-major, the last variable fastest; copied at create; +inf allowed, NaN
+ * and -inf rejected).  Separator s has the variables
+ * sep_vars[sep_var_begin[s] .. ), its neighbour cliques
+ * sep_cliques[sep_clique_begin[s] .. ) in the order of its inclusion sequence
+ * (the intersections with the first two cliques equal, the rest nested), and
+ * optionally a constraint: the variables sep_gamma[sep_gamma_begin[s] .. )
+ * (inside the smallest intersection; none: unconstrained) with the marginal
+ * sep_mu[s] (host FP64, row-major over the constraint's variables; NULL when
+ * unconstrained).  Every clique must join exactly two separators, and the
+ * separators must two-colour through the cliques (TREE_OT_ERR_NOT_TREE
+ * otherwise).  A clique holds at most 8 variables.
+ * The dual variable u^s_i lives on s n c_i (variables in the separator's
+ * order); a half-step updates every separator of one colour (separator 0's
+ * colour first), all on the device in FP64 log domain.  The stopping quantity
+ * (the paper defines none for Sec. 4; this reading): per separator, the L1
+ * distances between the marginals on s n c_i of clique c_i's plan and of clique
+ * c_1's, i >= 2, plus the distance of c_1's marginal on the constraint from
+ * mu (or |mass - 1| unconstrained); its sum and largest term. */
+typedef struct tree_ot_jt_problem {
+    int32_t num_vars;
+    const int32_t *var_size;          /* [num_vars]                                  */
+    int32_t num_cliques;
+    const int32_t *clique_var_begin;  /* [num_cliques + 1]                           */
+    const int32_t *clique_vars;
+    const float *const *clique_cost;  /* [num_cliques] host pointers                 */
+    int32_t num_seps;
+    const int32_t *sep_var_begin;     /* [num_seps + 1]                              */
+    const int32_t *sep_vars;
+    const int32_t *sep_clique_begin;  /* [num_seps + 1]                              */
+    const int32_t *sep_cliques;
+    const int32_t *sep_gamma_begin;   /* [num_seps + 1]                              */
+    const int32_t *sep_gamma;
+    const double *const *sep_mu;      /* [num_seps] host pointers or NULL            */
+    double eps;
+} tree_ot_jt_problem;
+
+typedef struct tree_ot_jt_handle tree_ot_jt_handle;
+
+/* Validates, plans the half-steps and uploads costs and marginals; u = 1. */
+int tree_ot_jt_create(const tree_ot_jt_problem *prob, void *cuda_stream, tree_ot_jt_handle **out);
+int tree_ot_jt_destroy(tree_ot_jt_handle *h);
+/* u = 1 again */
+int tree_ot_jt_reset(tree_ot_jt_handle *h, void *cuda_stream);
+/* T half-steps, colours alternating (prop:general_algo per separator) */
+int tree_ot_jt_half_steps(tree_ot_jt_handle *h, void *cuda_stream, int64_t T);
+/* the stopping quantity of the current iterate: its sum and largest term */
+int tree_ot_jt_residual(tree_ot_jt_handle *h, void *cuda_stream, double *sum, double *max);
+/* half-steps in groups of check_every until the stopping quantity (tol_kind
+ * TREE_OT_TOL_SUM or _MAX) is below tol or max_half_steps are done; returns
+ * TREE_OT_OK or TREE_OT_NOT_CONVERGED, the half-steps done and the quantity */
+int tree_ot_jt_solve(tree_ot_jt_handle *h, void *cuda_stream, double tol, int32_t tol_kind, int64_t max_half_steps,
+                     int32_t check_every, int64_t *half_steps, double *residual);
+/* clique c's plan B_c (prop:local_reg_dual) into host memory, in the axis
+ * order of its cost tensor */
+int tree_ot_jt_plan(tree_ot_jt_handle *h, void *cuda_stream, int32_t clique, double *plan);
+/* sum_c <C_c, B_c> */
+int tree_ot_jt_transport_cost(tree_ot_jt_handle *h, void *cuda_stream, double *cost);
+/* log u^s_i (s = sep, i = pos in its clique list) into host memory, over
+ * s n c_i in the separator's variable order */
+int tree_ot_jt_get_dual(tree_ot_jt_handle *h, void *cuda_stream, int32_t sep, int32_t pos, double *log_u);
+/* the two-colouring: colour[s] for every separator (host) */
+int tree_ot_jt_colour(tree_ot_jt_handle *h, int32_t *colour);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtreeot.so")
 SOURCES = ["api.cpp", "mlp_api.cpp", "apply_f32.cu", "apply_bf16.cu", "apply_tma.cu", "apply_sk.cu", "apply_f64.cu",
            "node_update.cu",
-           "check.cu", "round.cu", "mlp.cu", "forest.cu", "forest_d1.cu", "forest_d2.cu", "forest_d3.cu"]
+           "check.cu", "round.cu", "mlp.cu", "forest.cu", "forest_d1.cu", "forest_d2.cu", "forest_d3.cu",
+           "junction.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-Xcompiler", "-pthread",
          f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]

@@ -166,6 +166,9 @@ int validate_problem(const tree_ot_problem* p, std::vector<std::vector<int32_t>>
 
 }  // namespace
 
+void treeot::set_last_error(const std::string& msg) { g_err = msg; }
+
+
 // ---------------------------------------------------------------------------
 // the handle
 // ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 // owner has colour c (edge apply), then applies those updates at the owners
 // (node update).
 #pragma once
+#include <string>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -324,6 +325,9 @@ cudaError_t launch_apply_tma(const ApplyArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_apply_f64(const ApplyArgs& a, int grid, cudaStream_t s);
 // fixed_only: every chunk of the launch belongs to a fixed node (a kernel without
 // the free-node path, so more CTAs fit on an SM)
+// the message tree_ot_last_error returns (thread-local; api.cpp)
+void set_last_error(const std::string& msg);
+
 cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cudaStream_t s);
 // the deferred bookkeeping of a node update of one colour (one warp per problem)
 cudaError_t launch_node_finish(const NodeArgs& a, const FinishList& l, cudaStream_t s);

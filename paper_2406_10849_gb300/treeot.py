@@ -150,6 +150,17 @@ SIGNATURES = {
                                          C.POINTER(C.c_double)]),
     "tree_ot_mlp_last_error": (C.c_char_p, []),
     "tree_ot_mlp_set_input_log": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double]),
+    "tree_ot_jt_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "tree_ot_jt_destroy": (C.c_int, [C.c_void_p]),
+    "tree_ot_jt_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tree_ot_jt_half_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "tree_ot_jt_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "tree_ot_jt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int64, C.c_int32,
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "tree_ot_jt_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_jt_transport_cost": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "tree_ot_jt_get_dual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "tree_ot_jt_colour": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
 }
 
 _lib = None
@@ -607,3 +618,128 @@ class MLP:
                                             C.c_void_p(target.data_ptr()), int(x.shape[0]), float(lr),
                                             C.byref(loss)))
         return float(loss.value)
+
+
+# ---- general graphs: modified junction trees (tree_ot_jt_*) ----------------
+
+class JtProblem(C.Structure):
+    _fields_ = [
+        ("num_vars", C.c_int32),
+        ("var_size", C.POINTER(C.c_int32)),
+        ("num_cliques", C.c_int32),
+        ("clique_var_begin", C.POINTER(C.c_int32)),
+        ("clique_vars", C.POINTER(C.c_int32)),
+        ("clique_cost", C.POINTER(C.POINTER(C.c_float))),
+        ("num_seps", C.c_int32),
+        ("sep_var_begin", C.POINTER(C.c_int32)),
+        ("sep_vars", C.POINTER(C.c_int32)),
+        ("sep_clique_begin", C.POINTER(C.c_int32)),
+        ("sep_cliques", C.POINTER(C.c_int32)),
+        ("sep_gamma_begin", C.POINTER(C.c_int32)),
+        ("sep_gamma", C.POINTER(C.c_int32)),
+        ("sep_mu", C.POINTER(C.POINTER(C.c_double))),
+        ("eps", C.c_double),
+    ]
+
+
+def _flat(lists):
+    begin = np.zeros(len(lists) + 1, np.int32)
+    for i, l in enumerate(lists):
+        begin[i + 1] = begin[i] + len(l)
+    items = np.array([int(x) for l in lists for x in l] or [0], np.int32)
+    return begin, items
+
+
+class JunctionSolver:
+    """One handle over a modified junction tree (tree_ot_jt_create .. tree_ot_jt_destroy).
+    ``jt`` carries d (support size per variable), clique_vars, clique_costs (arrays with
+    axes in the clique's variable order), sep_vars, sep_cliques (inclusion order),
+    sep_gamma (None or the constraint's variables), sep_mu and eps."""
+
+    def __init__(self, jt, stream=None):
+        load()
+        self.jt = jt
+        self.stream = stream
+        keep = []
+        d = np.ascontiguousarray(np.asarray(jt.d, np.int32))
+        cb, cv = _flat(jt.clique_vars)
+        sb, sv = _flat(jt.sep_vars)
+        kb, kc = _flat(jt.sep_cliques)
+        gb, gv = _flat([g if g is not None else () for g in jt.sep_gamma])
+        costs = [np.ascontiguousarray(np.asarray(c, np.float32)).reshape(-1) for c in jt.clique_costs]
+        mus = [None if g is None else np.ascontiguousarray(np.asarray(m, np.float64)).reshape(-1)
+               for g, m in zip(jt.sep_gamma, jt.sep_mu)]
+        keep += [d, cb, cv, sb, sv, kb, kc, gb, gv] + costs + [m for m in mus if m is not None]
+        cost_ptrs = (C.POINTER(C.c_float) * len(costs))(*[c.ctypes.data_as(C.POINTER(C.c_float)) for c in costs])
+        mu_ptrs = (C.POINTER(C.c_double) * len(mus))(
+            *[m.ctypes.data_as(C.POINTER(C.c_double)) if m is not None else C.POINTER(C.c_double)() for m in mus])
+        keep += [cost_ptrs, mu_ptrs]
+        i32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        self.struct = JtProblem(len(d), i32(d), len(costs), i32(cb), i32(cv), cost_ptrs, len(jt.sep_vars), i32(sb),
+                                i32(sv), i32(kb), i32(kc), i32(gb), i32(gv), mu_ptrs, float(jt.eps))
+        self._keep = keep
+        h = C.c_void_p()
+        _check(_lib.tree_ot_jt_create(C.byref(self.struct), C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+
+    def _s(self):
+        return C.c_void_p(_stream_ptr(self.stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tree_ot_jt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        _check(_lib.tree_ot_jt_reset(self.h, self._s()))
+
+    def half_steps(self, T: int):
+        _check(_lib.tree_ot_jt_half_steps(self.h, self._s(), int(T)))
+
+    def residual(self):
+        s, m = C.c_double(), C.c_double()
+        _check(_lib.tree_ot_jt_residual(self.h, self._s(), C.byref(s), C.byref(m)))
+        return s.value, m.value
+
+    def solve(self, tol: float, tol_kind: str = "sum", max_half_steps: int = 100000, check_every: int = 16):
+        hs, r = C.c_int64(), C.c_double()
+        rc = _check(_lib.tree_ot_jt_solve(self.h, self._s(), float(tol), TOL_KIND[tol_kind], int(max_half_steps),
+                                          int(check_every), C.byref(hs), C.byref(r)), allow=(OK, NOT_CONVERGED))
+        return rc, int(hs.value), r.value
+
+    def plan(self, clique: int) -> np.ndarray:
+        shape = tuple(int(self.jt.d[v]) for v in self.jt.clique_vars[clique])
+        out = np.zeros(int(np.prod(shape)), np.float64)
+        _check(_lib.tree_ot_jt_plan(self.h, self._s(), int(clique), out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(shape)
+
+    def transport_cost(self) -> float:
+        v = C.c_double()
+        _check(_lib.tree_ot_jt_transport_cost(self.h, self._s(), C.byref(v)))
+        return v.value
+
+    def dual(self, sep: int, pos: int) -> np.ndarray:
+        c = self.jt.sep_cliques[sep][pos]
+        vars_ = [v for v in self.jt.sep_vars[sep] if v in self.jt.clique_vars[c]]
+        shape = tuple(int(self.jt.d[v]) for v in vars_)
+        out = np.zeros(int(np.prod(shape)) if shape else 1, np.float64)
+        _check(_lib.tree_ot_jt_get_dual(self.h, self._s(), int(sep), int(pos),
+                                        out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(shape) if shape else out[0]
+
+    def colours(self) -> np.ndarray:
+        out = np.zeros(len(self.jt.sep_vars), np.int32)
+        _check(_lib.tree_ot_jt_colour(self.h, out.ctypes.data_as(C.POINTER(C.c_int32))))
+        return out

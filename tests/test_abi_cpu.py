@@ -102,3 +102,40 @@ def test_disconnected_and_self_loop(T):
     assert T.validate(p) == -2
     p.edges = np.array([[0, 1], [0, 1], [2, 3]], np.int32)
     assert T.validate(p) == -2
+
+
+def test_junction_tree_structure_checks_on_host(T):
+    """tree_ot_jt_create checks def:jt_general and ass:inclusion on the host before
+    any device call: broken structures are refused with their codes."""
+    from paper_2406_10849_gb300.treeot import JunctionSolver, TreeOTError
+
+    def code_of(jt):
+        try:
+            JunctionSolver(jt).close()
+        except TreeOTError as e:
+            return e.kind
+        return "OK"
+
+    bad = gen.nested_junction_tree(9000, d=2)
+    bad.sep_cliques = [[2, 0, 1], [0], [1], [2]]        # first two intersections differ
+    assert code_of(bad) == "NOT_TREE"
+    bad = gen.nested_junction_tree(9000, d=2)
+    bad.sep_gamma = list(bad.sep_gamma)
+    bad.sep_gamma[0] = (4,)                              # constraint outside the smallest intersection
+    bad.sep_mu = list(bad.sep_mu)
+    assert code_of(bad) == "NOT_TREE"
+    bad = gen.nested_junction_tree(9000, d=2)
+    bad.sep_cliques = [[0, 1, 2], [0], [1], [1]]         # clique 1 joins three separators, clique 2 one
+    assert code_of(bad) == "NOT_TREE"
+    bad = gen.nested_junction_tree(9000, d=2)
+    bad.sep_mu = list(bad.sep_mu)
+    bad.sep_mu[2] = np.asarray(bad.sep_mu[2]) * 0.5     # not a probability vector
+    assert code_of(bad) == "MARGINAL"
+    bad = gen.nested_junction_tree(9000, d=2)
+    bad.eps = 0.0
+    assert code_of(bad) == "EPS"
+    bad = gen.nested_junction_tree(9000, d=2)
+    bad.clique_costs = list(bad.clique_costs)
+    bad.clique_costs[1] = np.array(bad.clique_costs[1], dtype=np.float64)
+    bad.clique_costs[1].reshape(-1)[0] = np.nan
+    assert code_of(bad) == "NONFINITE"
