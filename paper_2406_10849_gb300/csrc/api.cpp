@@ -1222,7 +1222,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
     const ProbD& pd = h->probs[g.prob_rep];
     const int32_t mp = (int32_t)align_up(own.n, kSkTileM), kd = (int32_t)align_up(nbn.n, kSkPadK);
     const int64_t maxc = (int64_t)std::max(g.cols[0].size(), g.cols[1].size());
-    float *b = nullptr, *rf = nullptr, *cmax = nullptr, *sout = nullptr;
+    float *b = nullptr, *rf = nullptr, *cmax = nullptr, *sout = nullptr, *benv = nullptr;
     __nv_bfloat16 *khi = nullptr, *klo = nullptr, *vhi = nullptr, *vlo = nullptr;
     SkCol* dc[2] = {nullptr, nullptr};
     int32_t* fix_count = nullptr;
@@ -1231,6 +1231,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
         (rc = h->alloc(&khi, (int64_t)mp * kd)) ||
         (rc = h->alloc(&klo, (int64_t)mp * kd)) || (rc = h->alloc(&vhi, maxc * kd)) ||
         (rc = h->alloc(&vlo, maxc * kd)) || (rc = h->alloc(&sout, maxc * own.n)) ||
+        (rc = h->alloc(&benv, ((maxc + kSkEnvCols - 1) / kSkEnvCols) * kd)) ||
         (rc = h->alloc(&dc[0], (int64_t)g.cols[0].size())) ||
         (rc = h->alloc(&dc[1], (int64_t)g.cols[1].size())) || (rc = h->alloc(&fix_count, 1)) ||
         (rc = h->alloc(&fix_list, (int64_t)own.n * maxc)))
@@ -1257,6 +1258,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       a.s_hi = pd.s2_scaled;
       a.s_lo = pd.s2_scaled_lo;
       a.b = b;
+      a.benv = benv;
       a.cmax = cmax;
       a.rf = rf;
       a.khi = khi;

@@ -41,7 +41,7 @@ __device__ __forceinline__ void atomic_max_float(float* addr, float v) {
     atomicMin(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
 }
 
-constexpr int kEnvCols = 32;  // columns per envelope CTA
+constexpr int kEnvCols = kSkEnvCols;
 
 // h + l of four consecutive points from a, b (16-byte aligned when y0 + 4 <= n)
 __device__ __forceinline__ void load_sum4(const float* a, const float* b, int y0, int n, float* v) {
@@ -175,9 +175,32 @@ __global__ void __launch_bounds__(256) sk_envelope1_kernel(SkArgs A) {
         for (int q = 0; q < 4; ++q) e[q] = fmaxf(e[q], v[i][q] - M);
     }
   }
+  // this CTA's envelope (the reduction over CTAs follows in sk_envelope_reduce_kernel:
+  // atomics here would meet ~500 times on every point and serialise)
+  float* const part = A.benv + (int64_t)blockIdx.x * A.kd;
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    if (y0 + q < A.ny) atomic_max_float(&A.b[y0 + q], e[q]);
+    if (y0 + q < A.ny) part[y0 + q] = e[q];
+}
+
+// b(y) = the largest of the one-pass kernel's per-CTA envelopes: 32 points per
+// CTA, its eight warps taking every eighth CTA's row
+__global__ void __launch_bounds__(256) sk_envelope_reduce_kernel(SkArgs A, int32_t nblk) {
+  __shared__ float s_m[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.x * 32 + lane;
+  float m = -kInf;
+  if (y < A.ny) {
+#pragma unroll 4
+    for (int p = warp; p < nblk; p += 8) m = fmaxf(m, A.benv[(int64_t)p * A.kd + y]);
+  }
+  s_m[warp][lane] = m;
+  __syncthreads();
+  if (warp == 0 && y < A.ny) {
+#pragma unroll
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, s_m[w][lane]);
+    A.b[y] = m;
+  }
 }
 
 __device__ __forceinline__ float sqdist(const float* p, const float* q, int dim) {
@@ -246,11 +269,13 @@ __global__ void __launch_bounds__(256) sk_kbuild_kernel(SkArgs A) {
   }
 }
 
-// one CTA per column, four consecutive points per thread and pass (the
-// operand's offset is a multiple of 32 points, kd of kSkPadK); inactive
+// one warp per column (eight per CTA), four consecutive points per lane and pass
+// (the operand's offset is a multiple of 32 points, kd of kSkPadK); inactive
 // columns are left alone (their outputs are not stored)
 __global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
-  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= A.ncols) return;
   const SkCol col = A.cols[j];
   const float M = A.cmax[j];
   if (!col_active(A, col) || !(M > -kInf)) return;
@@ -258,7 +283,8 @@ __global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
   __nv_bfloat16* vlo = A.vlo + (int64_t)j * A.kd;
   const float* hh = A.hh + col.h_off;
   const float* hl = A.hl + col.h_off;
-  for (int y0 = 4 * (int)threadIdx.x; y0 < A.kd; y0 += 4 * 256) {
+#pragma unroll 4
+  for (int y0 = 4 * lane; y0 < A.kd; y0 += 4 * 32) {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (y0 + 4 <= A.ny) {
       const float4 h4 = *reinterpret_cast<const float4*>(hh + y0);
@@ -781,12 +807,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
-// one warp per listed output: frame = the largest term on the 2^-10 grid, then
+// one CTA per listed output (eight warps over the reduction points, so an output
+// costs two rounds of loads): frame = the largest term on the 2^-10 grid, then
 // the sum of 2^(term - frame) with the recomputed-cost apply's argument
 __global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
-  const int lane = threadIdx.x & 31;
+  __shared__ float red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nfix = *A.fix_count;
-  for (int w = blockIdx.x * 8 + (threadIdx.x >> 5); w < nfix; w += gridDim.x * 8) {
+  for (int w = blockIdx.x; w < nfix; w += gridDim.x) {  // block-uniform
     const int2 e = A.fix_list[w];
     const int x = e.x;
     const SkCol col = A.cols[e.y];
@@ -796,14 +824,20 @@ __global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
     for (int d = 0; d < A.dim; ++d) p[d] = A.xc[(int64_t)x * A.dim + d];
     float mx = -kInf;
 #pragma unroll 4
-    for (int y = lane; y < A.ny; y += 32)
+    for (int y = threadIdx.x; y < A.ny; y += 256)
       mx = fmaxf(mx, fmaf(-sqdist(p, A.yc + (int64_t)y * A.dim, A.dim), A.s_hi, hh[y]));
     mx = warp_max(mx);
+    __syncthreads();  // red is free (previous output)
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) mx = fmaxf(mx, red[i]);
     float R = 0.f, S = 0.f;
     if (mx > -kInf) {
       R = quant(mx);
 #pragma unroll 4
-      for (int y = lane; y < A.ny; y += 32) {
+      for (int y = threadIdx.x; y < A.ny; y += 256) {
         if (!(hh[y] > -kInf)) continue;
         const float c = sqdist(p, A.yc + (int64_t)y * A.dim, A.dim);
         float t = fmaf(-c, A.s_hi, hh[y] - R);
@@ -811,8 +845,14 @@ __global__ void __launch_bounds__(256) sk_fixup_kernel(SkArgs A) {
         S += ex2(t + hl[y]);
       }
       S = warp_sum(S);
+      __syncthreads();
+      if (lane == 0) red[warp] = S;
+      __syncthreads();
+      S = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) S += red[i];
     }
-    if (lane == 0) A.part32[col.part_off + x] = make_float2(R, S);
+    if (threadIdx.x == 0) A.part32[col.part_off + x] = make_float2(R, S);
   }
 }
 
@@ -892,12 +932,15 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
   if (a.ncols <= 0) return cudaSuccess;
   if (a.use_tc && !maps) return cudaErrorInvalidValue;
   if (!(a.use_tc ? sk_tc_ready() : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
-  if (a.ny <= 4 * 256)
-    sk_envelope1_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
-  else
-    sk_envelope_kernel<<<(a.ncols + kEnvCols - 1) / kEnvCols, 256, 0, s>>>(a);
+  const int nenv = (a.ncols + kEnvCols - 1) / kEnvCols;
+  if (a.ny <= 4 * 256 && a.benv) {
+    sk_envelope1_kernel<<<nenv, 256, 0, s>>>(a);
+    sk_envelope_reduce_kernel<<<(a.ny + 31) / 32, 256, 0, s>>>(a, nenv);
+  } else {
+    sk_envelope_kernel<<<nenv, 256, 0, s>>>(a);
+  }
   sk_kbuild_kernel<<<a.mp, 256, 0, s>>>(a);
-  sk_vbuild_kernel<<<a.ncols, 256, 0, s>>>(a);
+  sk_vbuild_kernel<<<(a.ncols + 7) / 8, 256, 0, s>>>(a);
   if (before_product) cudaEventRecord(before_product, s);
   const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
   if (a.use_tc) {

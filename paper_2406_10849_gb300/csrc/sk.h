@@ -29,6 +29,7 @@ constexpr int kSkTileM = 128;  // rows (x) per GEMM CTA
 constexpr int kSkTileN = 128;  // columns (directed edges) per GEMM CTA
 constexpr int kSkTileK = 32;   // reduction points (y) per stage (mma.sync variant)
 constexpr int kSkPadK = 64;    // reduction length padding (a multiple of both products' stages)
+constexpr int kSkEnvCols = 32;  // columns per envelope CTA (one partial envelope each)
 
 // Outputs whose sum S(x,j) falls below 2^-96 (the column's message more than
 // ~96 binades under the row frame R(x), where its terms' factors may have left
@@ -59,6 +60,7 @@ struct SkArgs {
   const float* yc;        // column (neighbour) support, ny x dim
   float s_hi, s_lo;       // scale log2(e) / eps as a two-float
   float* b;               // [kd] envelope; -inf between uses
+  float* benv;            // [ceil(ncols / kSkEnvCols)][kd] per-CTA envelopes of the one-pass envelope kernel
   float* cmax;            // [ncols] column maxima M_j (-inf: inactive)
   float* rf;              // [mp] row frames R(x)
   __nv_bfloat16* khi;     // [mp][kd]
