@@ -284,6 +284,7 @@ struct tree_ot_handle {
   bool node_defer[2] = {false, false};     // per colour: bookkeeping in node_finish_kernel
   int32_t chunk_pairs[2] = {0, 0};         // per colour: (edge, point) pairs per node-update chunk
   SkRefD* d_skref = nullptr;               // per directed edge: its shared-kernel product's output
+  FixedChunkD* d_fixed[2] = {nullptr, nullptr};  // per colour: records of its fixed-leaf chunks
   int32_t* d_fin[2] = {nullptr, nullptr};  // per colour: the FinishList arrays, one allocation
   FinishList fin[2] = {};
   int persistent = 0;
@@ -604,14 +605,18 @@ int launch_update(tree_ot_handle* h, int colour, bool retire, cudaStream_t s) {
   if (split) {
     a.nchunks = nf;
     a.count_launch = 0;
+    a.fixed = defer ? h->d_fixed[colour] : nullptr;
     e = launch_node_update(a, h->fp64, true, s);
+    a.fixed = nullptr;
   }
   if (e == cudaSuccess && nall > 0) {
     const int32_t first = split ? nf : 0;
     a.chunks = h->d_chunks[colour] + first;
     a.nchunks = nall - first;
     a.count_launch = defer ? 0 : 1;
+    a.fixed = (all_fixed && defer) ? h->d_fixed[colour] : nullptr;
     e = launch_node_update(a, h->fp64, all_fixed, s);
+    a.fixed = nullptr;
   }
   if (e == cudaSuccess && defer) {  // the bookkeeping; its last CTA advances the half-step counter
     a.count_launch = 1;
@@ -1744,6 +1749,31 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
     }
   }
   if ((rc = setup_shared_kernels(h, s))) return bail(rc);
+  if (!h->fp64) {  // host-resolved records of the fixed leaves' chunks, per colour
+    std::vector<SkRefD> skref(h->dedges.size(), SkRefD{nullptr, nullptr, nullptr});
+    if (h->d_skref) {
+      cudaError_t ce = cudaMemcpyAsync(skref.data(), h->d_skref, sizeof(SkRefD) * skref.size(), cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) return bail(cuda_fail(ce, "read shared-kernel references"));
+    }
+    for (int c = 0; c < 2; ++c) {
+      std::vector<FixedChunkD> fr;
+      for (int32_t k = 0; k < h->nfixed_chunks[c]; ++k) {
+        const NodeChunk& ch = h->chunks[c][k];
+        const NodeD& nd = h->nodes[ch.node];
+        const int32_t di = h->node_dedges[nd.dedge_begin];
+        const DEdgeD& d = h->dedges[di];
+        const ProbD& pd = h->probs[nd.prob];
+        fr.push_back(FixedChunkD{d.off, d.part_off, nd.node_off, ch.node, ch.x0, ch.cnt, nd.n, nd.prob, di, d.nbr,
+                                 d.edge, d.nsplit, pd.cost_kind, pd.eps * 0.69314718055994530942, skref[di]});
+      }
+      if (fr.empty()) continue;
+      if ((rc = h->alloc(&h->d_fixed[c], (int64_t)fr.size()))) return bail(rc);
+      const cudaError_t ce =
+          cudaMemcpyAsync(h->d_fixed[c], fr.data(), sizeof(FixedChunkD) * fr.size(), cudaMemcpyHostToDevice, s);
+      if (ce != cudaSuccess) return bail(cuda_fail(ce, "upload fixed-leaf chunk records"));
+    }
+  }
 
   auto up = [&](void* dst, const void* src, size_t bytes) -> int {
     if (bytes == 0) return TREE_OT_OK;

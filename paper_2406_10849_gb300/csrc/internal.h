@@ -103,6 +103,18 @@ struct SkRefD {
   const float* rf;
   const float* cm;
 };
+// A fixed leaf's node-update chunk with its node and its one owned directed edge
+// resolved on the host (the fixed-leaf kernel's fast path: the chunk's loads
+// depend on one load of this record).
+struct FixedChunkD {
+  int64_t d_off, part_off, node_off;  // the directed edge's vectors, its partials, the node's vectors
+  int32_t node, x0, cnt, n;           // node, first point, points, support size
+  int32_t prob, di, nbr, edge;        // problem, directed edge, neighbour node, edge
+  int32_t nsplit, cost_kind;
+  double eps_ln2;
+  SkRefD sk;                          // shared-kernel references (null pointers outside a group)
+};
+
 // the same, as a node-update CTA keeps it (the column maximum read once)
 struct SkEdgeS {
   const float* s;
@@ -279,6 +291,7 @@ struct NodeArgs {
   int32_t count_launch;      // 1: the last CTA of the launch advances the half-step counter
   int32_t defer;             // 1: chunks leave the arrival bookkeeping to node_finish_kernel
   const SkRefD* sk_ref;      // per directed edge, for problems in the shared-kernel phase (or null)
+  const FixedChunkD* fixed;  // per chunk of a fixed-leaf launch with deferred bookkeeping (or null)
 };
 
 // Per problem, what node_finish_kernel reads for one colour: the directed

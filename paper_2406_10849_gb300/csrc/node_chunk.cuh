@@ -373,6 +373,92 @@ __device__ __forceinline__ float2 regrid(float hi, float lo) {
   return make_float2(hi + q, lo - q);
 }
 
+// One fixed leaf's chunk (FP32 path), from whichever source resolved its data:
+// merge the partials (or the shared-kernel product's sum) into the message,
+// the frame for the next apply, the stopping term of the previous iterate, the
+// potential's operand, drift from an absorbed base; then the chunk's sums.
+struct FixedView {
+  int64_t d_off, part_off, node_off;
+  int32_t n, x0, cnt, ns, edge, di;
+  float2 zk;     // the neighbour's normaliser Z_k log2(e), two-float
+  double eps_ln2;
+  bool one_piece, track;
+  SkEdgeS sk;
+};
+
+template <int kItF>
+__device__ __forceinline__ void fixed_leaf_pass(const NodeArgs& A, const FixedView& v, double* red) {
+  const int tid = threadIdx.x;
+  float r = 0.f;
+  bool drift = false, bad = false;
+  for (int xb = 0; xb < v.cnt; xb += kItF * kNodeThreads) {
+    Part2 pv[kItF];
+    float4 lg[kItF];
+    float oh[kItF], ol[kItF];
+#pragma unroll
+    for (int k = 0; k < kItF; ++k) {
+      const int x = v.x0 + min(xb + tid + k * kNodeThreads, v.cnt - 1);  // past the end: reload the last point
+      pv[k] = v.one_piece ? load_sk_raw(v.sk, x) : load_part2(A.part32 + v.part_off + x, v.ns, v.n);
+      lg[k] = A.lgf[v.node_off + x];  // log2 mu (hi, lo), mu
+      oh[k] = A.hh[v.d_off + x];
+      ol[k] = A.hl[v.d_off + x];
+    }
+#pragma unroll
+    for (int k = 0; k < kItF; ++k) {
+      const int xi = xb + tid + k * kNodeThreads;
+      if (xi >= v.cnt) break;
+      const int x = v.x0 + xi;
+      if (v.one_piece) resolve_sk(pv[k], v.sk.cm, A.part32 + v.part_off, x);
+      const float2 mm = merge32_l2(pv[k], A.part32 + v.part_off + x, v.ns, v.n);
+      A.fr[v.d_off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+      const float mh = mm.x - v.zk.x, ml = mm.y - v.zk.y;  // (m - Z_k) log2(e)
+      // stopping term mu |exp(f/eps + m) - 1| of the previous iterate; f/eps log2(e) = h - log2 mu
+      if (lg[k].z > 0.f) r += lg[k].z * fabsf(ex2(((oh[k] - lg[k].x) + mh) + ((ol[k] - lg[k].y) + ml)) - 1.f);
+      float2 h2;
+      if (lg[k].x == -INFINITY) {
+        A.f[v.d_off + x] = -v.eps_ln2 * ((double)mh + (double)ml);  // mu = 0: the operand cannot carry f
+        h2 = make_float2(-INFINITY, 0.f);
+      } else {
+        h2 = regrid(lg[k].x - mh, lg[k].y - ml);
+        if (!isfinite(mh)) bad = true;
+      }
+      A.hh[v.d_off + x] = h2.x;
+      A.hl[v.d_off + x] = h2.y;
+      if (v.track && h2.x > -INFINITY && fabsf((h2.x - A.bh[v.d_off + x]) + (h2.y - A.bl[v.d_off + x])) > A.tau)
+        drift = true;
+    }
+  }
+  if (__syncthreads_or(drift) && tid == 0) atomicOr(&A.drift[v.edge], 1);
+  const float rs = block_sum_f0(r, reinterpret_cast<float*>(red));
+  if (tid == 0) atomicAdd(&A.resid_acc[v.di], (double)rs);
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
+}
+
+// A fixed leaf's chunk from its host-resolved record (the fixed-leaf kernel, FP32,
+// deferred bookkeeping): one load of the record, then the problem's flags, the
+// neighbour's normaliser and the column maximum, then the pass -- instead of the
+// chunk -> node -> owned edge -> edge record -> normaliser chain of the general path.
+__device__ __forceinline__ void fixed_chunk_fast(const NodeArgs& A, const FixedChunkD& fc, double* red) {
+  if (A.done[fc.prob] != 0) return;  // block-uniform
+  const int lp = A.absorbed ? A.lowp[fc.prob] : 0;
+  FixedView v;
+  v.d_off = fc.d_off;
+  v.part_off = fc.part_off;
+  v.node_off = fc.node_off;
+  v.n = fc.n;
+  v.x0 = fc.x0;
+  v.cnt = fc.cnt;
+  v.edge = fc.edge;
+  v.di = fc.di;
+  v.zk = split_l2(A.Z[fc.nbr] * kLog2e);
+  v.eps_ln2 = fc.eps_ln2;
+  v.one_piece = lp == 1 && fc.cost_kind != 0 && fc.sk.s != nullptr;
+  v.track = lp == 1 && fc.cost_kind == 0;
+  v.ns = v.one_piece ? 1 : fc.nsplit;
+  if (v.one_piece) v.sk = SkEdgeS{fc.sk.s, fc.sk.rf, *fc.sk.cm, 0.f};
+  fixed_leaf_pass<2>(A, v, red);
+}
+
 template <bool FIXED_ONLY>
 __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
                                unsigned char* sm, int node_id) {
@@ -414,55 +500,24 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   constexpr int kIt = 4;
 
   if (FIXED_ONLY || nd.fixed) {  // a leaf: one edge, one pass
-    // the fixed-leaf kernel batches two pairs per thread (fewer live registers, more CTAs per SM)
-    constexpr int kItF = FIXED_ONLY ? 2 : kIt;
     const DEdgeD& d = s_de[0];
-    const float2 zk = s_zk[0];
-    const int ns = one_piece ? 1 : d.nsplit;
-    const double eps_ln2 = P.eps * kLn2;
-    float r = 0.f;
-    bool drift = false;
-    for (int xb = 0; xb < cnt; xb += kItF * kNodeThreads) {
-      Part2 pv[kItF];
-      float4 lg[kItF];
-      float oh[kItF], ol[kItF];
-#pragma unroll
-      for (int k = 0; k < kItF; ++k) {
-        const int x = c.x0 + min(xb + tid + k * kNodeThreads, cnt - 1);  // past the end: reload the last point
-        pv[k] = one_piece ? load_sk_raw(s_sk[0], x) : load_part2(A.part32 + d.part_off + x, ns, nd.n);
-        lg[k] = A.lgf[nd.node_off + x];  // log2 mu (hi, lo), mu
-        oh[k] = A.hh[d.off + x];
-        ol[k] = A.hl[d.off + x];
-      }
-#pragma unroll
-      for (int k = 0; k < kItF; ++k) {
-        const int xi = xb + tid + k * kNodeThreads;
-        if (xi >= cnt) break;
-        const int x = c.x0 + xi;
-        if (one_piece) resolve_sk(pv[k], s_sk[0].cm, A.part32 + d.part_off, x);
-        const float2 mm = merge32_l2(pv[k], A.part32 + d.part_off + x, ns, nd.n);
-        A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
-        const float mh = mm.x - zk.x, ml = mm.y - zk.y;  // (m - Z_k) log2(e)
-        // stopping term mu |exp(f/eps + m) - 1| of the previous iterate; f/eps log2(e) = h - log2 mu
-        if (lg[k].z > 0.f) r += lg[k].z * fabsf(ex2(((oh[k] - lg[k].x) + mh) + ((ol[k] - lg[k].y) + ml)) - 1.f);
-        float2 h2;
-        if (lg[k].x == -INFINITY) {
-          A.f[d.off + x] = -eps_ln2 * ((double)mh + (double)ml);  // mu = 0: the operand cannot carry f
-          h2 = make_float2(-INFINITY, 0.f);
-        } else {
-          h2 = regrid(lg[k].x - mh, lg[k].y - ml);
-          if (!isfinite(mh)) bad = true;
-        }
-        A.hh[d.off + x] = h2.x;
-        A.hl[d.off + x] = h2.y;
-        if (track && h2.x > -INFINITY && fabsf((h2.x - A.bh[d.off + x]) + (h2.y - A.bl[d.off + x])) > A.tau)
-          drift = true;
-      }
-    }
-    if (__syncthreads_or(drift) && tid == 0) atomicOr(&A.drift[d.edge], 1);
-    const float rs = block_sum_f0(r, reinterpret_cast<float*>(red));
-    if (tid == 0) atomicAdd(&A.resid_acc[s_di[0]], (double)rs);
-    if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
+    FixedView v;
+    v.d_off = d.off;
+    v.part_off = d.part_off;
+    v.node_off = nd.node_off;
+    v.n = nd.n;
+    v.x0 = c.x0;
+    v.cnt = cnt;
+    v.ns = one_piece ? 1 : d.nsplit;
+    v.edge = d.edge;
+    v.di = s_di[0];
+    v.zk = s_zk[0];
+    v.eps_ln2 = P.eps * kLn2;
+    v.one_piece = one_piece;
+    v.track = track;
+    if (one_piece) v.sk = s_sk[0];
+    // the fixed-leaf kernel batches two pairs per thread (fewer live registers, more CTAs per SM)
+    fixed_leaf_pass<FIXED_ONLY ? 2 : kIt>(A, v, red);
     return;
   }
 

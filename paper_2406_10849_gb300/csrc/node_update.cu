@@ -61,6 +61,12 @@ template <bool F64>
 __global__ void __launch_bounds__(kNodeThreads, 4) node_update_fixed_kernel(NodeArgs A) {
   extern __shared__ __align__(16) unsigned char node_sm[];
   __shared__ double red[kNodeThreads / 32];
+  if constexpr (!F64) {
+    if (A.fixed && A.defer) {  // launch-uniform: host-resolved chunk records
+      fixed_chunk_fast(A, A.fixed[blockIdx.x], red);
+      return;
+    }
+  }
   const NodeChunk c = A.chunks[blockIdx.x];
   const int64_t t_now = *((volatile const int64_t*)A.hs);
   node_chunk_item<F64, true>(A, c, t_now, node_sm, red);
