@@ -13,6 +13,7 @@
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled (the encoder is fetched through the runtime)
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <cmath>
@@ -496,12 +497,14 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
 // ---------------------------------------------------------------------------
 constexpr int kTcEpiWarps = 8;                        // two per tensor-memory lane quarter (4 or 8)
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;     // producer, MMA, epilogue warps
-constexpr int kTcK = 64;                              // reduction points per stage (128-byte rows)
-constexpr int kTcN = 128;                             // output columns per tile (MMA N)
-constexpr int kTcTileBytes = kSkTileM * kTcK * 2;     // 16 KB: one K' part (128 rows)
-constexpr int kTcBBytes = kTcN * kTcK * 2;            // one V' part (kTcN columns)
+constexpr int kTcK = 64;                              // reduction points per stage: 64 (128-byte rows,
+                                                      // 128-byte swizzle) or 32 (64-byte rows and swizzle)
+constexpr int kTcN = 128;                             // output columns per tile (MMA N: 128 or 256)
+constexpr int kTcRowBytes = kTcK * 2;                 // one operand row of a stage (the swizzle span)
+constexpr int kTcTileBytes = kSkTileM * kTcRowBytes;  // one K' part (128 rows)
+constexpr int kTcBBytes = kTcN * kTcRowBytes;         // one V' part (kTcN columns)
 constexpr int kTcStageBytes = 2 * kTcTileBytes + 2 * kTcBBytes;
-constexpr int kTcStages = kTcN == 256 ? 2 : 3;
+constexpr int kTcStages = std::min(8, (216 * 1024) / kTcStageBytes);  // as many as shared memory holds
 constexpr int kTcAcc = 2;                             // accumulators in tensor memory
 constexpr int kTcMaxTiles = 512;                      // tiles one CTA may own (the grid grows beyond)
 constexpr size_t kTcSmem = kTcStages * kTcStageBytes + 1024;  // stages + alignment slack
@@ -510,15 +513,18 @@ constexpr uint32_t kTcCols = kTcAcc * kTcN;                   // tensor memory c
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kSkTileM >> 4) << 24);
 constexpr uint64_t kTcWaitNs = 250ull * 1000 * 1000;  // a wait gives up after 250 ms
-static_assert(kSkTileM == 128 && (kTcN == 128 || kTcN == 256) && kSkPadK % kTcK == 0, "tcgen05 tile 128 x N x 64");
+static_assert(kSkTileM == 128 && (kTcN == 128 || kTcN == 256) && (kTcK == 64 || kTcK == 32) && kSkPadK % kTcK == 0,
+              "tcgen05 tile 128 x N x 32 or 64");
 static_assert(kTcStages * kTcStageBytes + 1024 <= 227 * 1024, "stages fit in shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: 128-byte-swizzled K-major tile, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// shared-memory matrix descriptor of a K-major tile swizzled over its row span
+// (128 or 64 bytes: layout codes 2 and 4), 8-row groups 8 rows apart
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+  constexpr uint64_t layout = kTcRowBytes == 128 ? 2 : 4;
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * kTcRowBytes) >> 4) << 32) |
+         ((uint64_t)1 << 46) | (layout << 61);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
@@ -703,8 +709,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = stage0 + b * kTcStageBytes;
-          const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + kTcTileBytes);
-          const uint64_t bh = sw128_desc(sa + 2 * kTcTileBytes), bl = sw128_desc(sa + 2 * kTcTileBytes + kTcBBytes);
+          const uint64_t ah = sw_desc(sa), al = sw_desc(sa + kTcTileBytes);
+          const uint64_t bh = sw_desc(sa + 2 * kTcTileBytes), bl = sw_desc(sa + 2 * kTcTileBytes + kTcBBytes);
           for (int k = 0; k < kTcK / 16; ++k) {
             const uint64_t dk = (uint64_t)((k * 32) >> 4);  // 16 BF16 further along K
             tc_mma(d, ah + dk, bh + dk, (kt | k) != 0 ? 1u : 0u);
@@ -920,7 +926,8 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
     const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, kTcRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
   return make(&m->khi, a.khi, a.mp, kSkTileM) && make(&m->klo, a.klo, a.mp, kSkTileM) &&
