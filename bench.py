@@ -621,6 +621,59 @@ def bench_fig4_wls(dev, stream, seeds: int = 5, delta: float = 0.2, alpha: float
             "trend": {"half_steps_per_log_d": float(slope_d), "r2_vs_log_d": r2_d, "loglog_exponent_vs_E": exp_E}}
 
 
+def bench_jt_general(dev, stream, steps: int = 40):
+    """General modified junction trees (Sec. 4) on the GPU's general path
+    (tree_ot_jt_*): the nested example of ass:inclusion at d = 8 (cliques of up to
+    8^4 entries) and the WLS junction tree (J = 12, d = 20, alpha = 10) through the
+    general separator update, against WLS reduced to its tree of separators and
+    solved by the tree kernels: us per half-step (CUDA events) and the solve to
+    the stopping threshold."""
+    import torch
+
+    import gen
+    import paper_2406_10849_gb300 as T
+    from paper_2406_10849_gb300 import junction as JR
+    from paper_2406_10849_gb300.treeot import JunctionSolver
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    out = {}
+    cases = {"nested_d8": (gen.nested_junction_tree(6_700_000, d=8, eps=0.1), 1e-8),
+             "wls_J12_d20": (gen.wls_junction_tree(6_700_001, 12, 20), None)}
+    for name, (jt, tol) in cases.items():
+        tol = jt.meta["tol"] if tol is None else tol
+        with JunctionSolver(jt, stream) as s:
+            s.half_steps(2)
+            ms = timed(lambda: s.half_steps(steps))
+            s.reset()
+            t0 = time.perf_counter()
+            rc, hs, r = s.solve(tol=tol, tol_kind="sum", max_half_steps=200000, check_every=16)
+            dt = time.perf_counter() - t0
+            out[name] = {"general_path_us_per_half_step": 1e3 * ms / steps, "solve_s": dt, "half_steps": hs,
+                         "stopping_sum": r, "status": rc, "transport_cost": s.transport_cost()}
+        if name.startswith("wls"):
+            tr = JR.reduce_junction_tree(jt)
+            with T.Solver([tr], T.options(precision="fp32", tol=tol, tol_kind="sum", max_half_steps=200000),
+                          stream=stream) as s:
+                s.half_steps(2)
+                ms = timed(lambda: s.half_steps(steps))
+                s.reset()
+                t0 = time.perf_counter()
+                rc, res = s.solve()
+                dt = time.perf_counter() - t0
+                out[name].update({"reduced_tree_us_per_half_step": 1e3 * ms / steps, "reduced_solve_s": dt,
+                                  "reduced_half_steps": res[0]["half_steps"],
+                                  "reduced_transport_cost": res[0]["transport_cost"]})
+    return out
+
+
 def bench_chain(dev, stream, steps: int):
     """The 5-node chain (n = 64 grid, eps = 0.01, FP64 handle): microseconds per
     half-step (CUDA events) and the solve to a stopping sum below 1e-9."""
@@ -1053,6 +1106,7 @@ def main():
         extra["chain_fp64"] = bench_chain(dev, stream, max(ks, 200))
         extra["fig4"] = bench_fig4(dev, stream)
         extra["fig4_wls"] = bench_fig4_wls(dev, stream)
+        extra["jt_general"] = bench_jt_general(dev, stream)
     cpu = None if (args.no_cpu or world > 1) else cpu_baseline(p)  # the host baseline: N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
