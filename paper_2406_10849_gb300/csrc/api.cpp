@@ -1235,7 +1235,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
     if ((rc = h->alloc(&b, kd)) || (rc = h->alloc(&rf, mp)) || (rc = h->alloc(&cmax, maxc)) ||
         (rc = h->alloc(&khi, (int64_t)mp * kd)) ||
         (rc = h->alloc(&klo, (int64_t)mp * kd)) || (rc = h->alloc(&vhi, maxc * kd)) ||
-        (rc = h->alloc(&vlo, maxc * kd)) || (rc = h->alloc(&sout, maxc * own.n)) ||
+        (rc = h->alloc(&vlo, maxc * kd)) || (rc = h->alloc(&sout, maxc * align_up(own.n, 32))) ||
         (rc = h->alloc(&benv, ((maxc + kSkEnvCols - 1) / kSkEnvCols) * kd)) ||
         (rc = h->alloc(&dc[0], (int64_t)g.cols[0].size())) ||
         (rc = h->alloc(&dc[1], (int64_t)g.cols[1].size())) || (rc = h->alloc(&fix_count, 1)) ||
@@ -1272,15 +1272,22 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       a.vlo = vlo;
       a.part32 = h->d_part32;
       a.sout = sout;
+      a.ldo = (int32_t)align_up(own.n, 32);
       a.fix_count = fix_count;
       a.fix_list = fix_list;
       a.err = h->d_err;
       a.use_tc = !(h->opt.flags & TREE_OT_OPT_SK_MMA_SYNC) && sk_tc_available() ? 1 : 0;
     }
-    // the tcgen05 product needs tensor maps of its operands; without them both colours use mma.sync
+    // the tcgen05 product needs tensor maps of its operands; without them both colours use mma.sync.
+    // Its sums leave through a TMA tensor map too where the shapes allow (else plain stores).
     bool tc = g.args[0].use_tc != 0;
-    for (int c = 0; c < 2 && tc; ++c)
-      if (g.args[c].ncols > 0 && !sk_encode_maps(g.args[c], &g.maps[c])) tc = false;
+    for (int c = 0; c < 2 && tc; ++c) {
+      if (g.args[c].ncols <= 0) continue;
+      g.args[c].store_tma = (g.args[c].nx >= 32 && g.args[c].ncols >= 16) ? 1 : 0;
+      if (sk_encode_maps(g.args[c], &g.maps[c])) continue;
+      g.args[c].store_tma = 0;
+      if (!sk_encode_maps(g.args[c], &g.maps[c])) tc = false;
+    }
     for (int c = 0; c < 2; ++c) g.args[c].use_tc = tc ? 1 : 0;
     CUDA_TRY(launch_sk_reset(b, kd, s));
   }
@@ -1290,7 +1297,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       for (int c = 0; c < 2; ++c)
         for (size_t j = 0; j < g.cols[c].size(); ++j)
           ref[g.cols[c][j].dedge] =
-              SkRefD{g.args[c].sout + (int64_t)j * g.args[c].nx, g.args[c].rf, g.args[c].cmax + j};
+              SkRefD{g.args[c].sout + (int64_t)j * g.args[c].ldo, g.args[c].rf, g.args[c].cmax + j};
     if ((rc = h->alloc(&h->d_skref, (int64_t)ref.size()))) return rc;
     CUDA_TRY(cudaMemcpyAsync(h->d_skref, ref.data(), sizeof(SkRefD) * ref.size(), cudaMemcpyHostToDevice, s));
   }

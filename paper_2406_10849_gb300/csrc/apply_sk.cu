@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
         const int x = m0 + wm + 16 * i + gid + (r >= 2 ? 8 : 0);
         const int cl = wn + 8 * j + 2 * tig + (r & 1);
         if (x >= A.nx || !s_act[cl]) continue;
-        float* const so = A.sout + (int64_t)(n0 + cl) * A.nx;
+        float* const so = A.sout + (int64_t)(n0 + cl) * A.ldo;
         if (!(s_cm[cl] > -kInf)) {  // an empty column (V' not built): no message
           so[x] = 0.f;
           continue;
@@ -504,10 +504,12 @@ constexpr int kTcRowBytes = kTcK * 2;                 // one operand row of a st
 constexpr int kTcTileBytes = kSkTileM * kTcRowBytes;  // one K' part (128 rows)
 constexpr int kTcBBytes = kTcN * kTcRowBytes;         // one V' part (kTcN columns)
 constexpr int kTcStageBytes = 2 * kTcTileBytes + 2 * kTcBBytes;
-constexpr int kTcStages = std::min(8, (216 * 1024) / kTcStageBytes);  // as many as shared memory holds
+constexpr int kTcStages = std::min(8, (200 * 1024) / kTcStageBytes);  // as many as shared memory holds
 constexpr int kTcAcc = 2;                             // accumulators in tensor memory
 constexpr int kTcMaxTiles = 512;                      // tiles one CTA may own (the grid grows beyond)
-constexpr size_t kTcSmem = kTcStages * kTcStageBytes + 1024;  // stages + alignment slack
+constexpr int kTcStgCols = 16;                                // columns per TMA store of the epilogue
+constexpr int kTcStgBytes = 32 * kTcStgCols * 4;              // one epilogue warp's staging buffer
+constexpr size_t kTcSmem = kTcStages * kTcStageBytes + kTcEpiWarps * kTcStgBytes + 1024;  // + alignment slack
 constexpr uint32_t kTcCols = kTcAcc * kTcN;                   // tensor memory columns
 // instruction descriptor: D FP32, A and B BF16, both K-major, N = kTcN, M = 128
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
@@ -515,7 +517,7 @@ constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(k
 constexpr uint64_t kTcWaitNs = 250ull * 1000 * 1000;  // a wait gives up after 250 ms
 static_assert(kSkTileM == 128 && (kTcN == 128 || kTcN == 256) && (kTcK == 64 || kTcK == 32) && kSkPadK % kTcK == 0,
               "tcgen05 tile 128 x N x 32 or 64");
-static_assert(kTcStages * kTcStageBytes + 1024 <= 227 * 1024, "stages fit in shared memory");
+static_assert(kTcSmem + 8 * 1024 <= 227 * 1024, "stages, staging and static tables fit in shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -600,7 +602,7 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n
 __global__ void __launch_bounds__(kTcThreads, 1)
     sk_gemm_tc_kernel(const __grid_constant__ SkArgs A, const __grid_constant__ CUtensorMap tkhi,
                       const __grid_constant__ CUtensorMap tklo, const __grid_constant__ CUtensorMap tvhi,
-                      const __grid_constant__ CUtensorMap tvlo) {
+                      const __grid_constant__ CUtensorMap tvlo, const __grid_constant__ CUtensorMap tout) {
   extern __shared__ __align__(16) unsigned char tc_raw[];
   __shared__ int64_t s_off[kTcN];  // the tile's columns: offset of their sums in sout (-1: inactive)
   __shared__ float s_cm[kTcN];     // and column maximum (-inf: an empty column, S = 0)
@@ -737,6 +739,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- epilogue: warps 2..9, tensor-memory lane quarter warp % 4, column half (warp - 2) / 4 ----
     const int et = tid - 64;  // 0 .. 32 kTcEpiWarps - 1 within the epilogue group
     const int quarter = warp & 3;
+    float* const stg = reinterpret_cast<float*>(tc_raw + (stage0 - raw) + kTcStages * kTcStageBytes +
+                                                (warp - 2) * kTcStgBytes);
+    const uint32_t stg_s = smem_u32(stg);
     constexpr int kSpan = kTcN * 4 / kTcEpiWarps;  // columns per warp
     const int c_beg = ((warp - 2) >> 2) * kSpan;
     for (int i = 0; i < nt; ++i) {
@@ -750,7 +755,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int64_t off = -1;
         if (j < A.ncols && col_active(A, A.cols[j])) {
           cm = A.cmax[j];
-          off = (int64_t)j * A.nx;
+          off = (int64_t)j * A.ldo;
         }
         s_off[c] = off;
         s_cm[c] = cm;
@@ -781,6 +786,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (A.store_tma) {
+          // through this warp's staging buffer ([column][32 rows] FP32) and one TMA store
+          // per 16 columns; rows past nx and columns past ncols are clipped by the tensor
+          // map, inactive columns get values nothing reads
+#pragma unroll
+          for (int hb = 0; hb < 32; hb += kTcStgCols) {
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // buffer free again
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < kTcStgCols; ++q) {
+              const int cl = c0 + hb + q;
+              float val = 0.f;  // inactive or empty column
+              if (row_in && s_off[cl] >= 0 && s_cm[cl] > -kInf) {
+                const float S = __uint_as_float(v[hb + q]);
+                if (!(S >= kSkFixBelow)) {  // (also NaN) recomputed by the fix-up
+                  const int slot = atomicAdd(A.fix_count, 1);
+                  A.fix_list[slot] = make_int2(x, n0 + cl);
+                  val = -1.f;
+                } else {
+                  val = fminf(S, FLT_MAX);
+                }
+              }
+              stg[q * 32 + lane] = val;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copy
+            __syncwarp();
+            if (lane == 0 && m0 + quarter * 32 < A.nx && n0 + c0 + hb < A.ncols)  // (a box wholly outside: none)
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n\t"
+                  "cp.async.bulk.commit_group;" ::"l"(reinterpret_cast<uint64_t>(&tout)),
+                  "r"(m0 + quarter * 32), "r"(n0 + c0 + hb), "r"(stg_s)
+                  : "memory");
+          }
+          continue;
+        }
         if (!row_in) continue;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -807,6 +847,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) tc_arrive(&s_aempty[a]);
     }
   }
+  if (warp >= 2 && lane == 0 && A.store_tma) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -930,8 +971,20 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  return make(&m->khi, a.khi, a.mp, kSkTileM) && make(&m->klo, a.klo, a.mp, kSkTileM) &&
-         make(&m->vhi, a.vhi, a.ncols, kTcN) && make(&m->vlo, a.vlo, a.ncols, kTcN);
+  if (!(make(&m->khi, a.khi, a.mp, kSkTileM) && make(&m->klo, a.klo, a.mp, kSkTileM) &&
+        make(&m->vhi, a.vhi, a.ncols, kTcN) && make(&m->vlo, a.vlo, a.ncols, kTcN)))
+    return false;
+  if (a.store_tma) {  // sums: FP32 [ncols][ldo] (valid x < nx), 32 x 16 boxes, no swizzle
+    const cuuint64_t dims[2] = {(cuuint64_t)a.nx, (cuuint64_t)a.ncols};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.ldo * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)kTcStgCols};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&m->sout, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.sout, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaEvent_t before_product,
@@ -958,7 +1011,7 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ntiles = (int)grid.x * ((a.ncols + kTcN - 1) / kTcN);
     const int ctas = std::max(std::min(ntiles, sms), (ntiles + kTcMaxTiles - 1) / kTcMaxTiles);
-    sk_gemm_tc_kernel<<<ctas, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo);
+    sk_gemm_tc_kernel<<<ctas, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo, maps->sout);
   } else {
     sk_gemm_kernel<<<grid, kSkThreads, kSkSmem, s>>>(a);
   }

@@ -68,7 +68,9 @@ struct SkArgs {
   __nv_bfloat16* vhi;     // [ncols][kd]
   __nv_bfloat16* vlo;
   float2* part32;
-  float* sout;            // [ncols][nx] sums S(x, j) (-1: listed for the fix-up, which writes part32)
+  float* sout;            // [ncols][ldo] sums S(x, j) (-1: listed for the fix-up, which writes part32)
+  int32_t ldo;            // sout's row stride: nx rounded up to 32 floats
+  int32_t store_tma;      // 1: the tcgen05 product writes sout through a TMA tensor map (SkMaps::sout)
   int32_t* fix_count;     // outputs listed for the exact fix-up (reset by the envelope launch)
   int2* fix_list;         // (x, column), capacity nx * ncols
   int32_t* err;           // error word: bit 1 = a bounded wait of the tcgen05 product ran out
@@ -77,6 +79,7 @@ struct SkArgs {
 // tensor maps of the tcgen05 product's operands (128 x 64 BF16 boxes, 128-byte swizzle)
 struct SkMaps {
   CUtensorMap khi, klo, vhi, vlo;
+  CUtensorMap sout;  // FP32 [ncols][ldo], 32 x 16 boxes (outputs x columns); valid when store_tma
 };
 // fills `m` for the operands of `a`; false when cuTensorMapEncodeTiled is unavailable or refuses them
 bool sk_encode_maps(const SkArgs& a, SkMaps* m);
