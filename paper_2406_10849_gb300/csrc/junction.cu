@@ -236,8 +236,11 @@ struct tree_ot_jt_handle {
   int64_t* d_tc_start = nullptr;
   int64_t res_blocks = 0, tc_blocks = 0;
   int64_t hs = 0;
+  cudaGraphExec_t pair = nullptr;   // two half-steps (colour 0, then 1) captured once, replayed
+  cudaStream_t pair_stream = nullptr;
   std::vector<void*> owned;
   ~tree_ot_jt_handle() {
+    if (pair) cudaGraphExecDestroy(pair);
     for (void* p : owned) cudaFree(p);
   }
 };
@@ -762,14 +765,57 @@ int tree_ot_jt_reset(tree_ot_jt_handle* h, void* cuda_stream) {
   return TREE_OT_OK;
 }
 
+namespace {
+int run_half_step(tree_ot_jt_handle* h, cudaStream_t s) {
+  for (const Stage& st : h->stages[h->hs % 2]) JT_TRY(run_stage(st, s));
+  ++h->hs;
+  return TREE_OT_OK;
+}
+
+// a half-step is a few dozen small launches: pairs of half-steps replay one
+// captured CUDA graph (captured on first use, per stream)
+int pair_graph(tree_ot_jt_handle* h, cudaStream_t s) {
+  if (h->pair && h->pair_stream == s) return TREE_OT_OK;
+  if (h->pair) {
+    cudaGraphExecDestroy(h->pair);
+    h->pair = nullptr;
+  }
+  cudaStream_t cap = nullptr;
+  JT_TRY(jt_cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate"));
+  cudaGraph_t g = nullptr;
+  int rc = jt_cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  if (!rc) {
+    const int64_t hs0 = h->hs;
+    h->hs = 0;
+    for (int c = 0; c < 2 && !rc; ++c) rc = run_half_step(h, cap);
+    h->hs = hs0;
+    const int rc2 = jt_cuda(cudaStreamEndCapture(cap, &g), "cudaStreamEndCapture");
+    if (!rc) rc = rc2;
+  }
+  if (!rc) rc = jt_cuda(cudaGraphInstantiate(&h->pair, g, 0), "cudaGraphInstantiate");
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (!rc) h->pair_stream = s;
+  return rc;
+}
+}  // namespace
+
 int tree_ot_jt_half_steps(tree_ot_jt_handle* h, void* cuda_stream, int64_t T) {
   set_last_error("");
   if (!h || T < 0) return jt_fail(TREE_OT_ERR_ARG, "handle is NULL or T < 0");
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  for (int64_t t = 0; t < T; ++t) {
-    for (const Stage& st : h->stages[h->hs % 2]) JT_TRY(run_stage(st, s));
-    ++h->hs;
+  if (T > 0 && h->hs % 2) {  // pairs start with colour 0
+    JT_TRY(run_half_step(h, s));
+    --T;
   }
+  if (T >= 2) {
+    JT_TRY(pair_graph(h, s));
+    for (; T >= 2; T -= 2) {
+      JT_TRY(jt_cuda(cudaGraphLaunch(h->pair, s), "cudaGraphLaunch"));
+      h->hs += 2;
+    }
+  }
+  if (T > 0) JT_TRY(run_half_step(h, s));
   return TREE_OT_OK;
 }
 

@@ -129,3 +129,18 @@ def test_broken_structures_are_rejected(T):
     assert e.value.kind == "MARGINAL"
     with JunctionSolver(jt) as s:   # a valid one still works
         s.half_steps(1)
+
+
+def test_graph_replay_matches_single_half_steps(T):
+    """Runs of two or more half-steps replay a captured pair of half-steps; the
+    iterates are bit-identical to the same half-steps launched one at a time."""
+    from paper_2406_10849_gb300.treeot import JunctionSolver
+    jt = fp32_costs(gen.nested_junction_tree(9100, d=3, eps=0.3))
+    with JunctionSolver(jt) as a, JunctionSolver(jt) as b:
+        a.half_steps(1)
+        a.half_steps(6)        # odd start: one single, then three pairs
+        a.half_steps(2)
+        for _ in range(9):
+            b.half_steps(1)
+        for c in range(len(jt.clique_vars)):
+            assert np.array_equal(a.plan(c), b.plan(c)), c
