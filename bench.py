@@ -434,7 +434,7 @@ def run_batched(args):
 
 
 def bench_stars(dev, stream, stars: int, side: int, steps: int, warmup: int, converge: bool,
-                refine_tol: float = 1.5e-6):
+                refine_tol: float = 1.5e-6, sk_product: str = "auto"):
     """The shared-kernel BF16 phase on a batch of barycenter stars (8 fixed leaves on
     a side x side grid, free centre, eps 0.005: every directed edge of every star
     shares one Gibbs kernel) against the FP32 recomputed-cost path: a half-step of
@@ -449,7 +449,8 @@ def bench_stars(dev, stream, stars: int, side: int, steps: int, warmup: int, con
     probs = gen.warmstart_stars(9_000_000, stars, side=side, eps=0.005)
     n = side * side
     cols = 8 * stars  # directed edges applied per half-step
-    forms = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0, refine_tol=0.0)}
+    forms = {"plain_fp32": {},
+             "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0, refine_tol=0.0, sk_product=sk_product)}
     res = {}
     clocks = None
     for name, kw in forms.items():
@@ -469,10 +470,12 @@ def bench_stars(dev, stream, stars: int, side: int, steps: int, warmup: int, con
                      "kernel_ms_per_half_step": {k: v[0] / steps for k, v in prof.items()}}
         if name == "bf16_shared_kernel":
             clocks = clk.summary()
+            sk_form = {0: "none", 1: "mma.sync", 2: "tcgen05, one CTA per 128-row tile",
+                       3: "tcgen05, CTA pairs (256-row MMAs)"}[s.plan_stats()["sk_product"]]
         s.close()
     if converge:
         solve = {"plain_fp32": {}, "bf16_shared_kernel": dict(apply_mode="bf16", lowp_start=0,
-                                                               refine_tol=refine_tol)}
+                                                               refine_tol=refine_tol, sk_product=sk_product)}
         for name, kw in solve.items():
             s = T.Solver(probs, T.options(tol=1e-6, tol_kind="max", max_half_steps=20000, **kw), stream=stream)
             torch.cuda.synchronize(dev)
@@ -496,7 +499,8 @@ def bench_stars(dev, stream, stars: int, side: int, steps: int, warmup: int, con
         "edge_applies_per_s": cols / (ph["ms_per_half_step"] / 1e3),
         "plain_fp32_edge_applies_per_s": cols / (res["plain_fp32"]["ms_per_half_step"] / 1e3),
         "speedup_per_half_step": res["plain_fp32"]["ms_per_half_step"] / ph["ms_per_half_step"],
-        "product": {"kernel": "sk_gemm_tc_kernel", "ms_per_launch": prod_ms,
+        "product": {"kernel": "sk_gemm_tc_kernel", "form": sk_form,
+                    "ms_per_launch": prod_ms,
                     "pflops_3_products": flops3 / (prod_ms / 1e3) / 1e15,
                     "pflops_method_1_product": flops1 / (prod_ms / 1e3) / 1e15,
                     "peak_pflops": bf16_peak / 1e3, "peak_kind": kind,
@@ -854,7 +858,7 @@ def run_stars(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     b = bench_stars(dev, stream, args.stars, args.side, args.steps, args.warmup, not args.no_converge,
-                    args.refine_tol)
+                    args.refine_tol, args.sk_product)
     ms = b["forms"]["bf16_shared_kernel"]["ms_per_half_step"]
     line = {
         "metric": "edge-kernel applies/sec, shared-kernel BF16 phase (stars on one grid)",
@@ -924,6 +928,8 @@ def main():
     ap.add_argument("--unit-rates", action="store_true",
                     help="only build and run the FP32 / MUFU unit-rate microbenchmark")
     ap.add_argument("--trees", type=int, default=512, help="batched workload: number of trees")
+    ap.add_argument("--sk-product", default="auto", choices=["auto", "one_cta", "mma"],
+                    help="stars workload: the shared-kernel product (auto: tcgen05 over CTA pairs)")
     ap.add_argument("--dense-kernel", default="auto", choices=["auto", "tma", "ldg"],
                     help="stored-cost apply kernel (auto: the solver's autotuner picks)")
     args = ap.parse_args()

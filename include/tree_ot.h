@@ -157,6 +157,10 @@ typedef struct tree_ot_problem {
                                        mma.sync kernel instead of tcgen05 (tensor memory
                                        accumulators); for comparison and for devices
                                        without tcgen05                                     */
+#define TREE_OT_OPT_SK_ONE_CTA 512u /* the tcgen05 product with one CTA per 128-row tile
+                                       instead of CTA pairs of one cluster (256-row MMAs,
+                                       each CTA holding half of a tile's V' operand); the
+                                       same sums, for comparison                           */
 
 #define TREE_OT_TOL_SUM          0  /* the paper's stopping sum (Bipartite Iterative Scaling) */
 #define TREE_OT_TOL_MAX          1  /* the largest single term of that sum                 */
@@ -395,7 +399,9 @@ int tree_ot_get_potentials_batch(tree_ot_handle *h, void *cuda_stream, int32_t c
  * [13] 0 when half-steps run as per-half-step launches, else the persistent
  * forest kernel's CTAs per SM (TREE_OT_OPT_PERSISTENT), [14] bit c set when
  * colour c's node update finishes its bookkeeping in an extra launch
- * (TREE_OT_OPT_NODE_DEFER). */
+ * (TREE_OT_OPT_NODE_DEFER), [15] the shared-kernel BF16 phase's product: 0
+ * no shared-kernel group, 1 mma.sync, 2 tcgen05 with one CTA per 128-row tile,
+ * 3 tcgen05 over CTA pairs (TREE_OT_OPT_SK_ONE_CTA, TREE_OT_OPT_SK_MMA_SYNC). */
 int tree_ot_plan_stats(tree_ot_handle *h, int64_t *stats, int32_t nstats);
 
 /* Launch timing (no paper counterpart: measurement support).  While enabled,

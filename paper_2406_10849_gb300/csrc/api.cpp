@@ -1277,6 +1277,7 @@ int setup_shared_kernels(tree_ot_handle* h, cudaStream_t s) {
       a.fix_list = fix_list;
       a.err = h->d_err;
       a.use_tc = !(h->opt.flags & TREE_OT_OPT_SK_MMA_SYNC) && sk_tc_available() ? 1 : 0;
+      a.tc_pair = a.use_tc && !(h->opt.flags & TREE_OT_OPT_SK_ONE_CTA) && sk_tc_pair_available() ? 1 : 0;
     }
     // the tcgen05 product needs tensor maps of its operands; without them both colours use mma.sync.
     // Its sums leave through a TMA tensor map too where the shapes allow (else plain stores).
@@ -2531,7 +2532,12 @@ int tree_ot_profile_read(tree_ot_handle* h, double* ms, int64_t* launches, int32
 int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
   g_err.clear();
   if (!h || !stats || nstats < 0) return fail(TREE_OT_ERR_ARG, "bad handle or stats pointer");
-  const int64_t v[15] = {(int64_t)h->dedges.size(),
+  int64_t sk_form = 0;  // the shared-kernel product: 0 none, 1 mma.sync, 2 tcgen05 one CTA per tile, 3 CTA pairs
+  for (const auto& g : h->sk)
+    for (int c = 0; c < 2; ++c)
+      if (g.args[c].ncols > 0)
+        sk_form = std::max<int64_t>(sk_form, g.args[c].use_tc ? (g.args[c].tc_pair ? 3 : 2) : 1);
+  const int64_t v[16] = {(int64_t)h->dedges.size(),
                         (int64_t)h->edges.size(),
                         h->elems,
                         h->matrix_bytes,
@@ -2545,8 +2551,9 @@ int tree_ot_plan_stats(tree_ot_handle* h, int64_t* stats, int32_t nstats) {
                         (int64_t)h->rec_variant,
                         (int64_t)h->dense_tma,
                         (int64_t)h->persistent,
-                        (int64_t)((h->node_defer[0] ? 1 : 0) | (h->node_defer[1] ? 2 : 0))};
-  for (int32_t i = 0; i < nstats && i < 15; ++i) stats[i] = v[i];
+                        (int64_t)((h->node_defer[0] ? 1 : 0) | (h->node_defer[1] ? 2 : 0)),
+                        sk_form};
+  for (int32_t i = 0; i < nstats && i < 16; ++i) stats[i] = v[i];
   return TREE_OT_OK;
 }
 

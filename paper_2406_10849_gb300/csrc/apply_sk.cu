@@ -499,27 +499,59 @@ constexpr int kTcEpiWarps = 8;                        // two per tensor-memory l
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;     // producer, MMA, epilogue warps
 constexpr int kTcK = 64;                              // reduction points per stage: 64 (128-byte rows,
                                                       // 128-byte swizzle) or 32 (64-byte rows and swizzle)
-constexpr int kTcN = 128;                             // output columns per tile (MMA N: 128 or 256)
+constexpr int kTcN = 128;                             // output columns per tile of one CTA (MMA N: 128 or 256)
+constexpr int kTcN2 = 256;                            // output columns per tile of a CTA pair (128 or 256)
 constexpr int kTcRowBytes = kTcK * 2;                 // one operand row of a stage (the swizzle span)
 constexpr int kTcTileBytes = kSkTileM * kTcRowBytes;  // one K' part (128 rows)
-constexpr int kTcBBytes = kTcN * kTcRowBytes;         // one V' part (kTcN columns)
-constexpr int kTcStageBytes = 2 * kTcTileBytes + 2 * kTcBBytes;
-constexpr int kTcStages = std::min(8, (200 * 1024) / kTcStageBytes);  // as many as shared memory holds
 constexpr int kTcAcc = 2;                             // accumulators in tensor memory
 constexpr int kTcMaxTiles = 512;                      // tiles one CTA may own (the grid grows beyond)
 constexpr int kTcStgCols = 16;                                // columns per TMA store of the epilogue
 constexpr int kTcStgBytes = 32 * kTcStgCols * 4;              // one epilogue warp's staging buffer
-constexpr size_t kTcSmem = kTcStages * kTcStageBytes + kTcEpiWarps * kTcStgBytes + 1024;  // + alignment slack
-constexpr uint32_t kTcCols = kTcAcc * kTcN;                   // tensor memory columns
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = kTcN, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kSkTileM >> 4) << 24);
 constexpr uint64_t kTcWaitNs = 250ull * 1000 * 1000;  // a wait gives up after 250 ms
-static_assert(kSkTileM == 128 && (kTcN == 128 || kTcN == 256) && (kTcK == 64 || kTcK == 32) && kSkPadK % kTcK == 0,
+static_assert(kSkTileM == 128 && (kTcN == 128 || kTcN == 256) && (kTcN2 == 128 || kTcN2 == 256) &&
+                  (kTcK == 64 || kTcK == 32) && kSkPadK % kTcK == 0,
               "tcgen05 tile 128 x N x 32 or 64");
-static_assert(kTcSmem + 8 * 1024 <= 227 * 1024, "stages, staging and static tables fit in shared memory");
+
+// shapes of the product over kCta CTAs (1, or 2: a CTA pair of one cluster whose
+// MMAs, issued by the even CTA, span 256 rows: each CTA holds its 128 rows of K'
+// and half of the tile's V' rows, and its 128 rows of the accumulator)
+template <int kCta>
+struct TcCfg {
+  static constexpr int kN = kCta == 1 ? kTcN : kTcN2;   // output columns per tile (MMA N)
+  static constexpr int kBRows = kN / kCta;              // V' rows (output columns) one CTA loads
+  static constexpr int kBBytes = kBRows * kTcRowBytes;  // one V' part of a stage
+  static constexpr int kStageBytes = 2 * kTcTileBytes + 2 * kBBytes;
+  static constexpr int kStages = std::min(8, (200 * 1024) / kStageBytes);  // as many as shared memory holds
+  static constexpr size_t kSmem = kStages * kStageBytes + kTcEpiWarps * kTcStgBytes + 1024;  // + alignment slack
+  static constexpr int kRows = kSkTileM * kCta;         // rows of one tile (MMA M)
+  static constexpr uint32_t kCols = kTcAcc * kN;       // tensor memory columns (per CTA)
+  // instruction descriptor: D FP32, A and B BF16, both K-major, M = kRows, N = w (kN or kN / 2)
+  __host__ __device__ static constexpr uint32_t idesc(int w) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(w >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+  }
+  static_assert(kCta == 1 || kCta == 2, "one CTA or a CTA pair");
+  static_assert(kSmem + 8 * 1024 <= 227 * 1024, "stages, staging and static tables fit in shared memory");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// the shared::cluster address of the same shared variable in CTA `rank` of this cluster
+__device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// every thread of both CTAs of the cluster
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // shared-memory matrix descriptor of a K-major tile swizzled over its row span
 // (128 or 64 bytes: layout codes 2 and 4), 8-row groups 8 rows apart
@@ -529,12 +561,20 @@ __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
          ((uint64_t)1 << 46) | (layout << 61);
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
-      : "memory");
+template <int kCta>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (kCta == 1)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_expect(uint64_t* bar, uint32_t bytes) {
@@ -542,28 +582,49 @@ __device__ __forceinline__ void tc_expect(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// one 2-D box (x = reduction index, y = row) into shared memory, completion on bar
-__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
+// one 2-D box (x = reduction index, y = row) into this CTA's shared memory; the
+// completion goes to the mbarrier at shared::cluster address `bar`, in this CTA
+// (kCta 1) or in either CTA of the pair (kCta 2)
+template <int kCta>
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  if constexpr (kCta == 1)
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
 // bounded wait on an mbarrier phase: kTcWaitNs of wall time, 2^24 polls at most
+// (the pair product's barriers see arrivals from the peer CTA: cluster-scope acquire)
+template <int kCta = 1>
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t addr = smem_u32(bar);
   uint64_t start = 0;
   for (uint32_t i = 0; i < (1u << 24); ++i) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
+    if constexpr (kCta == 1)
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(addr), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(addr), "r"(parity)
+          : "memory");
     if (ok) return true;
     if ((i & 63) == 63) {
       uint64_t now;
@@ -578,9 +639,9 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// whether any column of the column tile starting at n0 takes part in this product
-__device__ __forceinline__ bool tc_tile_active(const SkArgs& A, int n0) {
-  for (int c = 0; c < kTcN; ++c) {
+// whether any column of the column tile [n0, n0 + w) takes part in this product
+__device__ __forceinline__ bool tc_tile_active(const SkArgs& A, int n0, int w) {
+  for (int c = 0; c < w; ++c) {
     const int j = n0 + c;
     if (j >= A.ncols) break;
     if (col_active(A, A.cols[j])) return true;  // (an empty column still gets S = 0 written)
@@ -592,79 +653,128 @@ __device__ __forceinline__ void tc_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// one arrival on the mbarrier at shared::cluster address `bar` (this CTA's or the peer's)
+__device__ __forceinline__ void tc_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// arrive on `bar` once every tcgen05.mma issued before has completed; for the
+// pair, on the barrier at the same offset in both CTAs
+template <int kCta>
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
+  if constexpr (kCta == 1)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kTcEpiWarps) : "memory"); }
 
+// kCta 1: one CTA per SM, 128 x kTcN tiles.  kCta 2: launched in clusters of two;
+// a pair owns 256 x kTcN2 tiles, the even CTA issues the MMAs (M = 256) over both
+// CTAs' stages, their copies complete on its full barriers (the odd CTA's through
+// the cta_group::2 form of the copy), its commits arrive on both CTAs' barriers,
+// and both CTAs' epilogue warps release an accumulator on its empty barrier.
+template <int kCta>
 __global__ void __launch_bounds__(kTcThreads, 1)
     sk_gemm_tc_kernel(const __grid_constant__ SkArgs A, const __grid_constant__ CUtensorMap tkhi,
                       const __grid_constant__ CUtensorMap tklo, const __grid_constant__ CUtensorMap tvhi,
                       const __grid_constant__ CUtensorMap tvlo, const __grid_constant__ CUtensorMap tout) {
+  using Cfg = TcCfg<kCta>;
+  constexpr int kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes, kBBytes = Cfg::kBBytes;
   extern __shared__ __align__(16) unsigned char tc_raw[];
-  __shared__ int64_t s_off[kTcN];  // the tile's columns: offset of their sums in sout (-1: inactive)
-  __shared__ float s_cm[kTcN];     // and column maximum (-inf: an empty column, S = 0)
-  __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages], s_afull[kTcAcc], s_aempty[kTcAcc];
+  constexpr int kN = Cfg::kN;
+  __shared__ int64_t s_off[kN];  // the tile's columns: offset of their sums in sout (-1: inactive)
+  __shared__ float s_cm[kN];     // and column maximum (-inf: an empty column, S = 0)
+  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_afull[kTcAcc], s_aempty[kTcAcc];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_tiles[kTcMaxTiles];   // this CTA's active tiles, in order
+  __shared__ int2 s_tiles[kTcMaxTiles];  // this CTA's (pair's) active tiles, in order: (row tile, 2 n0 + whole)
   __shared__ int s_ntiles;
   __shared__ volatile int s_abort;
   __shared__ int s_epi_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = A.mp / kSkTileM;                              // row tiles
-  const int ntiles = mt * ((A.ncols + kTcN - 1) / kTcN);
+  const uint32_t rank = kCta == 1 ? 0u : cluster_rank();  // this CTA's half of a pair tile
+  const int unit = (int)blockIdx.x / kCta, nunits = (int)gridDim.x / kCta;
+  const int mt = (A.mp + Cfg::kRows - 1) / Cfg::kRows;          // row tiles
+  const int ntiles = mt * ((A.ncols + kN - 1) / kN);
   if (blockIdx.x == 0)  // the envelope is consumed: reset it for the next product
     for (int y = tid; y < A.kd; y += kTcThreads) A.b[y] = -kInf;
-  // this CTA's tiles (t = blockIdx.x + i gridDim.x), the inactive ones left out
+  // this CTA's (pair's) tiles, the inactive ones left out; both CTAs of a pair build the
+  // same list.  Tiles t (row tiles fastest) go round-robin (t = unit + i nunits) in
+  // whole rounds; the last, partial round's tiles are split into two kN / 2 column
+  // halves, dealt round-robin as well, when the halves fit one round
   if (tid == 0) {
+    const int rounds = ntiles / nunits, left = ntiles - rounds * nunits;
+    const bool split = left > 0 && 2 * left <= nunits;
+    const int whole = split ? rounds * nunits : ntiles;
     int n = 0;
-    for (int t = blockIdx.x; t < ntiles && n < kTcMaxTiles; t += gridDim.x)
-      if (tc_tile_active(A, (t / mt) * kTcN)) s_tiles[n++] = t;
+    for (int t = unit; t < whole && n < kTcMaxTiles; t += nunits) {
+      const int n0 = (t / mt) * kN;
+      if (tc_tile_active(A, n0, kN)) s_tiles[n++] = make_int2(t % mt, 2 * n0 + 1);
+    }
+    for (int h = unit; split && h < 2 * left && n < kTcMaxTiles; h += nunits) {
+      const int t = whole + h / 2;
+      const int n0 = (t / mt) * kN + (h & 1) * (kN / 2);
+      if (n0 < A.ncols && tc_tile_active(A, n0, kN / 2)) s_tiles[n++] = make_int2(t % mt, 2 * n0);
+    }
     s_ntiles = n;
     s_abort = 0;
   }
   __syncthreads();
   const int nt = s_ntiles;
-  if (nt == 0) return;  // block-uniform
+  if (nt == 0) return;  // uniform across the block and the pair
 
   // stages on a 1024-byte boundary (the swizzle pattern follows the address bits)
   const uint32_t raw = smem_u32(tc_raw);
   const uint32_t stage0 = (raw + 1023u) & ~1023u;
   if (tid == 0) {
-    for (int i = 0; i < kTcStages; ++i) {
+    for (int i = 0; i < kStages; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[i])));
     }
     for (int i = 0; i < kTcAcc; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_afull[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_aempty[i])), "n"(kTcEpiWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_aempty[i])), "n"(kCta * kTcEpiWarps));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(kTcCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (kCta == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                   "r"(Cfg::kCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                   "r"(Cfg::kCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if constexpr (kCta == 2) cluster_sync();  // both CTAs' barriers and tensor memory exist
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const int nk = A.kd / kTcK;
 
   if (warp == 0) {
-    // ---- TMA producer ----
+    // ---- TMA producer (each CTA its own stages) ----
     if (lane == 0) {
       int g = 0;  // stage uses so far, across tiles
       bool ok = true;
       for (int i = 0; i < nt && ok; ++i) {
-        const int t = s_tiles[i];
-        const int m0 = (t % mt) * kSkTileM, n0 = (t / mt) * kTcN;
+        const int2 t = s_tiles[i];
+        const int w = (t.y & 1) ? kN : kN / 2;  // the tile's columns (a V' box holds kBRows rows:
+                                                 // a half tile leaves the box's far half unused)
+        const int m0 = t.x * Cfg::kRows + (int)rank * kSkTileM;
+        const int n0 = (t.y >> 1) + (int)rank * (w / kCta);
         for (int kt = 0; kt < nk; ++kt, ++g) {
-          const int b = g % kTcStages;
-          if (g >= kTcStages && !tc_wait(&s_empty[b], ((g / kTcStages) - 1) & 1)) {
+          const int b = g % kStages;
+          if (g >= kStages && !tc_wait<kCta>(&s_empty[b], ((g / kStages) - 1) & 1)) {
             ok = false;
             break;
           }
@@ -672,57 +782,66 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = false;
             break;
           }
-          const uint32_t dst = stage0 + b * kTcStageBytes;
-          tc_expect(&s_full[b], kTcStageBytes);
-          tma_box(dst, &tkhi, kt * kTcK, m0, &s_full[b]);
-          tma_box(dst + kTcTileBytes, &tklo, kt * kTcK, m0, &s_full[b]);
-          tma_box(dst + 2 * kTcTileBytes, &tvhi, kt * kTcK, n0, &s_full[b]);
-          tma_box(dst + 2 * kTcTileBytes + kTcBBytes, &tvlo, kt * kTcK, n0, &s_full[b]);
+          const uint32_t dst = stage0 + b * kStageBytes;
+          // the pair's copies complete on the even CTA's full barrier, which expects both halves
+          const uint32_t full = kCta == 1 ? smem_u32(&s_full[b]) : peer_addr(smem_u32(&s_full[b]), 0);
+          if (rank == 0) tc_expect(&s_full[b], kCta * kStageBytes);
+          tma_box<kCta>(dst, &tkhi, kt * kTcK, m0, full);
+          tma_box<kCta>(dst + kTcTileBytes, &tklo, kt * kTcK, m0, full);
+          tma_box<kCta>(dst + 2 * kTcTileBytes, &tvhi, kt * kTcK, n0, full);
+          tma_box<kCta>(dst + 2 * kTcTileBytes + kBBytes, &tvlo, kt * kTcK, n0, full);
         }
       }
       if (!ok) {
         s_abort = 1;
         atomicOr(A.err, 2);
       }
-      // every copy issued lands before the CTA may leave (bounded)
-      for (int q = (g > kTcStages ? g - kTcStages : 0); q < g; ++q)
-        (void)tc_wait(&s_full[q % kTcStages], (q / kTcStages) & 1);
+      // every copy issued lands before the CTA may leave (bounded): the even CTA sees
+      // them on its full barriers; the odd CTA through the empty barriers, which the
+      // MMAs that read its copies release
+      for (int q = (g > kStages ? g - kStages : 0); q < g; ++q) {
+        if (rank == 0)
+          (void)tc_wait<kCta>(&s_full[q % kStages], (q / kStages) & 1);
+        else
+          (void)tc_wait<kCta>(&s_empty[q % kStages], (q / kStages) & 1);
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ---- MMA issuer ----
-    if (lane == 0) {
+    // ---- MMA issuer (the even CTA of a pair) ----
+    if (lane == 0 && rank == 0) {
       int g = 0;
       bool ok = true;
       int last_acc = -1, last_use = 0;
       for (int i = 0; i < nt && ok; ++i) {
         const int a = i % kTcAcc;
-        if (i >= kTcAcc && !tc_wait(&s_aempty[a], ((i / kTcAcc) - 1) & 1)) {
+        if (i >= kTcAcc && !tc_wait<kCta>(&s_aempty[a], ((i / kTcAcc) - 1) & 1)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(a * kTcN);
+        const uint32_t d = tmem + (uint32_t)(a * kN);
+        const uint32_t idesc = Cfg::idesc((s_tiles[i].y & 1) ? kN : kN / 2);
         for (int kt = 0; kt < nk; ++kt, ++g) {
-          const int b = g % kTcStages;
-          if (!tc_wait(&s_full[b], (g / kTcStages) & 1) || s_abort) {
+          const int b = g % kStages;
+          if (!tc_wait<kCta>(&s_full[b], (g / kStages) & 1) || s_abort) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = stage0 + b * kTcStageBytes;
+          const uint32_t sa = stage0 + b * kStageBytes;
           const uint64_t ah = sw_desc(sa), al = sw_desc(sa + kTcTileBytes);
-          const uint64_t bh = sw_desc(sa + 2 * kTcTileBytes), bl = sw_desc(sa + 2 * kTcTileBytes + kTcBBytes);
+          const uint64_t bh = sw_desc(sa + 2 * kTcTileBytes), bl = sw_desc(sa + 2 * kTcTileBytes + kBBytes);
           for (int k = 0; k < kTcK / 16; ++k) {
             const uint64_t dk = (uint64_t)((k * 32) >> 4);  // 16 BF16 further along K
-            tc_mma(d, ah + dk, bh + dk, (kt | k) != 0 ? 1u : 0u);
-            tc_mma(d, ah + dk, bl + dk, 1u);
-            tc_mma(d, al + dk, bh + dk, 1u);
+            tc_mma<kCta>(d, ah + dk, bh + dk, idesc, (kt | k) != 0 ? 1u : 0u);
+            tc_mma<kCta>(d, ah + dk, bl + dk, idesc, 1u);
+            tc_mma<kCta>(d, al + dk, bh + dk, idesc, 1u);
           }
-          tc_commit(&s_empty[b]);  // the stage's buffer is free once these MMAs have read it
+          tc_commit<kCta>(&s_empty[b]);  // the stage's buffers are free once these MMAs have read them
         }
         if (!ok) break;
-        tc_commit(&s_afull[a]);  // the tile's accumulator is complete once every MMA before it is
+        tc_commit<kCta>(&s_afull[a]);  // the tile's accumulator is complete once every MMA before it is
         last_acc = a;
         last_use = i / kTcAcc;
       }
@@ -731,25 +850,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         atomicOr(A.err, 2);
       }
       // the last commit covers every MMA issued before it: wait for it before tensor memory goes
-      if (last_acc >= 0) (void)tc_wait(&s_afull[last_acc], last_use & 1);
-      if (g > 0) (void)tc_wait(&s_empty[(g - 1) % kTcStages], ((g - 1) / kTcStages) & 1);
+      if (last_acc >= 0) (void)tc_wait<kCta>(&s_afull[last_acc], last_use & 1);
+      if (g > 0) (void)tc_wait<kCta>(&s_empty[(g - 1) % kStages], ((g - 1) / kStages) & 1);
     }
     __syncwarp();
   } else {
     // ---- epilogue: warps 2..9, tensor-memory lane quarter warp % 4, column half (warp - 2) / 4 ----
     const int et = tid - 64;  // 0 .. 32 kTcEpiWarps - 1 within the epilogue group
     const int quarter = warp & 3;
-    float* const stg = reinterpret_cast<float*>(tc_raw + (stage0 - raw) + kTcStages * kTcStageBytes +
+    float* const stg = reinterpret_cast<float*>(tc_raw + (stage0 - raw) + kStages * kStageBytes +
                                                 (warp - 2) * kTcStgBytes);
     const uint32_t stg_s = smem_u32(stg);
-    constexpr int kSpan = kTcN * 4 / kTcEpiWarps;  // columns per warp
-    const int c_beg = ((warp - 2) >> 2) * kSpan;
+    static_assert(kTcEpiWarps == 8 && kN / 4 >= 32, "two column halves of at least 32 columns");
     for (int i = 0; i < nt; ++i) {
       const int a = i % kTcAcc;
-      const int t = s_tiles[i];
-      const int m0 = (t % mt) * kSkTileM, n0 = (t / mt) * kTcN;
+      const int2 t = s_tiles[i];
+      const int w = (t.y & 1) ? kN : kN / 2;
+      const int span = w / 2;                          // columns per warp
+      const int c_beg = ((warp - 2) >> 2) * span;
+      const int m0 = t.x * Cfg::kRows + (int)rank * kSkTileM, n0 = t.y >> 1;
       epi_sync();  // the previous tile's column table is no longer read
-      for (int c = et; c < kTcN; c += 32 * kTcEpiWarps) {  // the tile's column table
+      for (int c = et; c < w; c += 32 * kTcEpiWarps) {  // the tile's column table
         const int j = n0 + c;
         float cm = -kInf;
         int64_t off = -1;
@@ -760,7 +881,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         s_off[c] = off;
         s_cm[c] = cm;
       }
-      if (et == 0) s_epi_ok = tc_wait(&s_afull[a], (i / kTcAcc) & 1) && !s_abort ? 1 : 0;
+      if (et == 0) s_epi_ok = tc_wait<kCta>(&s_afull[a], (i / kTcAcc) & 1) && !s_abort ? 1 : 0;
       epi_sync();
       if (!s_epi_ok) {
         if (et == 0) {
@@ -773,9 +894,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int x = m0 + quarter * 32 + lane;  // tensor-memory lane = output row
       const bool row_in = x < A.nx;
       float* const sout = A.sout;
-      for (int c0 = c_beg; c0 < c_beg + kSpan; c0 += 32) {
+      for (int c0 = c_beg; c0 < c_beg + span; c0 += 32) {
         uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kTcN + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -844,14 +965,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // this warp's reads of the accumulator are done: release it to the MMA issuer
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) tc_arrive(&s_aempty[a]);
+      if (lane == 0) {
+        if constexpr (kCta == 1)
+          tc_arrive(&s_aempty[a]);
+        else
+          tc_arrive_cluster(peer_addr(smem_u32(&s_aempty[a]), 0));  // the even CTA's
+      }
     }
   }
   if (warp >= 2 && lane == 0 && A.store_tma) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // the pair: neither CTA leaves (nor frees tensor memory) while the other may still
+  // touch its barriers, stages or tensor memory
+  if constexpr (kCta == 2) cluster_sync();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+  if (warp == 1) {
+    if constexpr (kCta == 1)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kCols));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kCols));
+  }
 }
 
 // one CTA per listed output (eight warps over the reduction points, so an output
@@ -924,29 +1058,57 @@ bool sk_gemm_ready() {
   return st == 1;
 }
 
-bool sk_tc_ready() {
+// resident units of the tcgen05 product on the current device: CTAs (kCta 1) or
+// CTA pairs (kCta 2, clusters of two); 0 when it cannot run
+template <int kCta>
+int sk_tc_units() {
   constexpr int kMaxDevices = 64;
-  static std::atomic<int> state[kMaxDevices];  // 0 unknown, 1 available, 2 not
+  static std::atomic<int> state[kMaxDevices];  // 0 unknown, else units + 1
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
   int st = state[dev].load();
   if (st == 0) {
-    int blocks = 0;
-    const bool ok =
-        cudaFuncSetAttribute(sk_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) ==
-            cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sk_gemm_tc_kernel, kTcThreads, kTcSmem) ==
-            cudaSuccess &&
-        blocks >= 1;
-    st = ok ? 1 : 2;
+    const auto kern = sk_gemm_tc_kernel<kCta>;
+    constexpr size_t smem = TcCfg<kCta>::kSmem;
+    int units = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+      if constexpr (kCta == 1) {
+        int blocks = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kTcThreads, smem) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+          units = blocks >= 1 ? sms : 0;  // one CTA per SM
+      } else {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 2;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cfg.gridDim = dim3((unsigned)std::max(2, sms & ~1));
+        cfg.blockDim = dim3(kTcThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess) units = clusters;
+      }
+    }
+    cudaGetLastError();  // (a refused query leaves no error behind)
+    st = units + 1;
     state[dev].store(st);
   }
-  return st == 1;
+  return st - 1;
 }
+
+bool sk_tc_ready(int pair) { return pair ? sk_tc_units<2>() > 0 : sk_tc_units<1>() > 0; }
 
 }  // namespace
 
-bool sk_tc_available() { return sk_tc_ready(); }
+bool sk_tc_available() { return sk_tc_ready(0); }
+
+bool sk_tc_pair_available() { return sk_tc_ready(1); }
 
 bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -972,7 +1134,8 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
   if (!(make(&m->khi, a.khi, a.mp, kSkTileM) && make(&m->klo, a.klo, a.mp, kSkTileM) &&
-        make(&m->vhi, a.vhi, a.ncols, kTcN) && make(&m->vlo, a.vlo, a.ncols, kTcN)))
+        make(&m->vhi, a.vhi, a.ncols, a.tc_pair ? TcCfg<2>::kBRows : TcCfg<1>::kBRows) &&
+        make(&m->vlo, a.vlo, a.ncols, a.tc_pair ? TcCfg<2>::kBRows : TcCfg<1>::kBRows)))
     return false;
   if (a.store_tma) {  // sums: FP32 [ncols][ldo] (valid x < nx), 32 x 16 boxes, no swizzle
     const cuuint64_t dims[2] = {(cuuint64_t)a.nx, (cuuint64_t)a.ncols};
@@ -991,7 +1154,7 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
                       cudaEvent_t after_product) {
   if (a.ncols <= 0) return cudaSuccess;
   if (a.use_tc && !maps) return cudaErrorInvalidValue;
-  if (!(a.use_tc ? sk_tc_ready() : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
+  if (!(a.use_tc ? sk_tc_ready(a.tc_pair) : sk_gemm_ready())) return cudaErrorInvalidConfiguration;
   const int nenv = (a.ncols + kEnvCols - 1) / kEnvCols;
   if (a.ny <= 4 * 256 && a.benv) {
     sk_envelope1_kernel<<<nenv, 256, 0, s>>>(a);
@@ -1003,15 +1166,34 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
   sk_vbuild_kernel<<<(a.ncols + 7) / 8, 256, 0, s>>>(a);
   if (before_product) cudaEventRecord(before_product, s);
   const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
-  if (a.use_tc) {
+  if (a.use_tc && a.tc_pair) {
+    // persistent: as many CTA pairs as can be resident (one CTA per SM), more only if
+    // a pair would own more tiles than its table holds
+    const int mt = (a.mp + 2 * kSkTileM - 1) / (2 * kSkTileM);
+    const int ntiles = mt * ((a.ncols + kTcN2 - 1) / kTcN2);
+    const int pairs = std::max(std::min(ntiles, sk_tc_units<2>()), (ntiles + kTcMaxTiles - 2) / (kTcMaxTiles - 1));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = TcCfg<2>::kSmem;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e =
+        cudaLaunchKernelEx(&cfg, sk_gemm_tc_kernel<2>, a, maps->khi, maps->klo, maps->vhi, maps->vlo, maps->sout);
+    if (e != cudaSuccess) return e;
+  } else if (a.use_tc) {
     // persistent: one CTA per SM (shared memory allows no second), more only if a CTA
     // would own more tiles than its table holds
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ntiles = (int)grid.x * ((a.ncols + kTcN - 1) / kTcN);
-    const int ctas = std::max(std::min(ntiles, sms), (ntiles + kTcMaxTiles - 1) / kTcMaxTiles);
-    sk_gemm_tc_kernel<<<ctas, kTcThreads, kTcSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo, maps->sout);
+    const int ctas = std::max(std::min(ntiles, sk_tc_units<1>()), (ntiles + kTcMaxTiles - 2) / (kTcMaxTiles - 1));
+    sk_gemm_tc_kernel<1><<<ctas, kTcThreads, TcCfg<1>::kSmem, s>>>(a, maps->khi, maps->klo, maps->vhi, maps->vlo,
+                                                                     maps->sout);
   } else {
     sk_gemm_kernel<<<grid, kSkThreads, kSkSmem, s>>>(a);
   }

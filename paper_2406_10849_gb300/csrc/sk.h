@@ -52,6 +52,7 @@ struct SkArgs {
   int32_t nx, ny, dim;
   int32_t mp, kd;         // rows padded to kSkTileM, reduction length padded to kSkPadK
   int32_t use_tc;         // 1: tcgen05 product (tensor memory accumulators), 0: mma.sync
+  int32_t tc_pair;        // 1: the tcgen05 product over CTA pairs (256-row MMAs), 0: one CTA per tile
   const float* hh;
   const float* hl;
   const int32_t* done;
@@ -76,7 +77,8 @@ struct SkArgs {
   int32_t* err;           // error word: bit 1 = a bounded wait of the tcgen05 product ran out
 };
 
-// tensor maps of the tcgen05 product's operands (128 x 64 BF16 boxes, 128-byte swizzle)
+// tensor maps of the tcgen05 product's operands (64-wide BF16 boxes of 128 rows, V' boxes
+// of 64 rows for the pair product; 128-byte swizzle)
 struct SkMaps {
   CUtensorMap khi, klo, vhi, vlo;
   CUtensorMap sout;  // FP32 [ncols][ldo], 32 x 16 boxes (outputs x columns); valid when store_tma
@@ -86,6 +88,8 @@ bool sk_encode_maps(const SkArgs& a, SkMaps* m);
 
 // whether the tcgen05 product can run on the current device
 bool sk_tc_available();
+// whether its CTA-pair form (clusters of two) can run on the current device
+bool sk_tc_pair_available();
 
 // the five launches of one group and colour (nothing to do when ncols == 0)
 // before_product / after_product (may be null): events recorded around the product launch

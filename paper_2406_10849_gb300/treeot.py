@@ -291,8 +291,8 @@ def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, c
     test_stall: test hook, the staged kernel's producer issues nothing (its waits run out);
     persistent: allow the persistent forest launch (TREE_OT_OPT_PERSISTENT; kept only where the
     create-time timing finds it faster);
-    sk_product: the shared-kernel BF16 phase's product ("auto": tcgen05 where available,
-    "mma": the legacy mma.sync kernel);
+    sk_product: the shared-kernel BF16 phase's product ("auto": tcgen05 over CTA pairs where
+    available, "one_cta": tcgen05 with one CTA per 128-row tile, "mma": the legacy mma.sync kernel);
     node_finish: where the node update's bookkeeping runs ("auto": by chunk count per colour,
     "defer": an extra launch after the chunks, "arrive": the last-arriving chunk)."""
     load()
@@ -314,7 +314,7 @@ def options(precision="fp32", tol=1e-6, tol_kind="sum", max_half_steps=100000, c
     if autotune is not None:
         o.autotune = 1 if autotune else 0
     o.flags = ({"auto": 0, "tma": 1, "ldg": 2}[dense_kernel] | (4 if exact_dist else 0) | (0 if transpose else 8)
-               | (16 if test_stall else 0) | {"auto": 0, "mma": 32}[sk_product] | (64 if persistent else 0)
+               | (16 if test_stall else 0) | {"auto": 0, "mma": 32, "one_cta": 512}[sk_product] | (64 if persistent else 0)
                | {"auto": 0, "defer": 128, "arrive": 256}[node_finish])
     return o
 
@@ -507,12 +507,12 @@ class Solver:
             self.set_potential(prob, 2 * e + 1, f[(int(b), int(a))])
 
     def plan_stats(self) -> dict:
-        st = (C.c_int64 * 15)()
-        _check(_lib.tree_ot_plan_stats(self.h, st, 15))
+        st = (C.c_int64 * 16)()
+        _check(_lib.tree_ot_plan_stats(self.h, st, 16))
         keys = ["directed_edges", "edges", "elements_per_half_step", "matrix_bytes_per_half_step",
                 "apply_tasks_c0", "apply_tasks_c1", "device_bytes", "node_ctas_c0", "node_ctas_c1",
                 "recompute_output_block", "recompute_ctas_per_sm", "recompute_variant", "dense_tma",
-                "persistent", "node_defer"]
+                "persistent", "node_defer", "sk_product"]
         return dict(zip(keys, [int(x) for x in st]))
 
 

@@ -116,19 +116,25 @@ def test_mixed_batch(T):
     assert [r["lowp_half_steps"] > 0 for r in res] == [True] * 7 + [False]
 
 
-def test_tensor_memory_product_matches_mma_sync(T):
-    """The tcgen05 product (tensor-memory accumulators) and the mma.sync product
-    form the same split-BF16 sums in a different order: 40 stars (320 columns
-    per colour, a ragged third column tile, two row tiles) agree after six
-    half-steps."""
-    probs = stars(40, side=16, eps=0.01, seed=7_400_000)
+@pytest.mark.parametrize("side", [16, 19, 10])
+def test_tensor_memory_product_matches_mma_sync(T, side):
+    """The tcgen05 product over CTA pairs (256-row MMAs), the one over single CTAs
+    (128-row MMAs) and the mma.sync product form the same split-BF16 sums, the
+    last in a different order: 40 stars (320 columns per colour, a ragged third
+    column tile whose second half lies wholly past the columns) agree after six
+    half-steps.  Supports of 256, 361 and 100 points: rows padded to 256, 384
+    and 128, so a pair tile is full, half past the padded rows, or wholly in the
+    even CTA."""
+    probs = stars(40, side=side, eps=0.01, seed=7_400_000 + side)
     got = {}
-    for prod in ("auto", "mma"):
+    for prod in ("auto", "one_cta", "mma"):
         with T.Solver(probs, T.options(apply_mode="bf16", lowp_start=0, refine_tol=0.0, sk_product=prod)) as s:
+            assert s.plan_stats()["sk_product"] == {"auto": 3, "one_cta": 2, "mma": 1}[prod]
             s.half_steps(6)
             got[prod] = [s.potentials(i) for i in (0, 17, 39)]
-    for a, b, i in zip(got["auto"], got["mma"], (0, 17, 39)):
-        assert rel_err(a, b, probs[i].eps) <= 1e-5
+    for i, a, b, c in zip((0, 17, 39), got["auto"], got["one_cta"], got["mma"]):
+        assert rel_err(a, b, probs[i].eps) <= 1e-6
+        assert rel_err(a, c, probs[i].eps) <= 1e-5
 
 
 def test_large_support_two_pass_envelope(T):
