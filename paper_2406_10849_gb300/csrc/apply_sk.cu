@@ -464,36 +464,47 @@ __global__ void __launch_bounds__(kSkThreads, 1) sk_gemm_kernel(SkArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// tcgen05 variant of the product: a persistent, warp-specialised kernel, one
-// CTA per SM walking 128 x 128 output tiles (row tiles fastest, so the CTAs
-// working on one column tile of V' at a time share it through L2).  A stage
-// holds 64 reduction points of K'hi, K'lo, V'hi and V'lo, each a 128 x 64 BF16
-// box brought by one TMA copy (cp.async.bulk.tensor) in the 128-byte-swizzled
-// K-major layout the MMA descriptors describe; three 64 KB stages.
+// tcgen05 variant of the product: a persistent, warp-specialised kernel in two
+// forms.  One CTA per SM walking 128 x 128 output tiles, or (the default) CTA
+// pairs, clusters of two CTAs on two SMs, walking 256 x 256 tiles: the even
+// CTA issues cta_group::2 MMAs (M = 256) that read K' rows 0-127 and the first
+// half of the tile's V' rows from its own shared memory and K' rows 128-255
+// and the second half of V' from its peer's, and accumulate each CTA's 128
+// rows in that CTA's tensor memory.  Tiles go round-robin, row tiles fastest
+// (so the CTAs working on one column tile of V' at a time share it through
+// L2); a last round that would leave most units idle is split into half-width
+// tiles.  A stage holds 64 reduction points of K'hi, K'lo, V'hi and V'lo, each
+// a 64-wide BF16 box of 128 rows brought by one TMA copy
+// (cp.async.bulk.tensor) in the 128-byte-swizzled K-major layout the MMA
+// descriptors describe; three 64 KB stages per CTA.
 //   warp 0 (one lane): TMA producer -- waits for a stage to be free (empty
-//     barrier), posts its transaction count and the four copies (full barrier);
-//   warp 1 (one lane): MMA issuer -- per stage waits for the copies, issues 12
-//     tcgen05.mma (kind::f16: BF16 operands from shared memory, FP32
-//     accumulators in tensor memory, 128 x 128 x 16 each: the three split
-//     products), commits them to the stage's empty barrier; after a tile's
-//     last stage commits to that accumulator's full barrier;
+//     barrier), posts its transaction count and the four copies (full
+//     barrier; the pair's copies all complete on the even CTA's, which the
+//     even CTA's producer arms with both CTAs' bytes);
+//   warp 1 (one lane, the even CTA's): MMA issuer -- per stage waits for the
+//     copies, issues 12 tcgen05.mma (kind::f16: BF16 operands from shared
+//     memory, FP32 accumulators in tensor memory: the three split products
+//     over four 16-point steps), commits them to the stage's empty barrier
+//     (both CTAs' for a pair); after a tile's last stage commits to that
+//     accumulator's full barrier;
 //   warps 2-9: epilogue -- read a finished accumulator with tcgen05.ld (each
 //     warp its 32-lane quarter of tensor memory, warp % 4, one output row per
-//     thread, and one half of the tile's columns), write the partials,
-//     release the accumulator (empty barrier, one arrival per warp).
-// Two accumulators (2 x 128 tensor-memory columns) let the epilogue of one
-// tile run under the MMAs of the next, and the producer runs up to three
-// stages ahead across tile boundaries.  The epilogue writes one float per
-// output, the sum S (the node update adds the frame R(x) + M_j): on 2000
-// stars the kernel took 117 us with four epilogue warps writing (frame, sum)
-// pairs and re-reading the row frame after every store, 94 us with eight
-// warps and the frame in a register, and 65.5 us with no stores at all;
-// writing half the bytes brings it to the latter (the operands' 1 GB of TMA
-// reads already keep L2 busy).  Tiles whose columns are all inactive
-// are skipped by every role alike (the same test on the same data).  Every
-// wait is bounded; a wait that runs out sets bit 1 of the error word and stops
-// every role; before tensor memory is released the MMA issuer waits (bounded)
-// for its last commit and the producer for every copy it issued.
+//     thread, and one half of the tile's columns), write the sums, release
+//     the accumulator (the even CTA's empty barrier, one arrival per warp of
+//     either CTA).
+// Two accumulators let the epilogue of one tile run under the MMAs of the
+// next, and the producer runs up to three stages ahead across tile
+// boundaries.  The epilogue writes one float per output, the sum S (the node
+// update adds the frame R(x) + M_j), through per-warp staging buffers and TMA
+// stores.  On 2000 stars (n = 1024): one CTA per tile, 90 us; pairs with
+// 128-column tiles, 91 us; pairs with 256-column tiles, 87 us, and 81 us with
+// the last round split.  Tiles whose columns are all inactive are skipped by
+// every role alike (the same test on the same data).  Every wait is bounded;
+// a wait that runs out sets bit 1 of the error word and stops its CTA's
+// roles (the peer's waits then run out too); before tensor memory is
+// released the MMA issuer waits (bounded) for its last commit and the
+// producers for every copy they issued, and a pair's CTAs meet at a cluster
+// barrier so neither leaves while the other may still touch its memory.
 // ---------------------------------------------------------------------------
 constexpr int kTcEpiWarps = 8;                        // two per tensor-memory lane quarter (4 or 8)
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;     // producer, MMA, epilogue warps
