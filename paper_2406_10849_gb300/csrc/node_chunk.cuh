@@ -434,11 +434,96 @@ __device__ __forceinline__ void fixed_leaf_pass(const NodeArgs& A, const FixedVi
   if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
 }
 
+// A fixed leaf's chunk of a shared-kernel column (at most kSkLeafPts points per
+// thread) while its problem is in the BF16 phase, the common case there: every
+// load the chunk makes -- the problem's flags, the neighbour's normaliser, the
+// column maximum and, for every point, the product's sum, the group's row frame,
+// log2 mu and the previous operand -- leaves at once, before the flags are known
+// (they only decide whether the values are used), so the chunk waits for memory
+// twice (its record, then everything else) instead of once per dependent step.
+// Returns false, having written nothing, when the problem is not in the phase.
+// The same arithmetic as fixed_leaf_pass with one piece.
+constexpr int kSkLeafPts = 4;
+__device__ __forceinline__ bool fixed_sk_chunk(const NodeArgs& A, const FixedChunkD& fc, double* red) {
+  const int tid = threadIdx.x;
+  const int done = A.done[fc.prob];
+  const int lp = A.absorbed ? A.lowp[fc.prob] : 0;
+  const double zn = A.Z[fc.nbr];
+  const float cm = *fc.sk.cm;
+  float rfv[kSkLeafPts], sv[kSkLeafPts], oh[kSkLeafPts], ol[kSkLeafPts];
+  float4 lg[kSkLeafPts];
+#pragma unroll
+  for (int k = 0; k < kSkLeafPts; ++k) {
+    const int x = fc.x0 + min(tid + k * kNodeThreads, fc.cnt - 1);  // past the end: reload the last point
+    rfv[k] = fc.sk.rf[x];
+    sv[k] = fc.sk.s[x];
+    lg[k] = A.lgf[fc.node_off + x];
+    oh[k] = A.hh[fc.d_off + x];
+    ol[k] = A.hl[fc.d_off + x];
+  }
+  if (done != 0) return true;  // block-uniform: retired, nothing to do
+  if (lp != 1) return false;   // block-uniform: not in the phase
+  const float2 zk = split_l2(zn * kLog2e);
+  float r = 0.f;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kSkLeafPts; ++k) {
+    const int xi = tid + k * kNodeThreads;
+    if (xi >= fc.cnt) break;
+    const int x = fc.x0 + xi;
+    Part2 pv;
+    pv.a = make_float2(rfv[k], sv[k]);
+    pv.b = make_float2(0.f, 0.f);
+    resolve_sk(pv, cm, A.part32 + fc.part_off, x);
+    const float2 mm = merge32_l2(pv, A.part32 + fc.part_off + x, 1, fc.n);
+    A.fr[fc.d_off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+    const float mh = mm.x - zk.x, ml = mm.y - zk.y;  // (m - Z_k) log2(e)
+    // stopping term mu |exp(f/eps + m) - 1| of the previous iterate; f/eps log2(e) = h - log2 mu
+    if (lg[k].z > 0.f) r += lg[k].z * fabsf(ex2(((oh[k] - lg[k].x) + mh) + ((ol[k] - lg[k].y) + ml)) - 1.f);
+    float2 h2;
+    if (lg[k].x == -INFINITY) {
+      A.f[fc.d_off + x] = -fc.eps_ln2 * ((double)mh + (double)ml);  // mu = 0: the operand cannot carry f
+      h2 = make_float2(-INFINITY, 0.f);
+    } else {
+      h2 = regrid(lg[k].x - mh, lg[k].y - ml);
+      if (!isfinite(mh)) bad = true;
+    }
+    A.hh[fc.d_off + x] = h2.x;
+    A.hl[fc.d_off + x] = h2.y;
+  }
+  // the chunk's stopping sum and error flag in one barrier
+  float* red_f = reinterpret_cast<float*>(red);
+  int* red_b = reinterpret_cast<int*>(red_f + kNodeThreads / 32);
+  r = warp_sum(r);
+  const bool wbad = __any_sync(0xffffffffu, bad);
+  const int lane = tid & 31, w = tid >> 5;
+  if (lane == 0) {
+    red_f[w] = r;
+    red_b[w] = wbad ? 1 : 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float rs = 0.f;
+    int anyb = 0;
+#pragma unroll
+    for (int i = 0; i < kNodeThreads / 32; ++i) {
+      rs += red_f[i];
+      anyb |= red_b[i];
+    }
+    atomicAdd(&A.resid_acc[fc.di], (double)rs);
+    if (anyb) atomicOr(A.err, 1);
+  }
+  return true;
+}
+
 // A fixed leaf's chunk from its host-resolved record (the fixed-leaf kernel, FP32,
 // deferred bookkeeping): one load of the record, then the problem's flags, the
 // neighbour's normaliser and the column maximum, then the pass -- instead of the
 // chunk -> node -> owned edge -> edge record -> normaliser chain of the general path.
 __device__ __forceinline__ void fixed_chunk_fast(const NodeArgs& A, const FixedChunkD& fc, double* red) {
+  if (fc.cost_kind != 0 && fc.sk.s != nullptr && fc.cnt <= kSkLeafPts * kNodeThreads &&
+      fixed_sk_chunk(A, fc, red))  // (record-static test: block-uniform)
+    return;
   if (A.done[fc.prob] != 0) return;  // block-uniform
   const int lp = A.absorbed ? A.lowp[fc.prob] : 0;
   FixedView v;

@@ -63,7 +63,24 @@ __global__ void __launch_bounds__(kNodeThreads, 4) node_update_fixed_kernel(Node
   __shared__ double red[kNodeThreads / 32];
   if constexpr (!F64) {
     if (A.fixed && A.defer) {  // launch-uniform: host-resolved chunk records
-      fixed_chunk_fast(A, A.fixed[blockIdx.x], red);
+      // a grid of resident CTAs walks the records; each CTA copies the next
+      // record into shared memory while it works on the current one
+      constexpr int kWords = sizeof(FixedChunkD) / 4;
+      static_assert(sizeof(FixedChunkD) % 4 == 0 && kWords <= kNodeThreads, "record copied as words");
+      __shared__ __align__(8) FixedChunkD s_rec[2];
+      const int tid = threadIdx.x;
+      if (tid < kWords && (int)blockIdx.x < A.nchunks)
+        reinterpret_cast<int*>(&s_rec[0])[tid] = reinterpret_cast<const int*>(&A.fixed[blockIdx.x])[tid];
+      __syncthreads();
+      int buf = 0;
+      for (int c = blockIdx.x; c < A.nchunks; c += gridDim.x, buf ^= 1) {  // block-uniform
+        const int cn = c + (int)gridDim.x;
+        int nxt = 0;
+        if (tid < kWords && cn < A.nchunks) nxt = reinterpret_cast<const int*>(&A.fixed[cn])[tid];
+        fixed_chunk_fast(A, s_rec[buf], red);
+        if (tid < kWords) reinterpret_cast<int*>(&s_rec[buf ^ 1])[tid] = nxt;
+        __syncthreads();  // the next record is in place; this chunk's shared values are free
+      }
       return;
     }
   }
@@ -173,6 +190,15 @@ cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cu
     if (e != cudaSuccess) return e;
   }
   void* args[] = {const_cast<NodeArgs*>(&a)};
+  if (!fp64 && fixed_only && a.fixed && a.defer) {
+    // host-resolved records of fixed leaves: four resident CTAs per SM walk them
+    // (no dynamic shared memory on that path)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    const int grid = std::min(a.nchunks, 4 * sms);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kNodeThreads), args, 0, s);
+  }
   return cudaLaunchKernel(fn, dim3(a.nchunks), dim3(kNodeThreads), args, a.smem, s);
 }
 
