@@ -544,6 +544,84 @@ __device__ __forceinline__ void fixed_chunk_fast(const NodeArgs& A, const FixedC
   fixed_leaf_pass<2>(A, v, red);
 }
 
+// Point-major form of the free-node update (FP32, degree DEG <= kNodePmDeg): a
+// thread takes a point and all of its DEG edges -- loads every edge's partials
+// and previous operand at once, then merges the messages, the previous
+// iterate's q_k, s = mean_k (m - Z_k) and mean q, and writes the frames, the
+// operands and the stopping terms -- with no per-pair arrays in shared memory.
+// The same arithmetic, in the same order per point, as the three passes of the
+// pair-major form below; then the chunk's part of Z_j.
+template <int DEG, bool ONE>
+__device__ __forceinline__ void free_points32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, double* red,
+                                              const DEdgeD* s_de, const float2* s_zk, int* s_dr, float* s_r,
+                                              const SkEdgeS* s_sk, float2* s_s, bool track, float2 zo, bool& bad) {
+  constexpr bool one_piece = ONE;  // the shared-kernel phase: one sum per output
+  const int tid = threadIdx.x, lane = tid & 31, cnt = c.cnt;
+  const float fdeg = (float)DEG, inv_deg = 1.f / fdeg;
+  float r[DEG];
+#pragma unroll
+  for (int k = 0; k < DEG; ++k) r[k] = 0.f;
+  float smax = -INFINITY;
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) {
+    const int x = c.x0 + xi;
+    Part2 pv[DEG];
+    float oh[DEG], ol[DEG];
+#pragma unroll
+    for (int k = 0; k < DEG; ++k) {
+      const DEdgeD& d = s_de[k];
+      pv[k] = one_piece ? load_sk_raw(s_sk[k], x) : load_part2(A.part32 + d.part_off + x, d.nsplit, nd.n);
+      oh[k] = A.hh[d.off + x];  // f/eps log2(e) of the previous iterate
+      ol[k] = A.hl[d.off + x];
+    }
+    float2 m[DEG];
+    float q[DEG];
+    float sh = 0.f, sl = 0.f, qsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < DEG; ++k) {
+      const DEdgeD& d = s_de[k];
+      if (one_piece) resolve_sk(pv[k], s_sk[k].cm, A.part32 + d.part_off, x);
+      const float2 mm = merge32_l2(pv[k], A.part32 + d.part_off + x, one_piece ? 1 : d.nsplit, nd.n);
+      A.fr[d.off + x] = isfinite(mm.x) ? quant(mm.x + mm.y) : 0.f;
+      const float2 zk = s_zk[k];
+      const float mh = mm.x - zk.x, ml = mm.y - zk.y;
+      m[k] = make_float2(mh, ml);
+      q[k] = ex2(((oh[k] + mh) - zo.x) + ((ol[k] + ml) - zo.y));
+      const float t = sh + mh;  // TwoSum of the hi parts, in edge order
+      const float bb = t - sh;
+      sl += ((sh - (t - bb)) + (mh - bb)) + ml;
+      sh = t;
+      qsum += q[k];
+    }
+    const float sm_h = quant(sh * inv_deg);
+    const float sm_l = (fmaf(-sm_h, fdeg, sh) + sl) * inv_deg;
+    if (!isfinite(sm_h)) bad = true;
+    s_s[xi] = make_float2(sm_h, sm_l);
+    const float qb = qsum * inv_deg;
+    smax = fmaxf(smax, sm_h + sm_l);
+    // g = s - (m - Z_k) (f'/eps in log2, the operand), |q_k - mean q|
+#pragma unroll
+    for (int k = 0; k < DEG; ++k) {
+      const DEdgeD& d = s_de[k];
+      r[k] += fabsf(q[k] - qb);
+      const float2 g = regrid(sm_h - m[k].x, sm_l - m[k].y);
+      A.hh[d.off + x] = g.x;
+      A.hl[d.off + x] = g.y;
+      if (track && fabsf((g.x - A.bh[d.off + x]) + (g.y - A.bl[d.off + x])) > A.tau) s_dr[k] = 1;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < DEG; ++k) {
+    const float v = warp_sum(r[k]);
+    if (lane == 0) atomicAdd(&s_r[k], v);
+  }
+  smax = block_max_f(smax, reinterpret_cast<float*>(red));  // its barriers also publish s_s
+  const float sq = isfinite(smax) ? quant(smax) : 0.f;
+  float se = 0.f;
+  for (int xi = tid; xi < cnt; xi += kNodeThreads) se += ex2((s_s[xi].x - sq) + s_s[xi].y);
+  const float2 sse = block_sum2_f0(se, reinterpret_cast<float2*>(red));
+  if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2((double)sq * kLn2, (double)sse.x + (double)sse.y);
+}
+
 template <bool FIXED_ONLY>
 __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
                                unsigned char* sm, int node_id) {
@@ -607,6 +685,36 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   }
 
   const float2 zo = split_l2(A.Z[node_id] * kLog2e);
+  if (!FIXED_ONLY && deg <= kNodePmDeg) {
+    float2* s_pm = reinterpret_cast<float2*>(sm + L.mi);  // s per point (see node_smem_pm_bytes)
+#define TREEOT_PM(D)                                                                                          \
+  case D:                                                                                                     \
+    if (one_piece)                                                                                            \
+      free_points32<D, true>(A, nd, c, red, s_de, s_zk, s_dr, s_r, s_sk, s_pm, track, zo, bad);               \
+    else                                                                                                      \
+      free_points32<D, false>(A, nd, c, red, s_de, s_zk, s_dr, s_r, s_sk, s_pm, track, zo, bad);              \
+    break;
+    switch (deg) {
+      TREEOT_PM(1)
+      TREEOT_PM(2)
+      TREEOT_PM(3)
+      TREEOT_PM(4)
+      TREEOT_PM(5)
+      TREEOT_PM(6)
+      TREEOT_PM(7)
+      TREEOT_PM(8)
+      default:
+        break;
+    }
+#undef TREEOT_PM
+    __syncthreads();
+    for (int i = tid; i < deg; i += kNodeThreads) {
+      atomicAdd(&A.resid_acc[s_di[i]], (double)s_r[i]);
+      if (s_dr[i]) atomicOr(&A.drift[s_de[i].edge], 1);
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(A.err, 1);
+    return;
+  }
   // pass 1, pairs: (m - Z_k) log2(e), its frame, and q_k = exp(f_(j,k)/eps + m_(j,k) - Z_j)
   {
     PairWalk w(cnt);

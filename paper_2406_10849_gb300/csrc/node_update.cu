@@ -45,8 +45,10 @@ __device__ __forceinline__ void node_launch_done(const NodeArgs& A) {
   }
 }
 
+// three CTAs per SM (the FP32 point-major free-node update would take ~128
+// registers; capped at 80 it spills a little and still runs faster)
 template <bool F64>
-__global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
+__global__ void __launch_bounds__(kNodeThreads, 3) node_update_kernel(NodeArgs A) {
   extern __shared__ __align__(16) unsigned char node_sm[];
   __shared__ double red[kNodeThreads / 32];
   const NodeChunk c = A.chunks[blockIdx.x];
