@@ -1,13 +1,13 @@
 // Shared-kernel BF16 phase: for a group of directed edges that share one
 // squared-Euclidean Gibbs kernel, one colour's messages are one matrix product
-// on the tensor cores (sk.h states the arithmetic).  Five launches per group
-// and colour:
-//   sk_envelope_kernel  M_j = max_y h_j(y), b(y) = max over the active columns of h_j(y) - M_j
-//   sk_kbuild_kernel    R(x) and K'(x,y) = 2^(b(y) - R(x) - s C(x,y)), BF16 hi + lo
-//   sk_vbuild_kernel    V'(y,j) = 2^(h_j(y) - M_j - b(y)), BF16 hi + lo
-//   sk_gemm_kernel      S = K'hi V'hi + K'hi V'lo + K'lo V'hi (mma.sync m16n8k16,
-//                       FP32 accumulation); partial (R(x) + M_j, S(x,j)) per output
-//   sk_fixup_kernel     outputs with S < 2^-96 recomputed as an FP32 log-sum-exp
+// on the tensor cores (sk.h states the arithmetic).  Per group and colour:
+//   sk_envelope(1)_kernel  M_j = max_y h_j(y), b(y) = max over the active columns of h_j(y) - M_j
+//                          (one pass with per-CTA envelopes and sk_envelope_reduce_kernel, or two)
+//   sk_kvbuild_kernel      R(x) and K'(x,y) = 2^(b(y) - R(x) - s C(x,y)) (sk_kbuild_row), and
+//                          V'(y,j) = 2^(h_j(y) - M_j - b(y)) (sk_vbuild_cols), BF16 hi + lo
+//   sk_gemm_tc_kernel      S = K'hi V'hi + K'hi V'lo + K'lo V'hi (tcgen05, FP32 accumulation in
+//                          tensor memory; sk_gemm_kernel: mma.sync m16n8k16); S(x,j) per output
+//   sk_fixup_kernel        outputs with S < 2^-96 recomputed as an FP32 log-sum-exp
 // M, b and R live on the 2^-10 grid, so b - R and h - M - b are exact and the cost
 // term is formed as in the recomputed-cost apply (FMAs with s = s_hi + s_lo).
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled (the encoder is fetched through the runtime)
@@ -229,9 +229,8 @@ __device__ __forceinline__ void store_split4(const float* v, __nv_bfloat16* hi, 
 
 // one CTA per row x, four consecutive columns y per thread and pass (kd is a
 // multiple of kSkPadK); rows past nx and columns past ny are zero
-__global__ void __launch_bounds__(256) sk_kbuild_kernel(SkArgs A) {
+__device__ __forceinline__ void sk_kbuild_row(const SkArgs& A, int x) {
   __shared__ float s_red[8];
-  const int x = blockIdx.x;
   __nv_bfloat16* khi = A.khi + (int64_t)x * A.kd;
   __nv_bfloat16* klo = A.klo + (int64_t)x * A.kd;
   if (x >= A.nx) {
@@ -273,9 +272,9 @@ __global__ void __launch_bounds__(256) sk_kbuild_kernel(SkArgs A) {
 // one warp per column (eight per CTA), four consecutive points per lane and pass
 // (the operand's offset is a multiple of 32 points, kd of kSkPadK); inactive
 // columns are left alone (their outputs are not stored)
-__global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
+__device__ __forceinline__ void sk_vbuild_cols(const SkArgs& A, int blk) {
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int j = blk * 8 + (threadIdx.x >> 5);
   if (j >= A.ncols) return;
   const SkCol col = A.cols[j];
   const float M = A.cmax[j];
@@ -305,6 +304,15 @@ __global__ void __launch_bounds__(256) sk_vbuild_kernel(SkArgs A) {
     }
     store_split4(v, vhi + y0, vlo + y0);
   }
+}
+
+// both operand builds in one launch (they read the same envelope and nothing
+// of each other): CTAs [0, mp) build rows of K', the rest columns of V'
+__global__ void __launch_bounds__(256) sk_kvbuild_kernel(SkArgs A) {
+  if ((int)blockIdx.x < A.mp)  // block-uniform
+    sk_kbuild_row(A, blockIdx.x);
+  else
+    sk_vbuild_cols(A, (int)blockIdx.x - A.mp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1173,8 +1181,7 @@ cudaError_t launch_sk(const SkArgs& a, const SkMaps* maps, cudaStream_t s, cudaE
   } else {
     sk_envelope_kernel<<<nenv, 256, 0, s>>>(a);
   }
-  sk_kbuild_kernel<<<a.mp, 256, 0, s>>>(a);
-  sk_vbuild_kernel<<<(a.ncols + 7) / 8, 256, 0, s>>>(a);
+  sk_kvbuild_kernel<<<a.mp + (a.ncols + 7) / 8, 256, 0, s>>>(a);
   if (before_product) cudaEventRecord(before_product, s);
   const dim3 grid(a.mp / kSkTileM, (a.ncols + kSkTileN - 1) / kSkTileN);
   if (a.use_tc && a.tc_pair) {

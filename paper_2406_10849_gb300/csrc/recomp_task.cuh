@@ -75,10 +75,12 @@ __device__ __forceinline__ float sqdist(float px, float py, float pz, float4 q) 
 // each staged chunk of reduction points; groups merge through shared memory at
 // the end.  Small supports (a few hundred points) thus keep all warps busy.
 //
-// The argument is t = (hh - R) - s |p - q|^2 + hl with s = s_hi + s_lo (exact
-// product inside the FMAs).  Staged values are stored duplicated, (v, v) pairs,
-// so every packed f32x2 operation reads its operands straight from shared
-// memory.
+// The argument is t = (hh - R) - s |p - q|^2 with s = s_hi + s_lo (exact
+// product inside the FMAs), and the term 2^t w with the point's weight
+// w = 2^hl (the operand's low part, |hl| <= 2^-11, staged once per point): one
+// FMA per term instead of an add to t and another to the sum.  Staged values
+// are stored duplicated, (v, v) pairs, so every packed f32x2 operation reads
+// its operands straight from shared memory.
 template <int D>
 __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
   const DEdgeD d = A.dedges[t.dedge];
@@ -125,7 +127,12 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
       const float qy = D > 1 ? -q[1] : 0.f;
       sq[tid] = make_float4(-q[0], -q[0], qy, qy);
       if (D == 3) sz[tid] = make_float4(-q[2], -q[2], 0.f, 0.f);
-      shl[tid] = make_float4(hh, hh, hl, hl);
+      // the operand's low part as a weight of the point's terms: w = 2^hl by its
+      // Taylor series in u = hl ln 2 to the cubic term (|hl| <= 2^-11 after the
+      // node update's regrid: truncation below 2^-40, one FP32 rounding or so)
+      const float u = hl * 0.69314718f;
+      const float w = fmaf(u, fmaf(u, fmaf(u, 1.f / 6.f, 0.5f), 1.f), 1.f);
+      shl[tid] = make_float4(hh, hh, w, w);
     }
     __syncthreads();
     const int cnt = min(kApplyThreads, t.rcount - ch);
@@ -158,11 +165,11 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
           c01 = fma2(dz01, dz01, c01);
           c23 = fma2(dz23, dz23, c23);
         }
-        const float2 h2 = make_float2(hv.x, hv.y), l2 = make_float2(hv.z, hv.w);
+        const float2 h2 = make_float2(hv.x, hv.y);
         float2 t01 = fma2(c01, nhi, add2(h2, nR01));
         float2 t23 = fma2(c23, nhi, add2(h2, nR23));
-        t01 = add2(fma2(c01, nlo, t01), l2);
-        t23 = add2(fma2(c23, nlo, t23), l2);
+        t01 = fma2(c01, nlo, t01);
+        t23 = fma2(c23, nlo, t23);
         tv[0][jj] = t01.x;
         tv[1][jj] = t01.y;
         tv[2][jj] = t23.x;
@@ -219,16 +226,23 @@ __device__ void recomp_task(const ApplyArgs& A, const Task& t, float* sm) {
                 const float dz = pzk + sz[j + jj].x;
                 c = fmaf(dz, dz, c);
               }
-              tv[k][jj] = arg1(hv.x, Rn, c, shi, slo, hv.z);
+              tv[k][jj] = fmaf(-c, slo, fmaf(-c, shi, hv.x - Rn));
             }
           }
         }
       }
+      // sum of 2^t 2^hl (the weight: t leaves out the operand's low part)
+      float2 w2[kRecPts];
+#pragma unroll
+      for (int jj = 0; jj < kRecPts; ++jj) {
+        const float w = shl[j + jj].z;
+        w2[jj] = make_float2(w, w);
+      }
 #pragma unroll
       for (int k = 0; k < 4; k += 2) {
-        float2 s01 = make_float2(ex2(tv[k][0]), ex2(tv[k + 1][0]));
+        float2 s01 = mul2(make_float2(ex2(tv[k][0]), ex2(tv[k + 1][0])), w2[0]);
 #pragma unroll
-        for (int jj = 1; jj < kRecPts; ++jj) s01 = add2(s01, make_float2(ex2(tv[k][jj]), ex2(tv[k + 1][jj])));
+        for (int jj = 1; jj < kRecPts; ++jj) s01 = fma2(make_float2(ex2(tv[k][jj]), ex2(tv[k + 1][jj])), w2[jj], s01);
         acc[k] += s01.x;
         acc[k + 1] += s01.y;
       }
