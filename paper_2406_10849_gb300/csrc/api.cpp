@@ -1691,9 +1691,7 @@ int tree_ot_create(const tree_ot_problem* probs, int32_t num_probs, const tree_o
       for (int32_t c = 0; c < nd.nchunks; ++c)
         h->chunks[nd.colour].push_back(NodeChunk{(int32_t)j, c, c * cp, std::min(cp, nd.n - c * cp)});
       if (pass == 0) h->nfixed_chunks[nd.colour] += nd.nchunks;
-      const uint32_t b = (!h->fp64 && !nd.fixed && nd.deg <= kNodePmDeg)
-                             ? node_smem_pm_bytes(nd.deg, std::min(cp, nd.n))
-                             : node_smem_layout(nd.deg, std::min(cp, nd.n), h->fp64).bytes;
+      const uint32_t b = node_smem_layout(nd.deg, std::min(cp, nd.n), h->fp64).bytes;
       h->node_smem[nd.colour] = std::max(h->node_smem[nd.colour], b);
     }
   if (std::max(h->node_smem[0], h->node_smem[1]) > kNodeSmemMax)

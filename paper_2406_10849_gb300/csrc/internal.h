@@ -147,9 +147,11 @@ __host__ __device__ inline NodeSmem node_smem_layout(int32_t deg, int32_t cnt, b
   L.bytes = L.qb + node_align16((uint32_t)cnt * qs);
   return L;
 }
-// FP32 free nodes of degree at most kNodePmDeg take the point-major update (one
-// thread per point, all of its edges in registers): of the layout above they
-// use the per-edge tables and s, placed where the per-pair arrays start
+// FP32 free nodes of degree at most kNodePmDeg take the point-major update in
+// the shared-kernel phase (one thread per point, all of its edges in
+// registers): of the layout above it uses the per-edge tables and s, placed
+// where the per-pair arrays start, node_smem_pm_bytes in all (the launch
+// reserves the full layout: outside the phase the same chunk is pair-major)
 constexpr int kNodePmDeg = 8;
 __host__ __device__ inline uint32_t node_smem_pm_bytes(int32_t deg, int32_t cnt) {
   return node_smem_layout(deg, cnt, false).mi + node_align16((uint32_t)cnt * 8u);

@@ -544,13 +544,15 @@ __device__ __forceinline__ void fixed_chunk_fast(const NodeArgs& A, const FixedC
   fixed_leaf_pass<2>(A, v, red);
 }
 
-// Point-major form of the free-node update (FP32, degree DEG <= kNodePmDeg): a
-// thread takes a point and all of its DEG edges -- loads every edge's partials
-// and previous operand at once, then merges the messages, the previous
-// iterate's q_k, s = mean_k (m - Z_k) and mean q, and writes the frames, the
-// operands and the stopping terms -- with no per-pair arrays in shared memory.
-// The same arithmetic, in the same order per point, as the three passes of the
-// pair-major form below; then the chunk's part of Z_j.
+// Point-major form of the free-node update (FP32, degree DEG <= kNodePmDeg,
+// taken in the shared-kernel phase, where each message is one sum): a thread
+// takes a point and all of its DEG edges -- loads every edge's sum and previous
+// operand at once, then merges the messages, the previous iterate's q_k,
+// s = mean_k (m - Z_k) and mean q, and writes the frames, the operands and the
+// stopping terms -- with no per-pair arrays in shared memory.  The same
+// arithmetic, in the same order per point, as the three passes of the
+// pair-major form below; then the chunk's part of Z_j.  (With several partial
+// pieces per message, as outside the phase, the pair-major form was faster.)
 template <int DEG, bool ONE>
 __device__ __forceinline__ void free_points32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, double* red,
                                               const DEdgeD* s_de, const float2* s_zk, int* s_dr, float* s_r,
@@ -622,7 +624,9 @@ __device__ __forceinline__ void free_points32(const NodeArgs& A, const NodeD& nd
   if (tid == 0) A.zpart[nd.chunk_base + c.chunk] = make_double2((double)sq * kLn2, (double)sse.x + (double)sse.y);
 }
 
-template <bool FIXED_ONLY>
+// PM: the kernel carries the point-major form for the shared-kernel phase
+// (handles with shared-kernel groups; it needs more registers than the rest)
+template <bool FIXED_ONLY, bool PM = false>
 __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, const ProbD& P, double* red,
                                unsigned char* sm, int node_id) {
   const int deg = nd.deg, cnt = c.cnt, np = deg * cnt;
@@ -685,14 +689,11 @@ __device__ void chunk_update32(const NodeArgs& A, const NodeD& nd, const NodeChu
   }
 
   const float2 zo = split_l2(A.Z[node_id] * kLog2e);
-  if (!FIXED_ONLY && deg <= kNodePmDeg) {
-    float2* s_pm = reinterpret_cast<float2*>(sm + L.mi);  // s per point (see node_smem_pm_bytes)
+  if (PM && !FIXED_ONLY && deg <= kNodePmDeg && one_piece) {
+    float2* s_pm = reinterpret_cast<float2*>(sm + L.mi);  // s per point, where the per-pair arrays start
 #define TREEOT_PM(D)                                                                                          \
   case D:                                                                                                     \
-    if (one_piece)                                                                                            \
-      free_points32<D, true>(A, nd, c, red, s_de, s_zk, s_dr, s_r, s_sk, s_pm, track, zo, bad);               \
-    else                                                                                                      \
-      free_points32<D, false>(A, nd, c, red, s_de, s_zk, s_dr, s_r, s_sk, s_pm, track, zo, bad);              \
+    free_points32<D, true>(A, nd, c, red, s_de, s_zk, s_dr, s_r, s_sk, s_pm, track, zo, bad);                 \
     break;
     switch (deg) {
       TREEOT_PM(1)
@@ -901,7 +902,7 @@ __device__ __forceinline__ void problem_after_update(const NodeArgs& A, int p, c
 // bookkeeping: the last chunk of a node merges Z_j and the node's stopping
 // terms; the last node of a problem records the stopping quantity of iterate
 // t_now and (when asked) retires the problem.
-template <bool F64, bool FIXED_ONLY = false>
+template <bool F64, bool FIXED_ONLY = false, bool PM = false>
 __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChunk c, int64_t t_now,
                                                 unsigned char* node_sm, double* red) {
   const NodeD nd = A.nodes[c.node];
@@ -913,7 +914,7 @@ __device__ __forceinline__ void node_chunk_item(const NodeArgs& A, const NodeChu
     if constexpr (F64)
       chunk_update64(A, nd, c, P, red, node_sm, c.node);
     else
-      chunk_update32<FIXED_ONLY>(A, nd, c, P, red, node_sm, c.node);
+      chunk_update32<FIXED_ONLY, PM>(A, nd, c, P, red, node_sm, c.node);
   }
   if (A.defer) return;  // launch-uniform: the chunk's terms are in resid_acc and zpart
   __syncthreads();

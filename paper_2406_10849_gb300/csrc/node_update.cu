@@ -45,15 +45,25 @@ __device__ __forceinline__ void node_launch_done(const NodeArgs& A) {
   }
 }
 
-// three CTAs per SM (the FP32 point-major free-node update would take ~128
-// registers; capped at 80 it spills a little and still runs faster)
 template <bool F64>
-__global__ void __launch_bounds__(kNodeThreads, 3) node_update_kernel(NodeArgs A) {
+__global__ void __launch_bounds__(kNodeThreads) node_update_kernel(NodeArgs A) {
   extern __shared__ __align__(16) unsigned char node_sm[];
   __shared__ double red[kNodeThreads / 32];
   const NodeChunk c = A.chunks[blockIdx.x];
   const int64_t t_now = *((volatile const int64_t*)A.hs);
   node_chunk_item<F64, false>(A, c, t_now, node_sm, red);
+  node_launch_done(A);
+}
+
+// FP32 handles with shared-kernel groups: the same, plus the point-major form
+// of free nodes in the phase; three CTAs per SM (it would take ~100 registers;
+// capped at 80 it spills a little and still runs faster than at two)
+__global__ void __launch_bounds__(kNodeThreads, 3) node_update_sk_kernel(NodeArgs A) {
+  extern __shared__ __align__(16) unsigned char node_sm[];
+  __shared__ double red[kNodeThreads / 32];
+  const NodeChunk c = A.chunks[blockIdx.x];
+  const int64_t t_now = *((volatile const int64_t*)A.hs);
+  node_chunk_item<false, false, true>(A, c, t_now, node_sm, red);
   node_launch_done(A);
 }
 
@@ -184,6 +194,7 @@ cudaError_t launch_node_update(const NodeArgs& a, bool fp64, bool fixed_only, cu
   const void* fn = fp64 ? (fixed_only ? reinterpret_cast<const void*>(node_update_fixed_kernel<true>)
                                       : reinterpret_cast<const void*>(node_update_kernel<true>))
                         : (fixed_only ? reinterpret_cast<const void*>(node_update_fixed_kernel<false>)
+                           : a.sk_ref ? reinterpret_cast<const void*>(node_update_sk_kernel)
                                       : reinterpret_cast<const void*>(node_update_kernel<false>));
   // more than the default 48 KB of dynamic shared memory only for nodes of very
   // high degree; the attribute is per device and cheap to set again
