@@ -552,7 +552,8 @@ __device__ __forceinline__ void fixed_chunk_fast(const NodeArgs& A, const FixedC
 // stopping terms -- with no per-pair arrays in shared memory.  The same
 // arithmetic, in the same order per point, as the three passes of the
 // pair-major form below; then the chunk's part of Z_j.  (With several partial
-// pieces per message, as outside the phase, the pair-major form was faster.)
+// pieces per message, as outside the phase, it gained little and its registers
+// would weigh on every other handle's node update.)
 template <int DEG, bool ONE>
 __device__ __forceinline__ void free_points32(const NodeArgs& A, const NodeD& nd, const NodeChunk& c, double* red,
                                               const DEdgeD* s_de, const float2* s_zk, int* s_dr, float* s_r,
