@@ -51,6 +51,25 @@ def test_default_options(T):
     assert o.tol == 1e-6 and o.check_every == 32 and o.use_graph == 1
 
 
+def header_option_bits():
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (TREE_OT_OPT_[A-Z_0-9]+)\s+(\d+)u", open(HEADER).read())}
+
+
+def test_option_flags_match_header(T):
+    """The binding's option names set the bits the header defines, each bit once."""
+    bits = header_option_bits()
+    assert len(set(bits.values())) == len(bits)
+    want = {("dense_kernel", "tma"): "DENSE_TMA", ("dense_kernel", "ldg"): "DENSE_LDG",
+            ("exact_dist", True): "EXACT_DIST", ("transpose", False): "NO_TRANSPOSE",
+            ("test_stall", True): "TEST_STALL", ("sk_product", "mma"): "SK_MMA_SYNC",
+            ("sk_product", "one_cta"): "SK_ONE_CTA", ("persistent", True): "PERSISTENT",
+            ("node_finish", "defer"): "NODE_DEFER", ("node_finish", "arrive"): "NODE_ARRIVE"}
+    assert set(want.values()) == {k[len("TREE_OT_OPT_"):] for k in bits}
+    assert T.options().flags == 0
+    for (key, value), name in want.items():
+        assert T.options(**{key: value}).flags == bits["TREE_OT_OPT_" + name], (key, value)
+
+
 @pytest.mark.parametrize("J", [2, 3, 7, 64, 200])
 def test_bipartition_matches_oracle(T, J):
     rng = np.random.default_rng(J)
